@@ -1,0 +1,227 @@
+/*
+ * mrcm.h - C ABI of libmrcm, the GB300 (sm_103a) implementation of the
+ * Multiscale Robin Coupled Method (MRCM) pressure solve for 3-D single-phase
+ * Darcy flow (arXiv 2103.08513).
+ *
+ * The library runs the paper's Alg. MRCM on one GPU:
+ *   mrcm_factor_local       Alg. MRCM first loop, "Assembly": local TPFA +
+ *                           Robin matrices A^H_l (Eq. aijk, Eq. localomegapar,
+ *                           Eq. localomegaint) and their factorisation
+ *   mrcm_solve_mbf          Alg. MRCM first loop, "LocalSolver": all MBFs and
+ *                           particular solutions (Eq. multiscale_functions,
+ *                           Eq. particular_problem_discrete) and their traces
+ *   mrcm_assemble_interface Alg. MRCM "Assembly" of Eq. interface_problem
+ *                           (Eq. sec2-int-APP, Eq. sec2-int-AUU, Eq. sec2-int-bU)
+ *   mrcm_solve_interface    Alg. MRCM "InterfaceSolver"
+ *   mrcm_reconstruct        Alg. MRCM second loop, "ReconstructMscSolution"
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: nx x ny x nz cells of size hx x hy x hz; cell c = i + nx*(j + ny*k)
+ * (x fastest).  Subdomains are the Cartesian products of per-axis edge lists;
+ * subdomain l = ix + Nx*(iy + Ny*iz).  The lower-indexed side of every
+ * interface is the side with the lower coordinate, so n_hat is the +axis.
+ *
+ * Interface space V_H: on every interface normal to axis a, fine faces are
+ * grouped in patches of patch[a][0] x patch[a][1] faces along the two
+ * tangential axes taken in increasing axis order (0 = whole face), tiled from
+ * the lower corner, the last patch truncated.  Basis functions are numbered by
+ * normal axis, then lower subdomain, then patch (second tangential axis slow).
+ * Interface unknowns X = (pi^p_0..pi^p_{NV-1}, pi^u_0..pi^u_{NV-1}).
+ *
+ * Pointers: "device" pointers must be CUDA device (or managed) memory on the
+ * device that is current when the call is made; the library never frees
+ * caller memory.  The workspace `ws` (size from mrcm_query_workspace, 256-byte
+ * aligned) is owned by the caller and must stay the same buffer for all calls
+ * of one solve.  The handle owns only its host tables and a device copy of
+ * them, allocated on the first device call (which synchronises the stream
+ * once; make that call before any stream capture).
+ *
+ * Streams: every device call is asynchronous on `stream` (a cudaStream_t; NULL
+ * is the legacy default stream).  Calls on one handle must not overlap.
+ *
+ * Errors: every call returns an mrcm_status; mrcm_last_error() describes the
+ * last failure of a handle.  No call aborts, traps or falls back to the CPU.
+ */
+#ifndef MRCM_H
+#define MRCM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRCM_OK = 0,
+    MRCM_ERR_INVALID_ARG = 1,       /* bad config, pointer or size */
+    MRCM_ERR_CUDA = 2,              /* a CUDA runtime call failed */
+    MRCM_ERR_NOT_SPD = 3,           /* a local block pivot was not positive */
+    MRCM_ERR_NO_CONVERGENCE = 4,    /* iterative refinement did not reach its tolerance */
+    MRCM_ERR_SINGULAR_INTERFACE = 5,/* zero pivot in the interface factorisation */
+    MRCM_ERR_TIMEOUT = 6,           /* a bounded device wait gave up */
+    MRCM_ERR_OOM = 7,               /* workspace too small */
+    MRCM_ERR_NOT_IMPLEMENTED = 8,   /* option not supported by this build */
+    MRCM_ERR_STATE = 9              /* calls made out of order */
+} mrcm_status;
+
+enum { MRCM_BETA_CONST = 0, MRCM_BETA_ALPHA_H_OVER_K = 1 };
+enum { MRCM_BC_NOFLOW = 0, MRCM_BC_DIRICHLET = 1 };
+enum {
+    MRCM_FP64 = 0,          /* local factor and solves in FP64 */
+    MRCM_FP32_IR = 1,       /* FP32 factor/solves + FP64 iterative refinement */
+    MRCM_TF32_IR = 2,       /* tensor-core TF32 solves + FP64 iterative refinement */
+    MRCM_LEARNED_PCG = 3    /* learned warm start + PCG (reserved) */
+};
+
+/* Problem description (Sec. "Domain decomposition and Darcy solvers").
+ *  nx, ny, nz         cells per axis (>= 1)
+ *  hx, hy, hz         cell sizes (> 0)
+ *  n_cuts[a], cuts[a] per-axis subdomain edge list (host pointer, n_cuts[a]
+ *                     positive ints summing to the axis' cell count); read
+ *                     during mrcm_setup only
+ *  patch[a][0..1]     patch size in faces on faces normal to axis a, along
+ *                     the first/second tangential axis (0 = whole face)
+ *  beta_mode          MRCM_BETA_CONST (beta = beta_const) or
+ *                     MRCM_BETA_ALPHA_H_OVER_K (Eq. Robin_par: beta = alpha *
+ *                     H_a / K_a with H_a the subdomain edge along the normal
+ *                     and K_a the normal permeability of the adjacent cell of
+ *                     the side being solved)
+ *  bc_type[a][side]   wall condition on the low (side 0) / high (side 1) wall
+ *                     normal to axis a: MRCM_BC_NOFLOW or MRCM_BC_DIRICHLET
+ *  bc_value[a][side]  Dirichlet pressure of that wall
+ *  precision          MRCM_FP64 / MRCM_FP32_IR / MRCM_TF32_IR
+ *  ir_max_sweeps      refinement sweeps after the first solve (mixed modes)
+ *  ir_tol             per-column stop: ||r||_2 <= ir_tol * ||b||_2
+ *  wave_bytes         reserved (memory budget for streamed waves); 0
+ *  tune_cache         reserved (autotuner cache path); may be NULL        */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int n_cuts[3];
+    const int* cuts[3];
+    int patch[3][2];
+    int beta_mode;
+    double alpha, beta_const;
+    int bc_type[3][2];
+    double bc_value[3][2];
+    int precision;
+    int ir_max_sweeps;
+    double ir_tol;
+    size_t wave_bytes;
+    const char* tune_cache;
+} mrcm_config;
+
+/* Sizes derived by mrcm_setup (host-side; no GPU needed). */
+typedef struct {
+    long long n_cells;          /* nx*ny*nz */
+    int n_sub;                  /* subdomains */
+    int n_basis;                /* NV, basis functions of V_H */
+    long long n_faces;          /* Robin faces counted once per side */
+    int max_rhs;                /* max over l of m_l = 2|I^l| + 1 */
+    long long total_rhs;        /* sum over l of m_l */
+    long long nnz_interface;    /* nonzeros of A^int in the CSR pattern */
+    int n_fronts;               /* internal nodes of the interface elimination tree */
+    int max_front;              /* largest dense front */
+    double front_flops;         /* flops of the interface factorisation */
+    double local_factor_flops;  /* flops of all local block factorisations */
+    double local_solve_flops;   /* flops of one solve sweep over all MBF columns */
+    int max_block;              /* largest slab block size b */
+} mrcm_sizes;
+
+typedef struct mrcm_handle mrcm_handle;
+
+/* Validate `cfg`, build the decomposition, interface-space, face and
+ * elimination-tree tables on the host.  Returns INVALID_ARG for inconsistent
+ * edge lists, non-positive sizes, unsupported block sizes, or a problem whose
+ * pressure is undetermined (one subdomain and no Dirichlet wall).  On success
+ * *out owns the tables; release with mrcm_destroy.  No device work. */
+mrcm_status mrcm_setup(const mrcm_config* cfg, mrcm_handle** out);
+
+/* Workspace bytes for one solve and the interface unknown count 2*NV. */
+mrcm_status mrcm_query_workspace(const mrcm_handle* h, size_t* ws_bytes, size_t* n_interface_unknowns);
+
+/* Derived sizes (see mrcm_sizes). */
+mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* out);
+
+/* Basis function i of V_H: normal axis, lower/upper subdomain, fine faces. */
+mrcm_status mrcm_query_basis(const mrcm_handle* h, int i, int* axis, int* sub_lo, int* sub_hi, int* n_faces);
+
+/* Assemble every local matrix A^H_l from K and factor it.
+ *  K   device, FP64 [3][nz][ny][nx] (Kxx, Kyy, Kzz), all entries > 0 and finite
+ *  ws  device workspace, ws_bytes >= mrcm_query_workspace
+ * The local matrices are built in FP64 (Eq. aijk with harmonic means; Robin
+ * faces with T_R = A_f / (h_n/(2K_n) + beta)); the block factor is kept in
+ * FP64 or FP32 by cfg.precision.  Non-positive pivots are reported as
+ * MRCM_ERR_NOT_SPD by the next synchronising call (mrcm_solve_mbf's status
+ * read-back) rather than here. */
+mrcm_status mrcm_factor_local(mrcm_handle* h, const double* K, void* ws, size_t ws_bytes, void* stream);
+
+/* Solve all MBF and particular right-hand sides of every subdomain (FP64, or
+ * low precision + FP64 iterative refinement) and reduce the flux traces to
+ * the per-subdomain interface blocks.
+ *  f   device, FP64 [nz][ny][nx] source density (div u = f) */
+mrcm_status mrcm_solve_mbf(mrcm_handle* h, const double* f, void* ws, void* stream);
+
+/* Gather the per-subdomain blocks into A^int (CSR, FP64) and b^int, then
+ * factor the interface system: J A^int (J = diag(I, -I)) is symmetric
+ * quasi-definite, so it is scaled symmetrically and factored by a nested-
+ * dissection multifrontal LDL^T without pivoting (FP64).  When no wall is
+ * Dirichlet the pressure constant is removed by adding -|A_00| e_0 e_0^T,
+ * which yields the solution with pi^p_0 = 0.  A zero pivot is reported as
+ * MRCM_ERR_SINGULAR_INTERFACE by mrcm_read_status. */
+mrcm_status mrcm_assemble_interface(mrcm_handle* h, void* ws, void* stream);
+
+/* Solve the interface system with the factor of mrcm_assemble_interface and
+ * two FP64 iterative-refinement steps (CSR residuals).
+ *  X   device, FP64 [2*NV], output */
+mrcm_status mrcm_solve_interface(mrcm_handle* h, double* X, void* ws, void* stream);
+
+/* Reconstruct p and u from the MBFs and X (reconstruction option 1).
+ *  X      device FP64 [2*NV] (input)
+ *  p      device FP64 [nz][ny][nx] (output); shifted to zero mean when no wall
+ *         is Dirichlet
+ *  u      device FP64 [6][nz][ny][nx] (output): +axis velocity on the
+ *         x-low, x-high, y-low, y-high, z-low, z-high face of each cell, as
+ *         seen from the cell's own subdomain (two values on Gamma faces)
+ *  mass_residual_max  device FP64 [1] (output): max over cells of
+ *         |sum of outward fluxes - f V|; may be NULL */
+mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double* u,
+                             double* mass_residual_max, void* ws, void* stream);
+
+/* Device-side status of the last solve, read back synchronously: number of
+ * non-positive local pivots, unconverged refinement columns, interface zero
+ * pivots and the refinement sweeps used. */
+mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconverged,
+                             int* interface_zero_pivots, int* sweeps_used);
+
+/* Copy device-resident intermediate results for inspection (device -> host,
+ * synchronous).  what: 0 = A^int CSR values (nnz_interface doubles), 1 = b^int
+ * (2*NV doubles), 2 = CSR row pointers (2*NV+1 ints), 3 = CSR column indices
+ * (nnz ints), 4 = MBF columns of subdomain `sub` (m_l x N_l doubles, column
+ * k over the subdomain's cells in global-lexicographic order). */
+mrcm_status mrcm_export(mrcm_handle* h, void* ws, int what, int sub, void* host_dst, size_t bytes);
+
+/* Per-kernel timing.  enable != 0 records a CUDA event pair on the launching
+ * stream around every kernel the library launches from now on (and clears
+ * earlier records); enable == 0 stops recording.  Launches are counted
+ * whether or not recording is on. */
+mrcm_status mrcm_profile(mrcm_handle* h, int enable);
+
+/* Synchronise on the last recorded event and write one line per kernel,
+ * "name launches total_ms\n", into buf (host, len bytes, NUL-terminated);
+ * *launches (may be NULL) receives the launch count.  Clears the records and
+ * the count.  INVALID_ARG if buf is too small (the text is truncated). */
+mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long* launches);
+
+/* Release the handle and its device tables (not the caller's buffers). */
+void mrcm_destroy(mrcm_handle* h);
+
+/* Message of the handle's last failure; with h == NULL, the message of the
+ * last failed mrcm_setup on the calling thread. */
+const char* mrcm_last_error(const mrcm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCM_H */

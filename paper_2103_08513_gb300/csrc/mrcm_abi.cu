@@ -1,0 +1,343 @@
+// extern "C" entry points of libmrcm (declared in include/mrcm.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mrcm_internal.h"
+
+using mrcm::Tables;
+
+namespace {
+
+thread_local std::string g_setup_err;   // message of the last failed mrcm_setup on this thread
+
+mrcm_status fail(mrcm_handle* h, mrcm_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+mrcm_status cuda_fail(mrcm_handle* h, cudaError_t e, const char* where) {
+    return fail(h, MRCM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_device(mrcm::DeviceTables& d) {
+    void* ptrs[] = {d.subs, d.faces, d.Ilist, d.rowptr, d.colidx, d.src_lo, d.src_hi, d.rhs_src_lo,
+                    d.rhs_src_hi, d.fronts, d.front_maps, d.front_dofs, d.level_ids};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    d = mrcm::DeviceTables();
+}
+
+mrcm_status ensure_device(mrcm_handle* h, void* stream) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+    if (h->d.ready) {
+        if (dev != h->d.device) return fail(h, MRCM_ERR_STATE, "handle was set up on another device");
+        return MRCM_OK;
+    }
+    // make sure nothing queued on the caller's stream still reads the tables we replace
+    if (stream) cudaStreamSynchronize((cudaStream_t)stream);
+    const Tables& t = h->t;
+    mrcm::DeviceTables& d = h->d;
+    std::vector<int> lvl;
+    d.level_off.assign(t.levels.size() + 1, 0);
+    for (size_t k = 0; k < t.levels.size(); ++k) {
+        d.level_off[k] = (int)lvl.size();
+        lvl.insert(lvl.end(), t.levels[k].begin(), t.levels[k].end());
+    }
+    d.level_off[t.levels.size()] = (int)lvl.size();
+#define UP(dst, src) do { e = upload(&d.dst, src); if (e != cudaSuccess) { free_device(d); return cuda_fail(h, e, "table upload"); } } while (0)
+    UP(subs, t.subs);
+    UP(faces, t.faces);
+    UP(Ilist, t.Ilist);
+    UP(rowptr, t.rowptr);
+    UP(colidx, t.colidx);
+    UP(src_lo, t.src_lo);
+    UP(src_hi, t.src_hi);
+    UP(rhs_src_lo, t.rhs_src_lo);
+    UP(rhs_src_hi, t.rhs_src_hi);
+    UP(fronts, t.fronts);
+    UP(front_maps, t.front_maps);
+    UP(front_dofs, t.front_dofs);
+    UP(level_ids, lvl);
+#undef UP
+    d.device = dev;
+    d.ready = true;
+    return MRCM_OK;
+}
+
+mrcm_status check_ws(mrcm_handle* h, const void* ws) {
+    if (!ws) return fail(h, MRCM_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)ws & 255u) != 0) return fail(h, MRCM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return MRCM_OK;
+}
+
+mrcm_status after_launch(mrcm_handle* h, int rc, const char* where) {
+    if (rc != 0) return cuda_fail(h, (cudaError_t)rc, where);
+    return MRCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrcm_status mrcm_setup(const mrcm_config* cfg, mrcm_handle** out) {
+    if (!out) return MRCM_ERR_INVALID_ARG;
+    *out = nullptr;
+    mrcm_handle* h = new (std::nothrow) mrcm_handle();
+    if (!h) return MRCM_ERR_OOM;
+    mrcm_status st = mrcm::build_tables(cfg, h->t, h->err);
+    const Tables& t = h->t;
+    if (st == MRCM_OK) {
+        for (const auto& s : t.subs) {
+            if (s.nI > mrcm::kMaxI) { st = MRCM_ERR_NOT_IMPLEMENTED; h->err = "too many basis functions on one subdomain"; break; }
+            if (s.N > 4096) { st = MRCM_ERR_NOT_IMPLEMENTED; h->err = "subdomain larger than 4096 cells"; break; }
+        }
+    }
+    size_t solve_smem = sizeof(double) * ((size_t)t.max_b * t.max_b + 2 * (size_t)t.max_b * t.max_m);
+    if (st == MRCM_OK && solve_smem > 227 * 1024) {
+        st = MRCM_ERR_NOT_IMPLEMENTED;
+        h->err = "slab block and right-hand-side count exceed shared memory";
+    }
+    if (st != MRCM_OK) {
+        g_setup_err = h->err;
+        delete h;
+        return st;
+    }
+    mrcm::compute_layout(h->t, h->lay);
+    *out = h;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_query_workspace(const mrcm_handle* h, size_t* ws_bytes, size_t* n_iface) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (ws_bytes) *ws_bytes = h->lay.total;
+    if (n_iface) *n_iface = (size_t)2 * h->t.NV;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
+    if (!h || !o) return MRCM_ERR_INVALID_ARG;
+    const Tables& t = h->t;
+    std::memset(o, 0, sizeof(*o));
+    o->n_cells = t.n_cells;
+    o->n_sub = (int)t.subs.size();
+    o->n_basis = t.NV;
+    o->n_faces = (long long)t.faces.size();
+    o->max_rhs = t.max_m;
+    o->total_rhs = t.total_rhs;
+    o->nnz_interface = (long long)t.colidx.size();
+    o->n_fronts = (int)t.fronts.size();
+    o->max_front = t.max_front;
+    o->front_flops = t.front_flops;
+    o->local_factor_flops = t.local_factor_flops;
+    o->local_solve_flops = t.local_solve_flops;
+    o->max_block = t.max_b;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_query_basis(const mrcm_handle* h, int i, int* axis, int* lo, int* hi, int* nf) {
+    if (!h || i < 0 || i >= h->t.NV) return MRCM_ERR_INVALID_ARG;
+    if (axis) *axis = h->t.b_axis[i];
+    if (lo) *lo = h->t.b_lo[i];
+    if (hi) *hi = h->t.b_hi[i];
+    if (nf) *nf = h->t.b_nfaces[i];
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_factor_local(mrcm_handle* h, const double* K, void* ws, size_t ws_bytes, void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (!K) return fail(h, MRCM_ERR_INVALID_ARG, "K is NULL");
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (ws_bytes < h->lay.total) return fail(h, MRCM_ERR_OOM, "workspace smaller than mrcm_query_workspace");
+    if ((st = ensure_device(h, stream)) != MRCM_OK) return st;
+    h->K = K;
+    int rc = mrcm::launch_factor(h->t, h->d, h->lay, (char*)ws, K, h->t.cfg.precision, stream, h->prof);
+    if ((st = after_launch(h, rc, "mrcm_factor_local")) != MRCM_OK) return st;
+    h->stage = 1;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_solve_mbf(mrcm_handle* h, const double* f, void* ws, void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (!f) return fail(h, MRCM_ERR_INVALID_ARG, "f is NULL");
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
+    h->f = f;
+    int sweeps = h->t.cfg.precision == MRCM_FP64 ? 0 : h->t.cfg.ir_max_sweeps;
+    double tol = h->t.cfg.ir_tol > 0 ? h->t.cfg.ir_tol : 1e-14;
+    int rc = mrcm::launch_solve_mbf(h->t, h->d, h->lay, (char*)ws, f, h->t.cfg.precision, sweeps, tol, stream, h->prof);
+    if ((st = after_launch(h, rc, "mrcm_solve_mbf")) != MRCM_OK) return st;
+    h->stage = 2;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_assemble_interface(mrcm_handle* h, void* ws, void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (h->stage < 2) return fail(h, MRCM_ERR_STATE, "mrcm_solve_mbf must run first");
+    int rc = mrcm::launch_assemble_interface(h->t, h->d, h->lay, (char*)ws, stream, h->prof);
+    if ((st = after_launch(h, rc, "mrcm_assemble_interface")) != MRCM_OK) return st;
+    h->stage = 3;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_solve_interface(mrcm_handle* h, double* X, void* ws, void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (!X && h->t.NV > 0) return fail(h, MRCM_ERR_INVALID_ARG, "X is NULL");
+    if (h->stage < 3) return fail(h, MRCM_ERR_STATE, "mrcm_assemble_interface must run first");
+    int rc = mrcm::launch_solve_interface(h->t, h->d, h->lay, (char*)ws, X, stream, h->prof);
+    if ((st = after_launch(h, rc, "mrcm_solve_interface")) != MRCM_OK) return st;
+    h->stage = 4;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double* u, double* mres, void* ws,
+                             void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (!p || !u || (!X && h->t.NV > 0)) return fail(h, MRCM_ERR_INVALID_ARG, "X, p and u must be non-NULL");
+    if (h->stage < 4) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must run first");
+    int rc = mrcm::launch_reconstruct(h->t, h->d, h->lay, (char*)ws, X, p, u, mres, h->K, h->f, stream, h->prof);
+    return after_launch(h, rc, "mrcm_reconstruct");
+}
+
+mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconverged, int* zero_piv,
+                             int* sweeps) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    int w[mrcm::ST_COUNT];
+    cudaError_t e = cudaMemcpy(w, (char*)ws + h->lay.status, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_read_status");
+    if (not_spd) *not_spd = w[mrcm::ST_NOT_SPD];
+    if (unconverged) *unconverged = w[mrcm::ST_UNCONVERGED];
+    if (zero_piv) *zero_piv = w[mrcm::ST_ZERO_PIVOT];
+    if (sweeps) *sweeps = w[mrcm::ST_SWEEPS];
+    if (w[mrcm::ST_NOT_SPD]) return fail(h, MRCM_ERR_NOT_SPD, "non-positive local block pivot");
+    if (w[mrcm::ST_ZERO_PIVOT]) return fail(h, MRCM_ERR_SINGULAR_INTERFACE, "zero pivot in the interface factorisation");
+    if (w[mrcm::ST_UNCONVERGED]) return fail(h, MRCM_ERR_NO_CONVERGENCE, "iterative refinement did not converge");
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_export(mrcm_handle* h, void* ws, int what, int sub, void* dst, size_t bytes) {
+    if (!h || !dst) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    const Tables& t = h->t;
+    const char* w = (const char*)ws;
+    cudaError_t e = cudaSuccess;
+    size_t need = 0;
+    const void* src = nullptr;
+    switch (what) {
+        case 0: need = t.colidx.size() * sizeof(double); src = w + h->lay.csr_val; break;
+        case 1: need = (size_t)2 * t.NV * sizeof(double); src = w + h->lay.b_int; break;
+        case 2:
+            need = t.rowptr.size() * sizeof(int);
+            if (bytes < need) return fail(h, MRCM_ERR_INVALID_ARG, "export buffer too small");
+            std::memcpy(dst, t.rowptr.data(), need);
+            return MRCM_OK;
+        case 3:
+            need = t.colidx.size() * sizeof(int);
+            if (bytes < need) return fail(h, MRCM_ERR_INVALID_ARG, "export buffer too small");
+            std::memcpy(dst, t.colidx.data(), need);
+            return MRCM_OK;
+        case 4: {
+            if (sub < 0 || sub >= (int)t.subs.size()) return fail(h, MRCM_ERR_INVALID_ARG, "bad subdomain");
+            const mrcm::SubInfo& s = t.subs[sub];
+            need = (size_t)s.m * s.N * sizeof(double);
+            if (bytes < need) return fail(h, MRCM_ERR_INVALID_ARG, "export buffer too small");
+            std::vector<double> tmp((size_t)s.m * s.N);
+            e = cudaMemcpy(tmp.data(), w + h->lay.X + s.x_off * sizeof(double), need, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_export");
+            // slab order -> lexicographic order (x fastest) inside the subdomain box
+            double* out = (double*)dst;
+            for (int c = 0; c < s.N; ++c) {
+                int sl = c / s.b, r = c % s.b, v = r / s.su, uu = r % s.su;
+                int lc[3];
+                lc[s.sa] = sl; lc[s.ua] = uu; lc[s.va] = v;
+                int lex = lc[0] + s.sz[0] * (lc[1] + s.sz[1] * lc[2]);
+                for (int j = 0; j < s.m; ++j) out[(size_t)j * s.N + lex] = tmp[(size_t)j * s.N + c];
+            }
+            return MRCM_OK;
+        }
+        default: return fail(h, MRCM_ERR_INVALID_ARG, "unknown export");
+    }
+    if (bytes < need) return fail(h, MRCM_ERR_INVALID_ARG, "export buffer too small");
+    e = cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_export");
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_profile(mrcm_handle* h, int enable) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long* launches) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm::Prof& P = h->prof;
+    if (launches) *launches = P.launches;
+    std::vector<double> ms(P.names.size(), 0.0);
+    std::vector<long long> cnt(P.names.size(), 0);
+    if (P.used) {
+        cudaError_t e = cudaEventSynchronize(P.pool[P.used - 1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_profile_report");
+    }
+    for (size_t i = 0; i < P.kid.size(); ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, P.pool[2 * i], P.pool[2 * i + 1]) == cudaSuccess) {
+            ms[P.kid[i]] += t;
+            cnt[P.kid[i]] += 1;
+        }
+    }
+    std::string out;
+    for (size_t k = 0; k < P.names.size(); ++k) {
+        if (!cnt[k]) continue;
+        char line[256];
+        snprintf(line, sizeof(line), "%s %lld %.6f\n", P.names[k].c_str(), cnt[k], ms[k]);
+        out += line;
+    }
+    if (buf && len) {
+        size_t n = std::min(len - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+        if (out.size() >= len) return fail(h, MRCM_ERR_INVALID_ARG, "profile buffer too small");
+    }
+    P.reset();
+    return MRCM_OK;
+}
+
+void mrcm_destroy(mrcm_handle* h) {
+    if (!h) return;
+    h->prof.release();
+    free_device(h->d);
+    delete h;
+}
+
+const char* mrcm_last_error(const mrcm_handle* h) {
+    if (!h) return g_setup_err.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Internal tables shared by the host setup and the CUDA kernels of libmrcm.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mrcm.h"
+#include "mrcm_prof.h"
+
+namespace mrcm {
+
+constexpr int kMaxBlock = 128;      // largest slab block b handled in shared memory
+constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
+
+// One subdomain.  Local cells are numbered slab-major: the slab axis `sa` is
+// the subdomain's longest axis; inside a slab the two other axes (ua < va)
+// run u fastest.  local = s*b + u + su*v.  With this order the local TPFA
+// matrix is block tridiagonal with b x b diagonal blocks (5-point stencils)
+// and diagonal coupling blocks between consecutive slabs.
+struct SubInfo {
+    int o[3];          // origin (cells)
+    int sz[3];         // extents
+    int sa, ua, va;    // slab axis, fast and slow in-slab axes
+    int su, sv, b, ns, N;
+    int nI;            // |I^l|
+    int m;             // 2|I^l| + 1 right-hand sides
+    int face_off, nface;
+    int I_off;         // offset into the I^l lists
+    int el_dim;        // 2|I^l|
+    long long cell_off;   // offset into per-cell arrays
+    long long x_off;      // offset (doubles) into the MBF array [m][N]
+    long long w_off;      // offset (elements) into the block factor array
+    long long el_off;     // offset (doubles) into element matrices
+    int elb_off;          // offset (doubles) into element right-hand sides
+    int pad;
+};
+
+// One Robin face of a subdomain (a fine face of Gamma seen from one side).
+struct FaceInfo {
+    int cell;          // local cell (slab order)
+    int col;           // position of its basis in I^l
+    int8_t axis;       // normal axis
+    int8_t s;          // +1 lower side, -1 upper side
+    int16_t pad;
+};
+
+// One internal node of the interface elimination tree (a dense front).
+struct FrontInfo {
+    int ne, nb, n;          // eliminated dofs, boundary dofs, n = ne + nb
+    int nchild;             // 2
+    long long f_off;        // offset (doubles) of the n x n front (row major)
+    int r_off;              // offset (doubles) of the front right-hand side
+    int child[2];           // child front index, or -(1 + element) for a leaf
+    int map_off[2];         // offset (ints) of the child -> front position maps
+    int map_len[2];
+    int e_dof_off;          // offset (ints) into the global dof list of E then B
+    int pin_row;            // front row of pi^p_0 when it is regularised, or -1
+    int height;
+    int parent;
+};
+
+struct Tables {
+    // configuration
+    mrcm_config cfg;
+    std::vector<int> cuts[3];
+    int N[3];                      // subdomains per axis
+    std::vector<int> starts[3];
+    bool has_dirichlet = false;
+
+    // subdomains and faces
+    std::vector<SubInfo> subs;
+    std::vector<FaceInfo> faces;
+    std::vector<int> Ilist;        // concatenated sorted I^l (global basis ids)
+    long long n_cells = 0, total_x = 0, total_w = 0, total_el = 0;
+    int total_elb = 0;
+    int max_m = 0, max_b = 0, max_el = 0, max_N = 0;
+    long long total_rhs = 0;
+
+    // bases
+    int NV = 0;
+    std::vector<int> b_axis, b_lo, b_hi, b_nfaces;
+
+    // interface CSR with two-sided sources (element entry offsets or -1)
+    std::vector<int> rowptr, colidx;
+    std::vector<long long> src_lo, src_hi;
+    std::vector<int> rhs_src_lo, rhs_src_hi;   // element rhs offsets per global dof
+
+    // elimination tree
+    std::vector<FrontInfo> fronts;
+    std::vector<int> front_maps;               // child -> front position maps
+    std::vector<int> front_dofs;               // global dof of each front row
+    std::vector<std::vector<int>> levels;      // fronts grouped by height
+    long long total_front = 0;
+    int total_frhs = 0;
+    int max_front = 0;
+    double front_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
+    int root = -1;
+    int pin_front = -1;
+};
+
+// Workspace layout (byte offsets into the caller's workspace).
+struct Layout {
+    size_t coef, scale, rhs_part, face_tr, face_beta, W, X, R, colnorm, conv;
+    size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, xres, xtmp, psum, status;
+    size_t total;
+};
+
+struct DeviceTables {
+    SubInfo* subs = nullptr;
+    FaceInfo* faces = nullptr;
+    int* Ilist = nullptr;
+    int* rowptr = nullptr;
+    int* colidx = nullptr;
+    long long* src_lo = nullptr;
+    long long* src_hi = nullptr;
+    int* rhs_src_lo = nullptr;
+    int* rhs_src_hi = nullptr;
+    FrontInfo* fronts = nullptr;
+    int* front_maps = nullptr;
+    int* front_dofs = nullptr;
+    int* level_ids = nullptr;                  // fronts of all levels, concatenated
+    std::vector<int> level_off;                // host: offsets of each level in level_ids
+    int device = -1;
+    bool ready = false;
+};
+
+// Device status words at Layout::status.
+enum StatusWord { ST_NOT_SPD = 0, ST_UNCONVERGED = 1, ST_ZERO_PIVOT = 2, ST_SWEEPS = 3,
+                  ST_TIMEOUT = 4, ST_COUNT = 8 };
+
+}  // namespace mrcm
+
+struct mrcm_handle {
+    mrcm::Tables t;
+    mrcm::Layout lay;
+    mrcm::DeviceTables d;
+    mrcm::Prof prof;
+    std::string err;
+    int stage = 0;     // 0 setup, 1 factored, 2 mbf, 3 assembled, 4 interface solved
+    const double* K = nullptr;   // caller's K (kept for reconstruction)
+    const double* f = nullptr;   // caller's f
+};
+
+// Host setup (mrcm_setup.cpp)
+namespace mrcm {
+mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err);
+void compute_layout(const Tables& t, Layout& lay);
+}
+
+// Kernel launchers (CUDA translation units).  Each returns cudaError_t as int.
+namespace mrcm {
+int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
+                  const double* K, int precision, void* stream, Prof& P);
+int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
+                     const double* f, int precision, int sweeps, double tol, void* stream, Prof& P);
+int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
+                              void* stream, Prof& P);
+int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
+                           double* X, void* stream, Prof& P);
+int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
+                       const double* X, double* p, double* u, double* mres, const double* K,
+                       const double* f, void* stream, Prof& P);
+}

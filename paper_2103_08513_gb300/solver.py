@@ -1,0 +1,190 @@
+"""Python binding of libmrcm: argument marshalling around the C ABI.
+
+PyTorch provides device memory and streams; every step of the solve runs in
+the library's CUDA kernels.  Method names match the C entry points
+(include/mrcm.h) without the ``mrcm_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class MRCM:
+    """One MRCM problem (grid, decomposition, interface space) bound to one GPU.
+
+    Parameters follow the mrcm_config struct: ``n = (nx, ny, nz)``,
+    ``h = (hx, hy, hz)``, ``edges`` = per-axis subdomain edge lists,
+    ``patch = ((p1, p2) for x-, y-, z-normal faces)`` (0 = whole face).
+    """
+
+    def __init__(self, n, edges, patch=((0, 0),) * 3, h=(1.0, 1.0, 1.0), beta_mode=0, alpha=1.0,
+                 beta_const=1.0, bc_type=((0, 0),) * 3, bc_value=((0.0, 0.0),) * 3,
+                 precision="fp64", ir_max_sweeps=4, ir_tol=1e-14, device=None, allocate=True):
+        self.lib = L.load()
+        cfg = L.mrcm_config()
+        cfg.nx, cfg.ny, cfg.nz = (int(v) for v in n)
+        cfg.hx, cfg.hy, cfg.hz = (float(v) for v in h)
+        self._cuts = []
+        for a in range(3):
+            arr = (C.c_int * len(edges[a]))(*[int(e) for e in edges[a]])
+            self._cuts.append(arr)
+            cfg.n_cuts[a] = len(edges[a])
+            cfg.cuts[a] = C.cast(arr, C.POINTER(C.c_int))
+            cfg.patch[a][0], cfg.patch[a][1] = int(patch[a][0]), int(patch[a][1])
+            cfg.bc_type[a][0], cfg.bc_type[a][1] = int(bc_type[a][0]), int(bc_type[a][1])
+            cfg.bc_value[a][0], cfg.bc_value[a][1] = float(bc_value[a][0]), float(bc_value[a][1])
+        cfg.beta_mode = int(beta_mode)
+        cfg.alpha = float(alpha)
+        cfg.beta_const = float(beta_const)
+        cfg.precision = L.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.ir_max_sweeps = int(ir_max_sweeps)
+        cfg.ir_tol = float(ir_tol)
+        cfg.wave_bytes = 0
+        cfg.tune_cache = None
+        self.cfg = cfg
+        self.n = tuple(int(v) for v in n)
+        h_ = C.c_void_p()
+        L.check(self.lib.mrcm_setup(C.byref(cfg), C.byref(h_)))
+        self.handle = h_
+        wsb, nif = C.c_size_t(), C.c_size_t()
+        L.check(self.lib.mrcm_query_workspace(self.handle, C.byref(wsb), C.byref(nif)), self.handle)
+        self.ws_bytes = int(wsb.value)
+        self.n_interface = int(nif.value)
+        sz = L.mrcm_sizes()
+        L.check(self.lib.mrcm_query_sizes(self.handle, C.byref(sz)), self.handle)
+        self.sizes = {k: getattr(sz, k) for k, _ in L.mrcm_sizes._fields_}
+        self.device = torch.device(device if device is not None else "cuda")
+        self.ws = None
+        if allocate:
+            self.allocate()
+
+    # ------------------------------------------------------------------ memory
+    def allocate(self):
+        """Allocate the workspace (caller-owned device memory, 256-byte aligned)."""
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._ws_off = (-base) % 256
+        return self.ws
+
+    @property
+    def ws_ptr(self):
+        return C.c_void_p(self.ws.data_ptr() + self._ws_off)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                self.lib.mrcm_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ steps
+    def factor_local(self, K, stream=None):
+        assert K.dtype == torch.float64 and K.is_cuda and K.is_contiguous()
+        self._K = K
+        L.check(self.lib.mrcm_factor_local(self.handle, _ptr(K), self.ws_ptr, C.c_size_t(self.ws_bytes),
+                                           _stream(stream)), self.handle)
+
+    def solve_mbf(self, f, stream=None):
+        assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous()
+        self._f = f
+        L.check(self.lib.mrcm_solve_mbf(self.handle, _ptr(f), self.ws_ptr, _stream(stream)), self.handle)
+
+    def assemble_interface(self, stream=None):
+        L.check(self.lib.mrcm_assemble_interface(self.handle, self.ws_ptr, _stream(stream)), self.handle)
+
+    def solve_interface(self, X=None, stream=None):
+        if X is None:
+            X = torch.empty(max(self.n_interface, 1), dtype=torch.float64, device=self.device)
+        L.check(self.lib.mrcm_solve_interface(self.handle, _ptr(X), self.ws_ptr, _stream(stream)), self.handle)
+        return X
+
+    def reconstruct(self, X, p=None, u=None, mres=None, stream=None):
+        nx, ny, nz = self.n
+        if p is None:
+            p = torch.empty((nz, ny, nx), dtype=torch.float64, device=self.device)
+        if u is None:
+            u = torch.empty((6, nz, ny, nx), dtype=torch.float64, device=self.device)
+        if mres is None:
+            mres = torch.empty(1, dtype=torch.float64, device=self.device)
+        L.check(self.lib.mrcm_reconstruct(self.handle, _ptr(X), _ptr(p), _ptr(u), _ptr(mres), self.ws_ptr,
+                                          _stream(stream)), self.handle)
+        return p, u, mres
+
+    def solve(self, K, f, out=None, stream=None):
+        """All five device steps of one MRCM pressure solve; returns (p, u, X, mres)."""
+        self.factor_local(K, stream)
+        self.solve_mbf(f, stream)
+        self.assemble_interface(stream)
+        if out is None:
+            X = self.solve_interface(stream=stream)
+            p, u, mres = self.reconstruct(X, stream=stream)
+        else:
+            X, p, u, mres = out
+            self.solve_interface(X, stream=stream)
+            self.reconstruct(X, p, u, mres, stream=stream)
+        return p, u, X, mres
+
+    # ------------------------------------------------------------------ profiling
+    def profile(self, enable=True):
+        """Start (or stop) per-kernel CUDA-event timing inside the library."""
+        L.check(self.lib.mrcm_profile(self.handle, int(bool(enable))), self.handle)
+
+    def profile_report(self):
+        """{kernel: (launches, total_ms)} since profile() and the launch count; clears both."""
+        buf = C.create_string_buffer(1 << 16)
+        n = C.c_longlong()
+        L.check(self.lib.mrcm_profile_report(self.handle, buf, C.c_size_t(len(buf)), C.byref(n)), self.handle)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split()
+            out[name] = (int(cnt), float(ms))
+        return out, int(n.value)
+
+    # ------------------------------------------------------------------ inspection
+    def read_status(self):
+        v = [C.c_int() for _ in range(4)]
+        code = self.lib.mrcm_read_status(self.handle, self.ws_ptr, *[C.byref(x) for x in v])
+        return code, {"not_spd": v[0].value, "unconverged": v[1].value, "interface_zero_pivots": v[2].value,
+                      "sweeps": v[3].value}
+
+    def basis(self, i):
+        v = [C.c_int() for _ in range(4)]
+        L.check(self.lib.mrcm_query_basis(self.handle, int(i), *[C.byref(x) for x in v]), self.handle)
+        return tuple(x.value for x in v)
+
+    def export(self, what, sub=0, count=None, dtype="float64"):
+        import numpy as np
+        if count is None:
+            raise ValueError("count required")
+        out = np.empty(count, dtype=dtype)
+        L.check(self.lib.mrcm_export(self.handle, self.ws_ptr, int(what), int(sub),
+                                     out.ctypes.data_as(C.c_void_p), C.c_size_t(out.nbytes)), self.handle)
+        return out
+
+    def interface_csr(self):
+        """(rowptr, colidx, values, b) of A^int after mrcm_assemble_interface."""
+        nd = self.n_interface
+        nnz = int(self.sizes["nnz_interface"])
+        rowptr = self.export(2, count=nd + 1, dtype="int32")
+        colidx = self.export(3, count=nnz, dtype="int32")
+        val = self.export(0, count=nnz)
+        b = self.export(1, count=nd)
+        return rowptr, colidx, val, b
+
+    def mbf_block(self, sub, m, n_cells):
+        """MBF columns of one subdomain, (m, n_cells) with cells in box-lexicographic order."""
+        return self.export(4, sub=sub, count=m * n_cells).reshape(m, n_cells)

@@ -1,0 +1,142 @@
+"""Host-side checks of the C ABI (no GPU): exports, setup tables, errors.
+
+mrcm_setup builds every table on the host, so the decomposition, the
+interface space and the derived sizes can be compared bit-exactly with the
+oracle's own enumeration without a GPU.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.problem import build_bases
+from synth.configs import BETA_ALPHA_H_OVER_K, small, workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_08513_gb300 import build
+    from paper_2103_08513_gb300 import _lib
+    build()
+    return _lib.load()
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "mrcm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrcm_[a-z_]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert "mrcm_setup" in syms and "mrcm_reconstruct" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    from paper_2103_08513_gb300._lib import SIGNATURES
+    assert set(SIGNATURES) == set(syms)
+
+
+def _cfg(w, precision=0):
+    from paper_2103_08513_gb300._lib import mrcm_config
+    cfg = mrcm_config()
+    cfg.nx, cfg.ny, cfg.nz = w.n
+    cfg.hx, cfg.hy, cfg.hz = w.h
+    keep = []
+    for a in range(3):
+        arr = (C.c_int * len(w.edges[a]))(*w.edges[a])
+        keep.append(arr)
+        cfg.n_cuts[a] = len(w.edges[a])
+        cfg.cuts[a] = C.cast(arr, C.POINTER(C.c_int))
+        cfg.patch[a][0], cfg.patch[a][1] = w.patch[a]
+    cfg.beta_mode = w.beta_mode
+    cfg.alpha = w.alpha
+    cfg.beta_const = w.beta_const
+    cfg.precision = precision
+    cfg.ir_max_sweeps = 4
+    cfg.ir_tol = 1e-14
+    return cfg, keep
+
+
+def _setup(lib, w):
+    cfg, keep = _cfg(w)
+    h = C.c_void_p()
+    rc = lib.mrcm_setup(C.byref(cfg), C.byref(h))
+    return rc, h
+
+
+WS = [
+    small(),
+    small(n=(9, 7, 5), edges=([4, 5], [2, 3, 2], [5]), patch=((2, 2), (3, 2), (2, 3))),
+    small(n=(6, 6, 6), edges=([3, 3], [3, 3], [2, 4]), patch=((0, 0), (2, 0), (0, 2)),
+          beta_mode=BETA_ALPHA_H_OVER_K),
+    small(n=(13, 11, 7), edges=([4, 4, 5], [3, 5, 3], [2, 5]), patch=((2, 3), (4, 1), (3, 3))),
+]
+
+
+@pytest.mark.parametrize("w", WS + ["c1"])
+def test_setup_tables_match_oracle(lib, w):
+    from paper_2103_08513_gb300._lib import mrcm_sizes
+    if isinstance(w, str):
+        w = workload(w)
+    nx, ny, nz = w.n
+    prob = oracle.from_workload(w, K=np.ones((3, nz, ny, nx)), f=np.zeros((nz, ny, nx)))
+    bases, sub_bases, _ = build_bases(prob)
+    rc, h = _setup(lib, w)
+    assert rc == 0, lib.mrcm_last_error(None)
+    try:
+        sz = mrcm_sizes()
+        assert lib.mrcm_query_sizes(h, C.byref(sz)) == 0
+        assert sz.n_basis == len(bases)
+        assert sz.n_sub == prob.nsub
+        assert sz.n_cells == prob.ncells
+        assert sz.max_rhs == max(2 * len(I) + 1 for I in sub_bases)
+        assert sz.total_rhs == sum(2 * len(I) + 1 for I in sub_bases)
+        assert sz.n_faces == 2 * sum(len(b.faces) for b in bases)
+        ax, lo, hi, nf = (C.c_int() for _ in range(4))
+        for i, b in enumerate(bases):
+            assert lib.mrcm_query_basis(h, i, C.byref(ax), C.byref(lo), C.byref(hi), C.byref(nf)) == 0
+            assert (ax.value, lo.value, hi.value, nf.value) == (b.axis, b.lo, b.hi, len(b.faces))
+    finally:
+        lib.mrcm_destroy(h)
+
+
+def test_c2_sizes(lib):
+    from paper_2103_08513_gb300._lib import mrcm_sizes
+    rc, h = _setup(lib, workload("c2"))
+    assert rc == 0
+    sz = mrcm_sizes()
+    lib.mrcm_query_sizes(h, C.byref(sz))
+    assert sz.n_sub == 2244 and sz.max_rhs == 33 and 2 * sz.n_basis == 32944
+    lib.mrcm_destroy(h)
+
+
+def test_setup_rejects_bad_configs(lib):
+    w = small()
+    cfg, keep = _cfg(w)
+    cfg.nx = 9          # edge list no longer sums to nx
+    h = C.c_void_p()
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
+    assert b"does not sum" in lib.mrcm_last_error(None)
+    cfg, keep = _cfg(small(n=(4, 4, 4), edges=([4], [4], [4])))
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1       # one subdomain, no-flow walls
+    cfg, keep = _cfg(w)
+    cfg.beta_const = -1.0
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
+    cfg, keep = _cfg(w)
+    cfg.precision = 3
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 8
+
+
+def test_device_calls_reject_bad_arguments_without_gpu(lib):
+    rc, h = _setup(lib, small())
+    assert rc == 0
+    # NULL pointers and misaligned workspaces are refused before any CUDA call
+    assert lib.mrcm_factor_local(h, None, None, 0, None) == 1
+    assert lib.mrcm_solve_mbf(h, C.c_void_p(256), C.c_void_p(256), None) == 9   # out of order
+    assert lib.mrcm_factor_local(h, C.c_void_p(256), C.c_void_p(257), 1 << 30, None) == 1
+    lib.mrcm_destroy(h)

@@ -1,0 +1,126 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: FP64 mode 1e-10 relative L2 on p, u and X; mixed mode (FP32
+block solves + FP64 iterative refinement) 1e-8.  Interface matrices compare
+entrywise at 1e-10 relative to the largest entry.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle.problem import DIRICHLET
+from synth.configs import BETA_ALPHA_H_OVER_K, small, workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from gpu_helpers import rel_l2, run_gpu  # noqa: E402
+
+CASES = {
+    "two_by_two": dict(),
+    "ragged": dict(n=(9, 7, 5), edges=([4, 5], [2, 3, 2], [5]), patch=((2, 2), (3, 2), (2, 3))),
+    "betaHK": dict(n=(6, 6, 6), edges=([3, 3], [3, 3], [2, 4]), patch=((0, 0), (2, 0), (0, 2)),
+                   beta_mode=BETA_ALPHA_H_OVER_K, alpha=0.7),
+    "aniso_h": dict(n=(8, 4, 4), edges=([2, 3, 3], [4], [2, 2]), patch=((1, 2), (1, 1), (3, 1)),
+                    beta_const=0.3, h=(0.5, 1.0, 2.0)),
+    "many_tiles": dict(n=(24, 20, 12), edges=([6, 6, 7, 5], [5, 5, 5, 5], [4, 4, 4]),
+                       patch=((3, 2), (2, 2), (3, 5)), sigma=2.0, lam=4.0),
+}
+
+
+def _oracle(w):
+    prob = oracle.from_workload(w)
+    return prob, oracle.solve_mrcm(prob)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_matches_oracle(name):
+    w = small(**CASES[name])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp64")
+    assert code == 0, st
+    assert rel_l2(X, r.X) < 1e-10
+    assert rel_l2(p, r.p) < 1e-10
+    assert rel_l2(u.ravel(), r.u.ravel()) < 1e-10
+    assert mres < 1e-11 * max(1.0, np.abs(prob.f).max())
+
+
+@pytest.mark.parametrize("name", ["two_by_two", "ragged", "many_tiles"])
+def test_interface_matrix_matches_oracle(name):
+    w = small(**CASES[name])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp64")
+    rowptr, colidx, val, b = s.interface_csr()
+    # A^int as assembled (the pressure constant is handled inside the solve)
+    A = sp.csr_matrix((val, colidx, rowptr), shape=r.A_int_raw.shape).toarray()
+    Ao = r.A_int_raw.toarray()
+    assert np.abs(A - Ao).max() <= 1e-10 * np.abs(Ao).max()
+    assert np.abs(b - r.b_int_raw).max() <= 1e-10 * max(np.abs(r.b_int_raw).max(), 1e-300)
+    # the structure the LDL^T relies on: J A symmetric
+    NV = A.shape[0] // 2
+    J = np.concatenate([np.ones(NV), -np.ones(NV)])
+    JA = J[:, None] * A
+    assert np.abs(JA - JA.T).max() <= 1e-10 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("name", ["ragged", "betaHK"])
+def test_mbf_columns_match_oracle(name):
+    w = small(**CASES[name])
+    prob, r = _oracle(w)
+    s, *_ = run_gpu(w, prob.K, prob.f, "fp64")
+    for l, (lp, Xl) in enumerate(zip(r.locals, r.mbfs)):
+        m = Xl.shape[1]
+        G = s.mbf_block(l, m, Xl.shape[0])
+        assert np.abs(G.T - Xl).max() <= 1e-10 * np.abs(Xl).max(), l
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_precision_matches_oracle(name):
+    w = small(**CASES[name])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp32_ir", ir_max_sweeps=8, ir_tol=1e-13)
+    assert st["not_spd"] == 0
+    assert rel_l2(p, r.p) < 1e-8
+    assert rel_l2(u.ravel(), r.u.ravel()) < 1e-8
+    assert rel_l2(X, r.X) < 1e-8
+
+
+def test_linear_pressure_dirichlet():
+    # homogeneous K, Dirichlet x walls, cuts normal to the gradient: MRCM is exact
+    nx, ny, nz = 12, 6, 4
+    # y-interfaces are parallel to grad p: their patches must be one face wide along x
+    w = small(n=(nx, ny, nz), edges=([3, 4, 5], [3, 3], [4]), patch=((0, 0), (1, 2), (0, 0)))
+    K = np.empty((3, nz, ny, nx)); K[0], K[1], K[2] = 1.5, 0.4, 0.2
+    f = np.zeros((nz, ny, nx))
+    bc = ((DIRICHLET, DIRICHLET), (0, 0), (0, 0))
+    bv = ((1.0, 0.0), (0.0, 0.0), (0.0, 0.0))
+    s, p, u, X, mres, code, st = run_gpu(w, K, f, "fp64", bc_type=bc, bc_value=bv)
+    x = np.arange(nx) + 0.5
+    assert np.abs(p.reshape(nz, ny, nx) - (1.0 - x / nx)[None, None, :]).max() < 1e-11
+    assert np.allclose(u[0], 1.5 / nx, rtol=1e-11)
+
+
+def test_c1_full_size_fp64_and_mixed():
+    w = workload("c1")
+    prob, r = _oracle(w)
+    for prec, tol in (("fp64", 1e-10), ("fp32_ir", 1e-8)):
+        s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, prec, ir_max_sweeps=8, ir_tol=1e-13)
+        assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
+        assert rel_l2(p, r.p) < tol, prec
+        assert rel_l2(u.ravel(), r.u.ravel()) < tol, prec
+
+
+def test_repeat_calls_are_deterministic():
+    w = small(**CASES["many_tiles"])
+    prob = oracle.from_workload(w)
+    import torch as T
+    from gpu_helpers import gpu_solver
+    s = gpu_solver(w, "fp64")
+    K = T.from_numpy(prob.K).cuda()
+    f = T.from_numpy(prob.f).cuda()
+    p1, u1, X1, _ = s.solve(K, f)
+    p1, X1 = p1.clone(), X1.clone()
+    p2, u2, X2, _ = s.solve(K, f)
+    assert T.equal(p1, p2) and T.equal(X1, X2)
