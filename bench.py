@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""MRCM pressure-solve benchmark on GB300.
+
+One step = one full MRCM pressure solve of the workload through the libmrcm C
+ABI: local assembly + block factor of every subdomain, all MBF and particular
+solves (with FP64 iterative refinement in mixed mode) and their traces, the
+interface assembly + multifrontal LDL^T, the interface solve with FP64
+refinement, and the reconstruction of p and u.  K and f are resident in HBM
+when the timed region starts; `e2e` repeats the measurement through host
+buffers (pinned H2D of K and f, D2H of p inside the timed region).
+
+Metric: completed MBF sets (subdomains: assembly + factor + all m_l solves to
+tolerance + traces, inside a full solve) per second, with the solve time per
+step; mixed precision is checked against the plain FP64 GPU form (relative L2
+error of p and u <= 1e-8) in the same run.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves an independent replica of the
+workload (the path has no data exchange between replicas); value = sets of all
+ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+# the CPU oracle baseline runs on one core: keep BLAS/OpenMP single-threaded
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+METRIC = "MRCM pressure solve s and MBF-sets/s, mixed/learned vs FP64 GPU at rel err 1e-8"
+UNIT = "MBF-sets/s"
+
+# Peaks (roofline denominators).  HBM and BF16 tensor from MEASURED_PEAKS.json
+# when present; SIMT ALU peaks from unit counts and the maximum SM clock:
+# FP32 = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 = the GB300 FP64
+# rate (1.25 TFLOP/s).
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    src = "measured"
+    try:
+        d = json.load(open(p))
+    except Exception:
+        d, src = dict(FALLBACK), "fallback"
+    sm_max = float(d.get("sm_max_mhz", 2070.0))
+    d["fp32_tflops"] = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    d["fp64_tflops"] = 1.25
+    d["source"] = src
+    return d
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(w, K, f, n_sub_sample, seed=0):
+    """Time the oracle's local MBF stage on a seeded sample of subdomains (1 core)."""
+    import numpy as np
+
+    import oracle
+    from oracle.mrcm import local_problem, solve_local, traces
+    from oracle.problem import build_bases
+    prob = oracle.from_workload(w, K=K, f=f)
+    bases, sub_bases, face_basis = build_bases(prob)
+    rng = np.random.default_rng(seed)
+    subs = rng.choice(prob.nsub, size=min(n_sub_sample, prob.nsub), replace=False)
+    t0 = time.perf_counter()
+    for l in subs:
+        lp = local_problem(prob, int(l), sub_bases, face_basis)
+        X = solve_local(lp)
+        traces(lp, X)
+    dt = time.perf_counter() - t0
+    return len(subs), dt
+
+
+def cpu_cores_used():
+    return 1
+
+
+# ------------------------------------------------------------------ roofline
+def roofline(name, total_ms, launches, sizes, precision, peaks):
+    """Achieved rate of the dominant kernel from its algorithmic work per launch."""
+    avg_s = total_ms / 1e3 / max(launches, 1)
+    n_sub = sizes["n_sub"]
+    cells = sizes["n_cells"]
+    mbf = sizes["mbf_entries"]
+    f32 = precision != "fp64"
+    if name == "k_block_solve":
+        # block-tridiagonal solve of all m_l columns: 4 N b m flops per subdomain
+        work = sizes["local_solve_flops"]
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp32_tflops"] if f32 else peaks["fp64_tflops"]
+        achieved = work / avg_s / 1e12
+    elif name == "k_block_factor":
+        work = sizes["local_factor_flops"]
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp32_tflops"] if f32 else peaks["fp64_tflops"]
+        achieved = work / avg_s / 1e12
+    elif name == "k_residual":
+        # FP64 7-point residual of every MBF column: 13 flops per cell per column
+        work = 13.0 * mbf
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
+        achieved = work / avg_s / 1e12
+    elif name in ("k_ldl_update", "k_ldl_rows", "k_ldl_diag"):
+        work = sizes["ldl_flops"] / max(launches, 1) * launches
+        bound, unit, peak = "alu", "TFLOP/s", peaks["fp64_tflops"]
+        achieved = sizes["ldl_flops"] / (total_ms / 1e3) / 1e12
+        work = sizes["ldl_flops"] / max(launches, 1)
+    else:
+        # bandwidth kernels: MBF array read once (8 B per entry) + 32 B per cell
+        work = 8.0 * mbf + 32.0 * cells
+        bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
+        achieved = work / avg_s / 1e9
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": unit,
+            "frac": round(achieved / peak, 4), "traffic": None, "launches": launches,
+            "avg_launch_ms": round(total_ms / max(launches, 1), 4), "peak_source": peaks["source"]}
+
+
+# ------------------------------------------------------------------ main
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--ir-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w, K, f, ws, rank):
+    if rank != 0:
+        return 0
+    per_step = max(8, args.cpu_sample // 8)
+    for i in range(args.warmup):
+        oracle_sample(w, K, f, per_step, seed=1000 + i)
+    tot_n, tot_t = 0, 0.0
+    for i in range(args.steps):
+        n, dt = oracle_sample(w, K, f, per_step, seed=i)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t
+    sample = (f"local MBF stage (assembly + sparse LU + all m_l right-hand sides + traces) of "
+              f"{per_step} seeded random subdomains per step out of {w.n_sub}; interface and "
+              f"reconstruction stages not included")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "cells": w.cells, "subdomains": w.n_sub},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    import numpy as np
+
+    from synth import workload
+    w = workload(args.workload)
+    K = w.K()
+    f = w.f()
+    if args.impl == "reference":
+        return run_reference(args, w, K, f, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2103_08513_gb300 import MRCM, build
+    if rank == 0:
+        build()
+    if ws > 1:
+        dist.barrier()
+    peaks = load_peaks()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(local)
+
+    def make(precision):
+        return MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const,
+                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=1e-13, device=dev)
+
+    Kd = torch.from_numpy(K).to(dev)
+    fd = torch.from_numpy(f).to(dev)
+    nx, ny, nz = w.n
+    s = make(args.precision)
+    s64 = make("fp64") if args.precision != "fp64" else s
+    outs = (torch.empty(max(s.n_interface, 1), dtype=torch.float64, device=dev),
+            torch.empty((nz, ny, nx), dtype=torch.float64, device=dev),
+            torch.empty((6, nz, ny, nx), dtype=torch.float64, device=dev),
+            torch.empty(1, dtype=torch.float64, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # reference FP64 GPU solution (untimed) and warm-up
+    p64, u64, X64, _ = s64.solve(Kd, fd)
+    p64, u64 = p64.clone(), u64.clone()
+    for _ in range(args.warmup):
+        s.solve(Kd, fd, out=outs)
+    torch.cuda.synchronize()
+    code, status = s.read_status()
+    p, u = outs[1], outs[2]
+    rel_p = float(torch.linalg.norm(p - p64) / torch.linalg.norm(p64))
+    rel_u = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
+    mres = float(outs[3].cpu()[0])
+
+    def timed(solver, steps, out, profile=False):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if profile:
+            solver.profile(True)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()                               # L2 flush outside the timed events
+            evs[i][0].record(stream)
+            solver.solve(Kd, fd, out=out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        prof = solver.profile_report() if profile else None
+        if profile:
+            solver.profile(False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, prof
+
+    clocks = ClockSampler(props.pci_bus_id if hasattr(props, "pci_bus_id") else local)
+    try:
+        pci = "%04x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        clocks = ClockSampler(pci)
+    except Exception:
+        clocks = ClockSampler(local)
+    clocks.start()
+    ms_total, (kprof, launches) = timed(s, args.steps, outs, profile=True)
+    # FP64 GPU form of the same solve, for the mixed-vs-FP64 comparison
+    steps64 = max(3, args.steps // 4)
+    outs64 = tuple(t.clone() for t in outs)
+    ms64 = timed(s64, steps64, outs64)[0] if s64 is not s else ms_total
+    if s64 is s:
+        steps64 = args.steps
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        Kh = torch.from_numpy(K).pin_memory()
+        fh = torch.from_numpy(f).pin_memory()
+        ph = torch.empty((nz, ny, nx), dtype=torch.float64).pin_memory()
+        e2e_steps = max(3, args.steps // 2)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(e2e_steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            Kd.copy_(Kh, non_blocking=True)
+            fd.copy_(fh, non_blocking=True)
+            s.solve(Kd, fd, out=outs)
+            ph.copy_(outs[1], non_blocking=True)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in evs)
+        e2e = (e2e_ms, e2e_steps, K.nbytes + f.nbytes, ph.numel() * 8)
+    clk = clocks.stop()
+
+    # max over ranks
+    t = torch.tensor([ms_total, ms64, e2e[0] if e2e else 0.0], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total, ms64, e2e_ms = (float(x) for x in t.cpu())
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    n_sub = w.n_sub
+    value = n_sub * args.steps * ws / (ms_total / 1e3)
+    sizes = s.sizes
+    dom = max(kprof.items(), key=lambda kv: kv[1][1])
+    roof = roofline(dom[0], dom[1][1], dom[1][0], sizes, args.precision, peaks)
+    kern_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(sum(x[1] for x in kprof.values()), 1e-9), 4)}
+                  for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_s, dt = oracle_sample(w, K, f, args.cpu_sample)
+        cpu = {"value": round(n_s / dt, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"local MBF stage (assembly + sparse LU + all m_l right-hand sides + traces) of {n_s} "
+                         f"seeded random subdomains of {n_sub} ({dt:.1f} s, one core); interface and "
+                         f"reconstruction stages not included"}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.cells, "subdomains": n_sub,
+                   "interface_unknowns": s.n_interface, "precision": args.precision,
+                   "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB write, outside the events)"},
+        "fp64_gpu": {"value": round(n_sub * steps64 * ws / (ms64 / 1e3), 2), "unit": UNIT,
+                     "ms_per_step": round(ms64 / steps64, 4)},
+        "rel_err_vs_fp64": {"p": rel_p, "u": rel_u, "tol": 1e-8, "ok": bool(rel_p <= 1e-8 and rel_u <= 1e-8)},
+        "status": status, "mass_residual_max": mres,
+        "roofline": roof,
+        "kernels": kern_share,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = {"value": round(n_sub * e2e[1] * ws / (e2e_ms / 1e3), 2), "unit": UNIT,
+                       "h2d_bytes_per_step": int(e2e[2]), "d2h_bytes_per_step": int(e2e[3]),
+                       "ms_per_step": round(e2e_ms / e2e[1], 4)}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

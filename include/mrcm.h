@@ -123,10 +123,12 @@ typedef struct {
     long long nnz_interface;    /* nonzeros of A^int in the CSR pattern */
     int n_fronts;               /* internal nodes of the interface elimination tree */
     int max_front;              /* largest dense front */
-    double front_flops;         /* flops of the interface factorisation */
+    double front_flops;         /* flops of an LU of the same fronts (2x the LDL^T) */
     double local_factor_flops;  /* flops of all local block factorisations */
     double local_solve_flops;   /* flops of one solve sweep over all MBF columns */
     int max_block;              /* largest slab block size b */
+    long long mbf_entries;      /* sum over l of m_l * N_l (MBF array length) */
+    double ldl_flops;           /* flops of the interface LDL^T (lower triangle) */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;

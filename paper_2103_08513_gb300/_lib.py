@@ -46,6 +46,7 @@ class mrcm_sizes(C.Structure):
         ("nnz_interface", C.c_longlong), ("n_fronts", C.c_int), ("max_front", C.c_int),
         ("front_flops", C.c_double), ("local_factor_flops", C.c_double),
         ("local_solve_flops", C.c_double), ("max_block", C.c_int),
+        ("mbf_entries", C.c_longlong), ("ldl_flops", C.c_double),
     ]
 
 

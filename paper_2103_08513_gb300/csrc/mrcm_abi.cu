@@ -34,7 +34,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 
 void free_device(mrcm::DeviceTables& d) {
     void* ptrs[] = {d.subs, d.faces, d.Ilist, d.rowptr, d.colidx, d.src_lo, d.src_hi, d.rhs_src_lo,
-                    d.rhs_src_hi, d.fronts, d.front_maps, d.front_dofs, d.level_ids};
+                    d.rhs_src_hi, d.fronts, d.front_maps, d.front_inv, d.front_dofs, d.level_ids};
     for (void* p : ptrs) if (p) cudaFree(p);
     d = mrcm::DeviceTables();
 }
@@ -70,6 +70,7 @@ mrcm_status ensure_device(mrcm_handle* h, void* stream) {
     UP(rhs_src_hi, t.rhs_src_hi);
     UP(fronts, t.fronts);
     UP(front_maps, t.front_maps);
+    UP(front_inv, t.front_inv);
     UP(front_dofs, t.front_dofs);
     UP(level_ids, lvl);
 #undef UP
@@ -106,7 +107,9 @@ mrcm_status mrcm_setup(const mrcm_config* cfg, mrcm_handle** out) {
             if (s.N > 4096) { st = MRCM_ERR_NOT_IMPLEMENTED; h->err = "subdomain larger than 4096 cells"; break; }
         }
     }
-    size_t solve_smem = sizeof(double) * ((size_t)t.max_b * t.max_b + 2 * (size_t)t.max_b * t.max_m);
+    const size_t mpad = (size_t)((t.max_m + 3) & ~3);
+    size_t solve_smem = sizeof(double) * ((size_t)t.max_b * t.max_b + 4 + 3 * (size_t)t.max_b * mpad + 2 * mpad) +
+                        12 * (size_t)t.max_N + 64;
     if (st == MRCM_OK && solve_smem > 227 * 1024) {
         st = MRCM_ERR_NOT_IMPLEMENTED;
         h->err = "slab block and right-hand-side count exceed shared memory";
@@ -145,6 +148,8 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
     o->local_factor_flops = t.local_factor_flops;
     o->local_solve_flops = t.local_solve_flops;
     o->max_block = t.max_b;
+    o->mbf_entries = t.total_x;
+    o->ldl_flops = t.ldl_flops;
     return MRCM_OK;
 }
 

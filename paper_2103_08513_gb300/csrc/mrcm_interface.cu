@@ -30,7 +30,7 @@
 // extend-add of the two children (subdomain blocks at the leaves), partially
 // factored by a blocked right-looking LDL^T (32-column panels, 64x64 update
 // tiles spread over the whole GPU), and leave the Schur complement on B for
-// their parent.  The solution is refined twice in FP64 with CSR residuals.
+// their parent.  The solution is refined once in FP64 with CSR residuals.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +44,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPanel = 32;        // LDL^T panel width
 constexpr int kRowTile = 256;     // rows per panel-solve CTA
-constexpr int kTile = 64;         // trailing-update tile
+constexpr int kTile = 64;         // trailing-update and assembly tile
+constexpr int kRefine = 1;        // FP64 refinement steps of the interface solve
 
 __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const long long* __restrict__ src_lo,
                                const long long* __restrict__ src_hi, const int* __restrict__ rsl,
@@ -68,119 +69,119 @@ __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const 
 
 __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 1.0 : -1.0; }
 
-// Zero the front (lower triangle) and add the two children's contributions:
-// scaled J-signed subdomain blocks for leaves, Schur complements otherwise.
+// Front assembly as a gather: every lower-triangle entry (r >= q) of the
+// front is written once, as the sum (child 0 first) of the children's
+// entries at the same dofs -- J-signed, scaled subdomain blocks for leaves,
+// the lower triangle of the Schur complement otherwise.  64x64 tiles of the
+// lower triangle are spread over the grid; blockIdx.y selects the front.
 __global__ void __launch_bounds__(kThreads)
 k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
-                 const int* __restrict__ maps, const int* __restrict__ dofs, const SubInfo* __restrict__ subs,
+                 const int* __restrict__ inv, const int* __restrict__ dofs, const SubInfo* __restrict__ subs,
                  const double* __restrict__ elem, const double* __restrict__ dscale, int NV,
                  double* __restrict__ F) {
-    const FrontInfo fr = fronts[ids[blockIdx.x]];
-    double* Fm = F + fr.f_off;
+    const FrontInfo fr = fronts[ids[blockIdx.y]];
     const int n = fr.n;
+    const int nt = (n + kTile - 1) / kTile;
+    const int t = blockIdx.x;
+    if (t >= nt * (nt + 1) / 2) return;
+    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    double* Fm = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) Fm[e] = 0.0;
-    __syncthreads();
+    const int* inv0 = inv + fr.inv_off;
+    const int* inv1 = inv0 + n;
+    const double* src[2];
+    int ld[2], off[2];
+    bool leaf[2];
     for (int ci = 0; ci < 2; ++ci) {
         const int c = fr.child[ci];
-        const int* mp = maps + fr.map_off[ci];
-        const int len = fr.map_len[ci];
-        const long long pairs = (long long)len * (len + 1) / 2;
+        leaf[ci] = c < 0;
         if (c < 0) {
             const SubInfo& s = subs[-(c + 1)];
-            const double* E = elem + s.el_off;
-            const int ld = s.el_dim;
-            for (long long e = threadIdx.x; e < pairs; e += blockDim.x) {
-                // e -> (i >= j)
-                int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-                while ((long long)i * (i + 1) / 2 > e) --i;
-                while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
-                int j = (int)(e - (long long)i * (i + 1) / 2);
-                int a = mp[i], bq = mp[j];
-                int da = fd[a], db = fd[bq];
-                double v = dof_sign(da, NV) * E[(long long)i * ld + j] * dscale[da] * dscale[db];
-                int r = max(a, bq), q = min(a, bq);
-                Fm[(long long)r * n + q] += v;
-            }
+            src[ci] = elem + s.el_off;
+            ld[ci] = s.el_dim;
+            off[ci] = 0;
         } else {
-            const FrontInfo cf = fronts[c];
-            const double* S = F + cf.f_off;
-            const int ldc = cf.n, o = cf.ne;
-            for (long long e = threadIdx.x; e < pairs; e += blockDim.x) {
-                int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-                while ((long long)i * (i + 1) / 2 > e) --i;
-                while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
-                int j = (int)(e - (long long)i * (i + 1) / 2);
-                int a = mp[i], bq = mp[j];
-                int r = max(a, bq), q = min(a, bq);
-                Fm[(long long)r * n + q] += S[(long long)(o + i) * ldc + (o + j)];
+            const FrontInfo& cf = fronts[c];
+            src[ci] = F + cf.f_off;
+            ld[ci] = cf.n;
+            off[ci] = cf.ne;
+        }
+    }
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = ti * kTile + e / kTile;
+        const int q = tj * kTile + e % kTile;
+        if (r >= n || q > r) continue;
+        double v = 0.0;
+        const int dr = fd[r], dq = fd[q];
+#pragma unroll
+        for (int ci = 0; ci < 2; ++ci) {
+            const int* iv = ci == 0 ? inv0 : inv1;
+            const int ir = iv[r], iq = iv[q];
+            if (ir < 0 || iq < 0) continue;
+            if (leaf[ci]) {
+                v += dof_sign(dr, NV) * src[ci][(long long)ir * ld[ci] + iq] * dscale[dr] * dscale[dq];
+            } else {
+                const int a = off[ci] + max(ir, iq), b2 = off[ci] + min(ir, iq);
+                v += src[ci][(long long)a * ld[ci] + b2];
             }
         }
-        __syncthreads();
+        if (r == fr.pin_row && q == fr.pin_row) v -= 1.0;
+        Fm[(long long)r * n + q] = v;
     }
-    if (fr.pin_row >= 0 && threadIdx.x == 0) Fm[(long long)fr.pin_row * n + fr.pin_row] -= 1.0;
 }
 
-// Panel step of the blocked LDL^T, part 1: factor the diagonal block
-// [k0, k0+nbk) of every front in shared memory (one CTA per front) and write
-// L11 (strict lower) and D (diagonal) back.
+// Panel step of the blocked LDL^T: every CTA factors the diagonal block
+// [k0, k0+nbk) of its front in shared memory (redundantly: the factored
+// block must not be written to the front while other CTAs of the same launch
+// still read it), then solves its tile of rows below, l = f L11^{-T} D^{-1},
+// one thread per row.  CTA x = 0 leaves the factored block (L11 strict lower,
+// D on the diagonal) in `scratch`; the trailing-update kernel copies it into
+// the front.
 __global__ void __launch_bounds__(kThreads)
-k_ldl_diag(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0,
-           double* __restrict__ F, int* __restrict__ status) {
-    const FrontInfo fr = fronts[ids[blockIdx.x]];
-    if (k0 >= fr.ne) return;
-    const int n = fr.n;
-    const int nbk = min(kPanel, fr.ne - k0);
-    double* A = F + fr.f_off;
-    __shared__ double L[kPanel][kPanel + 1];
-    for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
-        int i = e / nbk, j = e % nbk;
-        if (i >= j) L[i][j] = A[(long long)(k0 + i) * n + k0 + j];
-    }
-    __syncthreads();
-    int zero = 0;
-    for (int k = 0; k < nbk; ++k) {
-        double d = L[k][k];
-        if (d == 0.0 || d != d) { zero = 1; d = 1.0; }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
-            int i = e / nbk, j = e % nbk;
-            if (j > k && i >= j) L[i][j] -= L[i][k] * L[j][k] / d;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) L[k][k] = d;
-        for (int i = k + 1 + threadIdx.x; i < nbk; i += blockDim.x) L[i][k] /= d;
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
-        int i = e / nbk, j = e % nbk;
-        if (i >= j) A[(long long)(k0 + i) * n + k0 + j] = L[i][j];
-    }
-    if (zero && threadIdx.x == 0) atomicAdd(&status[ST_ZERO_PIVOT], 1);
-}
-
-// Panel step, part 2: rows below the diagonal block, l = f L11^{-T} D^{-1};
-// one thread per row, kRowTile rows per CTA.
-__global__ void __launch_bounds__(kThreads)
-k_ldl_rows(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F) {
+k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0,
+            const double* __restrict__ F, double* __restrict__ Fw, double* __restrict__ scratch,
+            int* __restrict__ status) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
     const int nbk = min(kPanel, fr.ne - k0);
     const int r0 = k0 + nbk + blockIdx.x * kRowTile;
-    if (r0 >= n) return;
-    double* A = F + fr.f_off;
+    if (blockIdx.x > 0 && r0 >= n) return;
+    const double* A = F + fr.f_off;
     __shared__ double L[kPanel][kPanel + 1];
-    __shared__ double D[kPanel];
-    for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
-        int i = e / kPanel, j = e % kPanel;
-        L[i][j] = (i < nbk && j < i) ? A[(long long)(k0 + i) * n + k0 + j] : 0.0;
-    }
-    for (int k = threadIdx.x; k < kPanel; k += blockDim.x) D[k] = k < nbk ? A[(long long)(k0 + k) * n + k0 + k] : 1.0;
+    __shared__ double Dinv[kPanel];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
+    for (int i = ty; i < kPanel; i += 8) L[i][tx] = (i < nbk && tx <= i) ? A[(long long)(k0 + i) * n + k0 + tx] : 0.0;
     __syncthreads();
+    int zero = 0;
+    for (int k = 0; k < nbk; ++k) {
+        if (threadIdx.x == 0) {
+            double d = L[k][k];
+            if (d == 0.0 || d != d) { zero = 1; d = 1.0; L[k][k] = 1.0; }
+            Dinv[k] = 1.0 / d;
+        }
+        __syncthreads();
+        const double inv = Dinv[k];
+        // l_ik for i > k (column k scaled in place after the trailing update below)
+        for (int i = k + 1 + ty; i < nbk; i += 8) {
+            const double lik = L[i][k] * inv;
+            for (int j = k + 1 + tx; j <= i; j += 32) L[i][j] -= lik * L[j][k];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32 && k + 1 + tx < nbk) L[k + 1 + tx][k] *= inv;
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
+        for (int i = ty; i < nbk; i += 8) sc[i * kPanel + tx] = (tx <= i) ? L[i][tx] : 0.0;
+        if (zero && threadIdx.x == 0) atomicAdd(&status[ST_ZERO_PIVOT], 1);
+    }
     const int r = r0 + threadIdx.x;
     if (r < n) {
-        double* row = A + (long long)r * n + k0;
+        double* row = Fw + fr.f_off + (long long)r * n + k0;
         double w[kPanel];
 #pragma unroll
         for (int j = 0; j < kPanel; ++j) w[j] = j < nbk ? row[j] : 0.0;
@@ -193,20 +194,29 @@ k_ldl_rows(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, in
         }
 #pragma unroll
         for (int j = 0; j < kPanel; ++j)
-            if (j < nbk) row[j] = w[j] / D[j];
+            if (j < nbk) row[j] = w[j] * Dinv[j];
     }
 }
 
 // Trailing update of the blocked LDL^T: F22 -= L21 D L21^T on 64x64 tiles of
 // the lower triangle; blockIdx.x enumerates the (ti >= tj) tile pairs.
 __global__ void __launch_bounds__(kThreads)
-k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F) {
+k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
+             const double* __restrict__ scratch) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
     const int nbk = min(kPanel, fr.ne - k0);
     const int k1 = k0 + nbk;
     const int m = n - k1;
+    if (blockIdx.x == 0) {                  // commit the factored diagonal block of this panel
+        const double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
+        double* A0 = F + fr.f_off;
+        for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
+            const int i = e >> 5, j = e & 31;
+            if (i < nbk && j <= i) A0[(long long)(k0 + i) * n + k0 + j] = sc[e];
+        }
+    }
     if (m <= 0) return;
     const int nt = (m + kTile - 1) / kTile;
     const int T = nt * (nt + 1) / 2;
@@ -220,8 +230,10 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
     __shared__ double Li[kTile][kPanel + 1];
     __shared__ double Lj[kTile][kPanel + 1];
     __shared__ double Dk[kPanel];
-    for (int k = threadIdx.x; k < kPanel; k += blockDim.x)
-        Dk[k] = k < nbk ? A[(long long)(k0 + k) * n + k0 + k] : 0.0;
+    {
+        const double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
+        for (int k = threadIdx.x; k < kPanel; k += blockDim.x) Dk[k] = k < nbk ? sc[k * kPanel + k] : 0.0;
+    }
     __syncthreads();
     const int i0 = k1 + ti * kTile, j0 = k1 + tj * kTile;
     for (int e = threadIdx.x; e < kTile * kPanel; e += blockDim.x) {
@@ -411,22 +423,24 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
                                                    (double*)(ws + L.b_int), dscale));
     // numeric multifrontal factorisation, leaves to root
     double* F = (double*)(ws + L.fronts);
+    double* scratch = (double*)(ws + L.panel);
     int* status = (int*)(ws + L.status);
     for (size_t h = 1; h < t.levels.size(); ++h) {
         int cnt = (int)t.levels[h].size();
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
-        MRCM_LAUNCH(P, "k_front_assemble", st, k_front_assemble<<<cnt, kThreads, 0, st>>>(d.fronts, ids, d.front_maps, d.front_dofs, d.subs,
+        int maxT = 1;
+        for (int id : t.levels[h]) { int nt = (t.fronts[id].n + kTile - 1) / kTile; maxT = std::max(maxT, nt * (nt + 1) / 2); }
+        dim3 ga(maxT, cnt);
+        MRCM_LAUNCH(P, "k_front_assemble", st, k_front_assemble<<<ga, kThreads, 0, st>>>(d.fronts, ids, d.front_inv, d.front_dofs, d.subs,
                                                   (const double*)(ws + L.elem), dscale, t.NV, F));
         LevelPlan p = plan_level(t, (int)h);
         for (int s = 0; s < p.steps; ++s) {
-            MRCM_LAUNCH(P, "k_ldl_diag", st, k_ldl_diag<<<cnt, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, status));
             dim3 gp(p.row_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_rows", st, k_ldl_rows<<<gp, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F));
-            if (p.upd_tiles[s] > 0) {
-                dim3 gu(p.upd_tiles[s], cnt);
-                MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F));
-            }
+            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, F,
+                                                                                 scratch, status));
+            dim3 gu(std::max(1, p.upd_tiles[s]), cnt);
+            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, scratch));
         }
     }
     return (int)cudaGetLastError();
@@ -469,7 +483,7 @@ int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout&
     const int pin = t.has_dirichlet ? 0 : 1;
     multifrontal_solve(t, d, L, ws, b, xs, st, P);
     MRCM_LAUNCH(P, "k_unscale", st, k_unscale<<<(nd + 255) / 256, 256, 0, st>>>(nd, xs, dscale, X, 0));
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kRefine; ++it) {
         MRCM_LAUNCH(P, "k_csr_residual", st, k_csr_residual<<<(nd + 127) / 128, 128, 0, st>>>(nd, d.rowptr, d.colidx, (const double*)(ws + L.csr_val),
                                                        b, X, dscale, pin, r));
         multifrontal_solve(t, d, L, ws, r, xs, st, P);

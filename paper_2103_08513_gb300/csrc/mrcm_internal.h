@@ -32,7 +32,7 @@ struct SubInfo {
     long long w_off;      // offset (elements) into the block factor array
     long long el_off;     // offset (doubles) into element matrices
     int elb_off;          // offset (doubles) into element right-hand sides
-    int pad;
+    int rhs_off;          // offset of the subdomain's columns in per-column arrays
 };
 
 // One Robin face of a subdomain (a fine face of Gamma seen from one side).
@@ -53,6 +53,7 @@ struct FrontInfo {
     int child[2];           // child front index, or -(1 + element) for a leaf
     int map_off[2];         // offset (ints) of the child -> front position maps
     int map_len[2];
+    int inv_off;            // offset (ints) of the front -> child position maps (2 x n, -1 = absent)
     int e_dof_off;          // offset (ints) into the global dof list of E then B
     int pin_row;            // front row of pi^p_0 when it is regularised, or -1
     int height;
@@ -88,20 +89,21 @@ struct Tables {
     // elimination tree
     std::vector<FrontInfo> fronts;
     std::vector<int> front_maps;               // child -> front position maps
+    std::vector<int> front_inv;                // front -> child position maps
     std::vector<int> front_dofs;               // global dof of each front row
     std::vector<std::vector<int>> levels;      // fronts grouped by height
     long long total_front = 0;
     int total_frhs = 0;
     int max_front = 0;
-    double front_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
+    double front_flops = 0, ldl_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
     int pin_front = -1;
 };
 
 // Workspace layout (byte offsets into the caller's workspace).
 struct Layout {
-    size_t coef, scale, rhs_part, face_tr, face_beta, W, X, R, colnorm, conv;
-    size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, xres, xtmp, psum, status;
+    size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, W, X, R, colnorm, conv;
+    size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, xres, xtmp, psum, status;
     size_t total;
 };
 
@@ -117,6 +119,7 @@ struct DeviceTables {
     int* rhs_src_hi = nullptr;
     FrontInfo* fronts = nullptr;
     int* front_maps = nullptr;
+    int* front_inv = nullptr;
     int* front_dofs = nullptr;
     int* level_ids = nullptr;                  // fronts of all levels, concatenated
     std::vector<int> level_off;                // host: offsets of each level in level_ids

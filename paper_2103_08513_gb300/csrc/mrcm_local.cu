@@ -136,7 +136,7 @@ template <typename T, bool kScaled>
 __global__ void __launch_bounds__(kThreads)
 k_block_factor(const SubInfo* __restrict__ subs, const double* __restrict__ coef,
                const double* __restrict__ scale, T* __restrict__ Wall, int* __restrict__ status,
-               long long nct, int bmax) {
+               long long nct, int bmax, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A = reinterpret_cast<T*>(smem_raw);          // b x b, row major
     T* col = A + bmax * bmax;                        // pivot column
@@ -149,300 +149,441 @@ k_block_factor(const SubInfo* __restrict__ subs, const double* __restrict__ coef
     const double* cs = coef + 3 * nct + s.cell_off;
     const double* sc = scale + s.cell_off;
     T* W = Wall + s.w_off;
+    float* scf = scf_all + s.cell_off;
+    float* tsc = tsc_all + s.cell_off;
     int bad = 0;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
         // S_s = D_s - diag(t) W_{s-1} diag(t), in place over W_{s-1}
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-            int i = e / b, j = e - (e / b) * b;
-            double dij = 0.0;
-            int ci = base + i, cj = base + j;
-            if (i == j) dij = cd[ci];
-            else {
-                int ui = i % su, uj = j % su;
-                if (j == i + 1 && uj == ui + 1) dij = -cu[ci];
-                else if (i == j + 1 && ui == uj + 1) dij = -cu[cj];
+        for (int i = ty; i < b; i += 8) {
+            const int ci = base + i;
+            const int ui = i % su;
+            const double si = kScaled ? sc[ci] : 1.0;
+            const double ti = sl > 0 ? cs[ci - b] * (kScaled ? sc[ci - b] * si : 1.0) : 0.0;
+            for (int j = tx; j < b; j += 32) {
+                const int cj = base + j;
+                double dij = 0.0;
+                if (i == j) dij = cd[ci];
+                else if (j == i + 1 && ui + 1 < su) dij = -cu[ci];
+                else if (i == j + 1 && ui > 0) dij = -cu[cj];
                 else if (j == i + su) dij = -cv[ci];
                 else if (i == j + su) dij = -cv[cj];
+                double v = dij;
+                if (kScaled) v *= si * sc[cj];
+                if (sl > 0) {
+                    const double tj = cs[cj - b] * (kScaled ? sc[cj - b] * sc[cj] : 1.0);
+                    v -= ti * tj * (double)A[i * b + j];
+                }
+                A[i * b + j] = (T)v;
             }
-            if (kScaled) dij *= sc[ci] * sc[cj];
-            double v = dij;
-            if (sl > 0) {
-                double ti = cs[ci - b], tj = cs[cj - b];
-                if (kScaled) { ti *= sc[ci - b] * sc[ci]; tj *= sc[cj - b] * sc[cj]; }
-                v -= ti * tj * (double)A[e];
-            }
-            A[e] = (T)v;
         }
         __syncthreads();
         // in-place Gauss-Jordan inversion (row k and column k saved separately:
         // the intermediate matrices are not symmetric)
         for (int k = 0; k < b; ++k) {
-            T p = A[k * b + k];
             for (int i = threadIdx.x; i < b; i += blockDim.x) { col[i] = A[i * b + k]; row[i] = A[k * b + i]; }
             __syncthreads();
+            T p = col[k];
             if (!(p > (T)0)) { bad = 1; p = (T)1; }
-            T ip = (T)1 / p;
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-                int i = e / b, j = e - (e / b) * b;
-                T v;
-                if (i == k && j == k) v = ip;
-                else if (i == k) v = row[j] * ip;
-                else if (j == k) v = -col[i] * ip;
-                else v = A[e] - col[i] * row[j] * ip;
-                A[e] = v;
+            const T ip = (T)1 / p;
+            for (int i = ty; i < b; i += 8) {
+                const T ci = col[i];
+                for (int j = tx; j < b; j += 32) {
+                    T v;
+                    if (i == k && j == k) v = ip;
+                    else if (i == k) v = row[j] * ip;
+                    else if (j == k) v = -ci * ip;
+                    else v = A[i * b + j] - ci * row[j] * ip;
+                    A[i * b + j] = v;
+                }
             }
             __syncthreads();
         }
-        // W_s: the block is symmetric; store it
+        // W_s (symmetric)
         T* Ws = W + (long long)sl * b * b;
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) Ws[e] = A[e];
+        if (kScaled) {
+            // FP32 copies for the solves: S and the scaled coupling t^ = t_s S_c S_{c+b}
+            for (int i = threadIdx.x; i < b; i += blockDim.x) {
+                const int c = base + i;
+                scf[c] = (float)sc[c];
+                tsc[c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+            }
+        }
         __syncthreads();
     }
     if (bad && threadIdx.x == 0) atomicAdd(&status[ST_NOT_SPD], 1);
 }
 
 // ---------------------------------------------------------------------------
-// Right-hand sides of all MBFs and the particular problem, written in place
-// into the MBF array [m][N] of each subdomain:
-//   P-MBF k: T_R on the faces of basis k;  U-MBF k: -beta s T_R on them;
-//   particular: f V + Dirichlet wall terms.
-// Each (cell, column) is written by at most one face: a cell has one face
-// per side and a basis lives on one side of one interface.
+// Register-resident variant of the block factorisation for b <= 64 (FP32,
+// scaled): a 64-thread CTA per subdomain, thread i holds row i of the running
+// block in registers, the pivot row is broadcast through shared memory, and
+// W_{s-1} stays in registers for the next block pivot.  Same arithmetic as
+// k_block_factor (in-place Gauss-Jordan without pivoting on the SPD block).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_rhs(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
-      const double* __restrict__ face_tr, const double* __restrict__ face_beta,
-      const double* __restrict__ rhs_dir, const double* __restrict__ f, Geo geo,
-      double* __restrict__ X) {
+constexpr int kRegMaxB = 64;
+
+__global__ void __launch_bounds__(kRegMaxB)
+k_block_factor_reg(const SubInfo* __restrict__ subs, const double* __restrict__ coef,
+                   const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
+                   long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
     const SubInfo s = subs[blockIdx.x];
-    double* Xs = X + s.x_off;
-    const double vol = geo.h[0] * geo.h[1] * geo.h[2];
-    const long long nN = (long long)s.m * s.N;
-    for (long long e = threadIdx.x; e < nN - s.N; e += blockDim.x) Xs[e] = 0.0;
-    double* part = Xs + (long long)(s.m - 1) * s.N;
-    for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
-        int lc[3];
-        local_coords(s, c, lc);
-        part[c] = rhs_dir[s.cell_off + c] + f[global_cell(s, lc, geo.n)] * vol;
+    const int b = s.b, su = s.su;
+    const int i = threadIdx.x;
+    const bool live = i < b;
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* sc = scale + s.cell_off;
+    float* W = Wall + s.w_off;
+    float* scf = scf_all + s.cell_off;
+    float* tsc = tsc_all + s.cell_off;
+    __shared__ __align__(16) float prow[kRegMaxB];
+    __shared__ float tv[kRegMaxB];
+    float a[kRegMaxB];
+#pragma unroll
+    for (int j = 0; j < kRegMaxB; ++j) a[j] = 0.0f;
+    int bad = 0;
+    for (int sl = 0; sl < s.ns; ++sl) {
+        const int base = sl * b;
+        float dd = 0.f, du = 0.f, dul = 0.f, dv = 0.f, dvl = 0.f, ti = 0.f;
+        if (live) {
+            const int c = base + i;
+            const int u = i % su;
+            dd = (float)(cd[c] * sc[c] * sc[c]);
+            if (u + 1 < su) du = (float)(-cu[c] * sc[c] * sc[c + 1]);
+            if (u > 0) dul = (float)(-cu[c - 1] * sc[c] * sc[c - 1]);
+            if (i + su < b) dv = (float)(-cv[c] * sc[c] * sc[c + su]);
+            if (i >= su) dvl = (float)(-cv[c - su] * sc[c] * sc[c - su]);
+            if (sl > 0) ti = (float)(cs[c - b] * sc[c - b] * sc[c]);
+            scf[c] = (float)sc[c];
+            tsc[c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+        }
+        tv[i] = ti;
+        __syncthreads();
+        // S_s = D_s - t o W_{s-1} o t   (W_{s-1} in registers; zero at the first slab)
+#pragma unroll
+        for (int j = 0; j < kRegMaxB; ++j) {
+            if (j < b) {
+                // independent terms: with su == 1 the u- and v-neighbours share an index
+                // (the u-coupling is then zero)
+                float v = -ti * tv[j] * a[j];
+                if (j == i) v += dd;
+                if (j == i + 1) v += du;
+                if (j == i - 1) v += dul;
+                if (j == i + su) v += dv;
+                if (j == i - su) v += dvl;
+                a[j] = live ? v : 0.0f;
+            }
+        }
+        // Gauss-Jordan inversion; the pivot row goes through shared memory.
+        // Gauss-Jordan on a symmetric matrix keeps M[i][k] = sigma_i M[k][i] with
+        // sigma_i = -1 for the columns already pivoted (i < k), +1 otherwise, so
+        // each thread reads its column-k entry back from the published row.
+#pragma unroll 1
+        for (int k = 0; k < b; ++k) {
+            __syncthreads();                                 // previous step done with prow
+            if (i == k) {
+                float4* pr4 = reinterpret_cast<float4*>(prow);
+#pragma unroll
+                for (int j = 0; j < kRegMaxB; j += 4) pr4[j >> 2] = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+            }
+            __syncthreads();
+            float p = prow[k];
+            if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+            const float ip = 1.0f / p;
+            const float ck = i < k ? -prow[i] : prow[i];     // M[i][k]
+            const bool own = i == k;
+            const float4* pr4 = reinterpret_cast<const float4*>(prow);
+#pragma unroll
+            for (int j4 = 0; j4 < kRegMaxB; j4 += 4) {
+                if (j4 < b) {
+                    const float4 q = pr4[j4 >> 2];
+                    const float pq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = j4 + t;
+                        const float tj = pq[t] * ip;
+                        if (j == k) a[j] = own ? ip : -ck * ip;
+                        else a[j] = own ? tj : fmaf(-ck, tj, a[j]);
+                    }
+                }
+            }
+        }
+        // store W_s (symmetric: thread i writes column i = row i), coalesced over threads
+        float* Ws = W + (long long)sl * b * b;
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < kRegMaxB; ++j)
+                if (j < b) Ws[j * b + i] = a[j];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
-        FaceInfo fi = faces[s.face_off + q];
-        double tr = face_tr[s.face_off + q];
-        Xs[(long long)fi.col * s.N + fi.cell] = tr;
-        Xs[(long long)(s.nI + fi.col) * s.N + fi.cell] = -face_beta[s.face_off + q] * fi.s * tr;
-    }
+    if (bad) atomicAdd(&status[ST_NOT_SPD], 1);
 }
 
 // ---------------------------------------------------------------------------
-// Multi-RHS block solve on one subdomain (all m columns), in place:
-//   forward   Z_s = r_s + t_{s-1} o Y_{s-1},   Y_s = W_s Z_s   (Y_s overwrites r_s)
+// Multi-RHS block solve, fused with the right-hand sides (first solve) or with
+// the FP64 residual (refinement sweep).  One CTA per subdomain.
+//
+//   first solve (kSweep = false):  r = B                     X  = S x
+//   refinement  (kSweep = true):   r = B - A X   (FP64)      X += S x
+// where x solves A^ x = S r slab by slab:
+//   forward   Z_s = S r_s + t_{s-1} o Y_{s-1},  Y_s = W_s Z_s
 //   backward  x_s = Y_s + W_s (t_s o x_{s+1})
-// The result is written to `out` (overwrite, or accumulate when kAccumulate).
-// In scaled (mixed) mode the solve is for A^ = S A S: r is scaled by S on
-// input and x by S on output.
+// (S = I in the unscaled FP64 mode).  B is built on the fly: the particular
+// column holds f V plus the Dirichlet wall terms; P-MBF column k holds T_R on
+// the faces of basis k and U-MBF column k holds -beta s T_R there.
+//
+// Only the columns not yet converged take part (compacted list); in a
+// refinement sweep each column's ||r||_2 is compared with tol ||b||_2 and the
+// column is retired for later sweeps once it passes.  Y_s is kept in a
+// workspace array of type T between the two sweeps.
 // ---------------------------------------------------------------------------
-constexpr int kMaxColsPerThread = 16;
 
-template <typename T, bool kScaled, bool kAccumulate>
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_16a; };
+
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type ld4(const T* p) { return *reinterpret_cast<const typename Vec4<T>::type*>(p); }
+
+// Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile 2 rows x 4 columns.
+// Results handed to `store(i, jj, value)`.
+template <typename T, typename Store>
+__device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* __restrict__ Z, int b, int na,
+                                           int mpad, Store store) {
+    const int bh = (b + 1) >> 1;
+    const int mq = (na + 3) >> 2;
+    for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
+        const int i0 = task % bh, cq = task / bh;
+        const int i1 = i0 + bh;
+        const bool has1 = i1 < b;
+        T a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        const T* zc = Z + 4 * cq;
+        for (int k = 0; k < b; ++k) {
+            const T w0 = Wsm[k * b + i0];
+            const T w1 = has1 ? Wsm[k * b + i1] : (T)0;
+            const typename Vec4<T>::type z = ld4(zc + k * mpad);
+            a0[0] += w0 * z.x; a0[1] += w0 * z.y; a0[2] += w0 * z.z; a0[3] += w0 * z.w;
+            a1[0] += w1 * z.x; a1[1] += w1 * z.y; a1[2] += w1 * z.z; a1[3] += w1 * z.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * cq + q;
+            if (jj < na) {
+                store(i0, jj, a0[q]);
+                if (has1) store(i1, jj, a1[q]);
+            }
+        }
+    }
+}
+
+struct LocalArgs {
+    const SubInfo* subs;
+    const FaceInfo* faces;
+    const double* coef;
+    const double* scale;
+    const float* scf;      // FP32 Jacobi scale (mixed mode)
+    const float* tsc;      // FP32 scaled slab coupling (mixed mode)
+    const double* face_tr;
+    const double* face_beta;
+    const double* rhs_dir;
+    const double* f;
+    Geo geo;
+    long long nct;
+    double* X;            // MBF array [m][N] per subdomain (FP64)
+    void* Ybuf;           // forward-sweep results, type T, same layout as X
+    int* conv;            // per column: 1 = converged (skip)
+    double* bnorm;        // per column ||b||^2
+    double tol2;
+    int* status;
+    int mpad;             // row stride of the shared column blocks (multiple of 4)
+};
+
+// Shared-memory layout of k_local_solve: W (b*b rounded up to 4 elements, so
+// that the column blocks stay 16-byte aligned for vector loads), Z and Yp
+// (b x mpad of T each), column norms, active columns and the per-cell
+// Robin-face map (six sides per cell).
+__host__ __device__ inline int wstride(int b) { return (b * b + 3) & ~3; }
+
+template <typename T>
+__host__ __device__ inline size_t local_smem_bytes(int b, int mpad, int N) {
+    size_t x = (sizeof(T) * ((size_t)wstride(b) + 2 * (size_t)b * mpad) + 15) & ~size_t(15);
+    x += sizeof(double) * mpad;
+    x += sizeof(int) * mpad;
+    x += sizeof(short) * 6 * (size_t)N;
+    return (x + 15) & ~size_t(15);
+}
+
+// Coupling between slab cells c and c+b in the solve's arithmetic: the FP32
+// scaled value t^ in mixed mode, the FP64 transmissibility otherwise.
+template <typename T, bool kScaled> struct Coupling;
+template <> struct Coupling<float, true> {
+    const float* tsc; const float* scf;
+    __device__ float t(int c) const { return tsc[c]; }
+    __device__ float in(double r, int c) const { return (float)r * scf[c]; }
+    __device__ double out(float x, int c) const { return (double)(x * scf[c]); }
+};
+template <> struct Coupling<double, false> {
+    const double* cs;
+    __device__ double t(int c) const { return cs[c]; }
+    __device__ double in(double r, int) const { return r; }
+    __device__ double out(double x, int) const { return x; }
+};
+
+template <typename T, bool kScaled, bool kSweep>
 __global__ void __launch_bounds__(kThreads)
-k_block_solve(const SubInfo* __restrict__ subs, const double* __restrict__ coef,
-              const double* __restrict__ scale, const T* __restrict__ Wall,
-              double* __restrict__ inout, double* __restrict__ out, long long nct,
-              const int* __restrict__ skip_flag) {
-    if (skip_flag && *skip_flag == 0) return;     // every column already converged
+k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SubInfo s = subs[blockIdx.x];
-    const int b = s.b, m = s.m, N = s.N;
-    T* Wsm = reinterpret_cast<T*>(smem_raw);       // b x b
-    T* Z = Wsm + b * b;                            // b x m, column major (Z[j*b + i])
-    T* Yp = Z + b * m;                             // previous slab's result
-    const double* cs = coef + 3 * nct + s.cell_off;
-    const double* sc = scale + s.cell_off;
+    const SubInfo s = g.subs[blockIdx.x];
+    const int b = s.b, m = s.m, N = s.N, su = s.su, nI = s.nI, mpad = g.mpad;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    T* Wsm = reinterpret_cast<T*>(smem_raw);                 // b x b (symmetric)
+    T* Z = Wsm + wstride(b);                                   // b x mpad, cell-major
+    T* Yp = Z + b * mpad;                                      // b x mpad: Y_{s-1} / x_{s+1}
+    double* nrm = reinterpret_cast<double*>(
+        smem_raw + ((sizeof(T) * ((size_t)wstride(b) + 2 * (size_t)b * mpad) + 15) & ~size_t(15)));
+    int* cols = reinterpret_cast<int*>(nrm + mpad);            // active columns
+    short* cf = reinterpret_cast<short*>(cols + mpad);         // Robin face per (cell, axis, side), -1 = none
+    __shared__ int na_s;
+
+    const double* cd = g.coef + s.cell_off;
+    const double* cu = g.coef + g.nct + s.cell_off;
+    const double* cv = g.coef + 2 * g.nct + s.cell_off;
+    const double* cs = g.coef + 3 * g.nct + s.cell_off;
+    Coupling<T, kScaled> cp;
+    if constexpr (kScaled) { cp.tsc = g.tsc + s.cell_off; cp.scf = g.scf + s.cell_off; }
+    else { cp.cs = cs; }
     const T* W = Wall + s.w_off;
-    double* io = inout + s.x_off;
-    double* ou = out + s.x_off;
-    const int groups = blockDim.x / b;             // b <= 128 so groups >= 2
-    const int i = threadIdx.x % b;
-    const int jg = threadIdx.x / b;
-    const bool active = jg < groups;
+    double* Xs = g.X + s.x_off;
+    T* Ys = reinterpret_cast<T*>(g.Ybuf) + s.x_off;
+    int* conv = g.conv + s.rhs_off;
+    const double vol = g.geo.h[0] * g.geo.h[1] * g.geo.h[2];
+
+    // active columns (deterministic compaction by one warp)
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            const int j = j0 + threadIdx.x;
+            const bool act = j < m && (!kSweep || conv[j] == 0);
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (act) cols[base + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
+            base += __popc(bal);
+        }
+        if (threadIdx.x == 0) na_s = base;
+    }
+    for (int e = threadIdx.x; e < 6 * N; e += blockDim.x) cf[e] = -1;
+    for (int e = threadIdx.x; e < mpad; e += blockDim.x) nrm[e] = 0.0;
+    __syncthreads();
+    const int na = na_s;
+    if (na == 0) return;
+    for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
+        const FaceInfo fi = g.faces[s.face_off + q];
+        cf[6 * fi.cell + 2 * fi.axis + (fi.s > 0 ? 1 : 0)] = (short)q;   // one face per cell side
+    }
+    __syncthreads();
 
     // ---- forward sweep
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wsm[e] = W[(long long)sl * b * b + e];
-        for (int e = threadIdx.x; e < b * m; e += blockDim.x) {
-            int j = e / b, ii = e - j * b;
-            double r = io[(long long)j * N + base + ii];
-            if (kScaled) r *= sc[base + ii];
-            if (sl > 0) {
-                double t = cs[base - b + ii];
-                if (kScaled) t *= sc[base - b + ii] * sc[base + ii];
-                r += t * (double)Yp[e];
+        // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
+        for (int jj = ty; jj < na; jj += 8) {
+            const int j = cols[jj];
+            const double* x = Xs + (long long)j * N;
+            double rr = 0.0;
+            for (int i = tx; i < b; i += 32) {
+                const int c = base + i;
+                double r;
+                if (j == m - 1) {
+                    int lc[3];
+                    local_coords(s, c, lc);
+                    r = g.rhs_dir[s.cell_off + c] + g.f[global_cell(s, lc, g.geo.n)] * vol;
+                } else {
+                    r = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) {
+                        const int q = cf[6 * c + a];
+                        if (q < 0) continue;
+                        const FaceInfo fi = g.faces[s.face_off + q];
+                        const double tr = g.face_tr[s.face_off + q];
+                        if (j == fi.col) r += tr;
+                        else if (j == nI + fi.col) r -= g.face_beta[s.face_off + q] * fi.s * tr;
+                    }
+                }
+                if (kSweep) {
+                    const int u = i % su;
+                    double ax = cd[c] * x[c];
+                    if (u + 1 < su) ax = fma(-cu[c], x[c + 1], ax);
+                    if (u > 0) ax = fma(-cu[c - 1], x[c - 1], ax);
+                    if (i + su < b) ax = fma(-cv[c], x[c + su], ax);
+                    if (i >= su) ax = fma(-cv[c - su], x[c - su], ax);
+                    if (c + b < N) ax = fma(-cs[c], x[c + b], ax);
+                    if (c >= b) ax = fma(-cs[c - b], x[c - b], ax);
+                    r -= ax;
+                }
+                rr = fma(r, r, rr);
+                T z = cp.in(r, c);
+                if (sl > 0) z += cp.t(c - b) * Yp[i * mpad + jj];
+                Z[i * mpad + jj] = z;
             }
-            Z[e] = (T)r;
+            for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
+            if (tx == 0) nrm[jj] += rr;          // column jj belongs to warp ty only: fixed order
         }
         __syncthreads();
-        if (active) {
-            for (int j0 = jg; j0 < m; j0 += groups * kMaxColsPerThread) {
-                T acc[kMaxColsPerThread];
-#pragma unroll
-                for (int q = 0; q < kMaxColsPerThread; ++q) acc[q] = (T)0;
-                for (int k = 0; k < b; ++k) {
-                    T w = Wsm[k * b + i];                       // W symmetric
-#pragma unroll
-                    for (int q = 0; q < kMaxColsPerThread; ++q) {
-                        int j = j0 + q * groups;
-                        if (j < m) acc[q] += w * Z[j * b + k];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kMaxColsPerThread; ++q) {
-                    int j = j0 + q * groups;
-                    if (j < m) {
-                        Yp[j * b + i] = acc[q];
-                        io[(long long)j * N + base + i] = (double)acc[q];
-                    }
-                }
-            }
-        }
+        block_gemm<T>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
+            Yp[i * mpad + jj] = v;
+            Ys[(long long)cols[jj] * N + base + i] = v;
+        });
         __syncthreads();
     }
-    // ---- backward sweep (Yp now holds x_{s+1} scratch)
+    // ---- backward sweep (Yp holds x_{s+1})
     for (int sl = s.ns - 1; sl >= 0; --sl) {
         const int base = sl * b;
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wsm[e] = W[(long long)sl * b * b + e];
-        for (int e = threadIdx.x; e < b * m; e += blockDim.x) {
-            int ii = e % b;
-            double v = 0.0;
-            if (sl < s.ns - 1) {
-                double t = cs[base + ii];
-                if (kScaled) t *= sc[base + ii] * sc[base + b + ii];
-                v = t * (double)Yp[e];
-            }
-            Z[e] = (T)v;
-        }
-        __syncthreads();
-        if (active) {
-            for (int j0 = jg; j0 < m; j0 += groups * kMaxColsPerThread) {
-                T acc[kMaxColsPerThread];
-#pragma unroll
-                for (int q = 0; q < kMaxColsPerThread; ++q) acc[q] = (T)0;
-                if (sl < s.ns - 1) {
-                    for (int k = 0; k < b; ++k) {
-                        T w = Wsm[k * b + i];
-#pragma unroll
-                        for (int q = 0; q < kMaxColsPerThread; ++q) {
-                            int j = j0 + q * groups;
-                            if (j < m) acc[q] += w * Z[j * b + k];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kMaxColsPerThread; ++q) {
-                    int j = j0 + q * groups;
-                    if (j < m) {
-                        long long gi = (long long)j * N + base + i;
-                        double x = io[gi] + (double)acc[q];      // Y_s + W_s (t o x_{s+1})
-                        Yp[j * b + i] = (T)x;
-                        double xo = kScaled ? x * sc[base + i] : x;
-                        if (kAccumulate) ou[gi] += xo; else ou[gi] = xo;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 residual R = B - A X of every MBF column (unscaled matrix), and the
-// per-subdomain count of columns with ||r||_2 > tol ||b||_2.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-k_residual(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
-           const double* __restrict__ coef, const double* __restrict__ face_tr,
-           const double* __restrict__ face_beta, const double* __restrict__ rhs_dir,
-           const double* __restrict__ f, Geo geo, const double* __restrict__ X,
-           double* __restrict__ R, long long nct, double tol, int* __restrict__ status) {
-    const SubInfo s = subs[blockIdx.x];
-    const int N = s.N, b = s.b, su = s.su, m = s.m;
-    const double* cd = coef + s.cell_off;
-    const double* cu = coef + nct + s.cell_off;
-    const double* cv = coef + 2 * nct + s.cell_off;
-    const double* cs = coef + 3 * nct + s.cell_off;
-    const double* Xs = X + s.x_off;
-    double* Rs = R + s.x_off;
-    const double vol = geo.h[0] * geo.h[1] * geo.h[2];
-    for (long long e = threadIdx.x; e < (long long)m * N; e += blockDim.x) {
-        int j = (int)(e / N);
-        int c = (int)(e - (long long)j * N);
-        const double* x = Xs + (long long)j * N;
-        int r = c % b;
-        int u = r % su;
-        double ax = cd[c] * x[c];
-        if (u + 1 < su) ax -= cu[c] * x[c + 1];
-        if (u > 0) ax -= cu[c - 1] * x[c - 1];
-        if (r + su < b) ax -= cv[c] * x[c + su];
-        if (r >= su) ax -= cv[c - su] * x[c - su];
-        if (c + b < N) ax -= cs[c] * x[c + b];
-        if (c >= b) ax -= cs[c - b] * x[c - b];
-        double bval = 0.0;
-        if (j == m - 1) {
-            int lc[3];
-            local_coords(s, c, lc);
-            bval = rhs_dir[s.cell_off + c] + f[global_cell(s, lc, geo.n)] * vol;
-        }
-        Rs[e] = bval - ax;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
-        FaceInfo fi = faces[s.face_off + q];
-        double tr = face_tr[s.face_off + q];
-        Rs[(long long)fi.col * N + fi.cell] += tr;
-        Rs[(long long)(s.nI + fi.col) * N + fi.cell] += -face_beta[s.face_off + q] * fi.s * tr;
-    }
-    __syncthreads();
-    // column norms: ||r_j||^2 vs ||b_j||^2 (b_j rebuilt from the faces / sources)
-    __shared__ double red_r[kThreads / 32], red_b[kThreads / 32];
-    __shared__ int nbad;
-    if (threadIdx.x == 0) nbad = 0;
-    __syncthreads();
-    for (int j = 0; j < m; ++j) {
-        double rr = 0.0, bb = 0.0;
-        for (int c = threadIdx.x; c < N; c += blockDim.x) { double v = Rs[(long long)j * N + c]; rr += v * v; }
-        if (j < 2 * s.nI) {
-            int col = j < s.nI ? j : j - s.nI;
-            for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
-                FaceInfo fi = faces[s.face_off + q];
-                if (fi.col != col) continue;
-                double tr = face_tr[s.face_off + q];
-                double v = j < s.nI ? tr : face_beta[s.face_off + q] * tr;
-                bb += v * v;
-            }
+        const bool last = sl == s.ns - 1;
+        auto finish = [&](int i, int jj, T acc) {
+            const int j = cols[jj];
+            const long long gi = (long long)j * N + base + i;
+            const T x = Ys[gi] + acc;
+            Yp[i * mpad + jj] = x;                 // Z, not Yp, feeds the product
+            const double xo = cp.out(x, base + i);
+            if (kSweep) Xs[gi] += xo; else Xs[gi] = xo;
+        };
+        if (!last) {
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wsm[e] = W[(long long)sl * b * b + e];
+            for (int jj = ty; jj < na; jj += 8)
+                for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = cp.t(base + i) * Yp[i * mpad + jj];
+            __syncthreads();
+            block_gemm<T>(Wsm, Z, b, na, mpad, finish);
         } else {
-            for (int c = threadIdx.x; c < N; c += blockDim.x) {
-                int lc[3];
-                local_coords(s, c, lc);
-                double v = rhs_dir[s.cell_off + c] + f[global_cell(s, lc, geo.n)] * vol;
-                bb += v * v;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            rr += __shfl_down_sync(0xffffffffu, rr, o);
-            bb += __shfl_down_sync(0xffffffffu, bb, o);
-        }
-        if ((threadIdx.x & 31) == 0) { red_r[threadIdx.x >> 5] = rr; red_b[threadIdx.x >> 5] = bb; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tr = 0.0, tb = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += red_r[w]; tb += red_b[w]; }
-            if (!(tr <= tol * tol * tb)) nbad += 1;
+            for (int jj = ty; jj < na; jj += 8)
+                for (int i = tx; i < b; i += 32) finish(i, jj, (T)0);
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && nbad) atomicAdd(&status[ST_UNCONVERGED], nbad);
+    // convergence bookkeeping
+    if (kSweep) {
+        __shared__ int nbad;
+        if (threadIdx.x == 0) nbad = 0;
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
+            const int j = cols[jj];
+            if (nrm[jj] <= g.tol2 * g.bnorm[s.rhs_off + j]) conv[j] = 1;
+            else atomicAdd(&nbad, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && nbad) atomicAdd(&g.status[ST_UNCONVERGED], nbad);
+    } else {
+        for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
+            const int j = cols[jj];
+            g.bnorm[s.rhs_off + j] = nrm[jj];
+            conv[j] = 0;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -509,8 +650,6 @@ Geo make_geo(const mrcm_config& c) {
     return g;
 }
 
-template <typename T>
-size_t solve_smem(int b, int m) { return sizeof(T) * ((size_t)b * b + 2 * (size_t)b * m); }
 
 }  // namespace
 
@@ -538,12 +677,17 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
         size_t sm = sizeof(double) * ((size_t)t.max_b * t.max_b + 2 * t.max_b);
         cudaFuncSetAttribute(k_block_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale, (double*)(ws + L.W),
-                                                                 status, t.n_cells, t.max_b));
+                                                                 status, t.n_cells, t.max_b, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
     } else {
+        if (t.max_b <= kRegMaxB) {
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<nsub, kRegMaxB, 0, st>>>(d.subs, coef, scale, (float*)(ws + L.W),
+                                                              status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+            return (int)cudaGetLastError();
+        }
         size_t sm = sizeof(float) * ((size_t)t.max_b * t.max_b + 2 * t.max_b);
         cudaFuncSetAttribute(k_block_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale, (float*)(ws + L.W),
-                                                               status, t.n_cells, t.max_b));
+                                                               status, t.n_cells, t.max_b, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
     }
     return (int)cudaGetLastError();
 }
@@ -553,40 +697,36 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     cudaStream_t st = (cudaStream_t)stream;
     const int nsub = (int)t.subs.size();
     Geo geo = make_geo(t.cfg);
-    double* X = (double*)(ws + L.X);
-    double* R = (double*)(ws + L.R);
-    double* coef = (double*)(ws + L.coef);
-    double* scale = (double*)(ws + L.scale);
     int* status = (int*)(ws + L.status);
-    MRCM_LAUNCH(P, "k_rhs", st, k_rhs<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
-                                    (double*)(ws + L.rhs_part), f, geo, X));
+    LocalArgs g;
+    g.subs = d.subs; g.faces = d.faces;
+    g.coef = (const double*)(ws + L.coef); g.scale = (const double*)(ws + L.scale);
+    g.scf = (const float*)(ws + L.scf); g.tsc = (const float*)(ws + L.tsc);
+    g.face_tr = (const double*)(ws + L.face_tr); g.face_beta = (const double*)(ws + L.face_beta);
+    g.rhs_dir = (const double*)(ws + L.rhs_part); g.f = f; g.geo = geo; g.nct = t.n_cells;
+    g.X = (double*)(ws + L.X); g.Ybuf = (void*)(ws + L.R);
+    g.conv = (int*)(ws + L.conv); g.bnorm = (double*)(ws + L.colnorm);
+    g.tol2 = tol * tol; g.status = status;
+    g.mpad = (t.max_m + 3) & ~3;
     if (precision == MRCM_FP64) {
-        size_t sm = solve_smem<double>(t.max_b, t.max_m);
-        cudaFuncSetAttribute(k_block_solve<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_block_solve", st, k_block_solve<double, false, false><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale,
-            (const double*)(ws + L.W), X, X, t.n_cells, nullptr));
+        size_t sm = local_smem_bytes<double>(t.max_b, g.mpad, t.max_N);
+        cudaFuncSetAttribute(k_local_solve<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        MRCM_LAUNCH(P, "k_local_solve", st, k_local_solve<double, false, false><<<nsub, kThreads, sm, st>>>(g, (const double*)(ws + L.W)));
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, 0));
     } else {
-        size_t sm = solve_smem<float>(t.max_b, t.max_m);
-        cudaFuncSetAttribute(k_block_solve<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_block_solve<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_block_solve", st, k_block_solve<float, true, false><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale,
-            (const float*)(ws + L.W), X, X, t.n_cells, nullptr));
-        for (int it = 0; it < sweeps; ++it) {
-            MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
-            MRCM_LAUNCH(P, "k_residual", st, k_residual<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, coef, (double*)(ws + L.face_tr),
-                (double*)(ws + L.face_beta), (double*)(ws + L.rhs_part), f, geo, X, R, t.n_cells, tol, status));
-            MRCM_LAUNCH(P, "k_block_solve", st, k_block_solve<float, true, true><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale,
-                (const float*)(ws + L.W), R, X, t.n_cells, status + ST_UNCONVERGED));
-        }
-        // final check of the refined columns
+        size_t sm = local_smem_bytes<float>(t.max_b, g.mpad, t.max_N);
+        cudaFuncSetAttribute(k_local_solve<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_local_solve<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        MRCM_LAUNCH(P, "k_local_solve", st, k_local_solve<float, true, false><<<nsub, kThreads, sm, st>>>(g, (const float*)(ws + L.W)));
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
-        MRCM_LAUNCH(P, "k_residual", st, k_residual<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, coef, (double*)(ws + L.face_tr),
-            (double*)(ws + L.face_beta), (double*)(ws + L.rhs_part), f, geo, X, R, t.n_cells, tol, status));
+        for (int it = 0; it < sweeps; ++it) {
+            if (it + 1 == sweeps) MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
+            MRCM_LAUNCH(P, "k_ir_sweep", st, k_local_solve<float, true, true><<<nsub, kThreads, sm, st>>>(g, (const float*)(ws + L.W)));
+        }
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, sweeps));
     }
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
-                                        X, geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+                                        (const double*)(ws + L.X), geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
     return (int)cudaGetLastError();
 }
 

@@ -230,6 +230,7 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         s.w_off = w_off;        w_off += (long long)s.ns * s.b * s.b;
         s.el_off = el_off;      el_off += (long long)s.el_dim * s.el_dim;
         s.elb_off = elb_off;    elb_off += s.el_dim;
+        s.rhs_off = (int)t.total_rhs;
         t.max_m = std::max(t.max_m, s.m);
         t.max_b = std::max(t.max_b, s.b);
         t.max_el = std::max(t.max_el, s.el_dim);
@@ -303,9 +304,12 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
             for (int kk = 0; kk < f.ne; ++kk) {
                 double rem = f.n - kk - 1;
                 t.front_flops += rem + 2.0 * rem * rem;
+                t.ldl_flops += rem + rem * (rem + 1.0);
             }
             std::unordered_map<int, int> pos;
             for (int q = 0; q < f.n; ++q) pos[t.front_dofs[f.e_dof_off + q]] = q;
+            f.inv_off = (int)t.front_inv.size();
+            t.front_inv.resize(t.front_inv.size() + 2 * (size_t)f.n, -1);
             for (int ci = 0; ci < 2; ++ci) {
                 int c = f.child[ci];
                 f.map_off[ci] = (int)t.front_maps.size();
@@ -319,6 +323,8 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
                     for (int q = cf.ne; q < cf.n; ++q) t.front_maps.push_back(pos.at(t.front_dofs[cf.e_dof_off + q]));
                     f.map_len[ci] = cf.nb;
                 }
+                for (int q = 0; q < f.map_len[ci]; ++q)
+                    t.front_inv[f.inv_off + (size_t)ci * f.n + t.front_maps[f.map_off[ci] + q]] = q;
             }
             if (!t.has_dirichlet && t.NV > 0) {
                 auto it = pos.find(0);
@@ -340,12 +346,14 @@ void compute_layout(const Tables& t, Layout& L) {
     const size_t nc = (size_t)t.n_cells;
     L.coef = take(4 * nc * sizeof(double));
     L.scale = take(nc * sizeof(double));
+    L.scf = take(nc * sizeof(float));
+    L.tsc = take(nc * sizeof(float));
     L.rhs_part = take(nc * sizeof(double));
     L.face_tr = take(t.faces.size() * sizeof(double));
     L.face_beta = take(t.faces.size() * sizeof(double));
     L.W = take((size_t)t.total_w * sizeof(double));
     L.X = take((size_t)t.total_x * sizeof(double));
-    L.R = take(t.cfg.precision == MRCM_FP64 ? 0 : (size_t)t.total_x * sizeof(double));
+    L.R = take(t.cfg.precision == MRCM_FP64 ? (size_t)t.total_x * sizeof(double) : (size_t)t.total_x * sizeof(float));
     L.colnorm = take((size_t)t.total_rhs * 2 * sizeof(double));
     L.conv = take((size_t)t.total_rhs * sizeof(int));
     L.elem = take((size_t)t.total_el * sizeof(double));
@@ -355,6 +363,11 @@ void compute_layout(const Tables& t, Layout& L) {
     L.dscale = take((size_t)2 * t.NV * sizeof(double));
     L.fronts = take((size_t)t.total_front * sizeof(double));
     L.frhs = take((size_t)t.total_frhs * sizeof(double));
+    {
+        size_t maxcnt = 1;
+        for (const auto& lv : t.levels) maxcnt = std::max(maxcnt, lv.size());
+        L.panel = take(maxcnt * 32 * 32 * sizeof(double));
+    }
     L.xres = take((size_t)2 * t.NV * sizeof(double));
     L.xtmp = take((size_t)2 * t.NV * sizeof(double));
     L.psum = take(((size_t)t.subs.size() + 64) * sizeof(double));

@@ -25,6 +25,7 @@ CASES = {
                    beta_mode=BETA_ALPHA_H_OVER_K, alpha=0.7),
     "aniso_h": dict(n=(8, 4, 4), edges=([2, 3, 3], [4], [2, 2]), patch=((1, 2), (1, 1), (3, 1)),
                     beta_const=0.3, h=(0.5, 1.0, 2.0)),
+    "thin": dict(n=(9, 6, 4), edges=([3, 1, 5], [2, 4], [1, 3]), patch=((1, 2), (2, 1), (2, 2))),
     "many_tiles": dict(n=(24, 20, 12), edges=([6, 6, 7, 5], [5, 5, 5, 5], [4, 4, 4]),
                        patch=((3, 2), (2, 2), (3, 5)), sigma=2.0, lam=4.0),
 }
