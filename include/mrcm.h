@@ -94,7 +94,8 @@ enum {
  *  ir_max_sweeps      refinement sweeps after the first solve (mixed modes)
  *  ir_tol             per-column stop: ||r||_2 <= ir_tol * ||b||_2
  *  wave_bytes         reserved (memory budget for streamed waves); 0
- *  tune_cache         reserved (autotuner cache path); may be NULL        */
+ *  tune_cache         path of the autotuner cache (text), or NULL; read at
+ *                     the first device call, written by mrcm_autotune      */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -124,11 +125,12 @@ typedef struct {
     int n_fronts;               /* internal nodes of the interface elimination tree */
     int max_front;              /* largest dense front */
     double front_flops;         /* flops of an LU of the same fronts (2x the LDL^T) */
-    double local_factor_flops;  /* flops of all local block factorisations */
+    double local_factor_flops;  /* sum of N_l b_l^2: band-Cholesky flops of the local factors */
     double local_solve_flops;   /* flops of one solve sweep over all MBF columns */
     int max_block;              /* largest slab block size b */
     long long mbf_entries;      /* sum over l of m_l * N_l (MBF array length) */
     double ldl_flops;           /* flops of the interface LDL^T (lower triangle) */
+    double ldl_update_flops;    /* part of ldl_flops in the trailing (Schur) updates */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;
@@ -191,11 +193,36 @@ mrcm_status mrcm_solve_interface(mrcm_handle* h, double* X, void* ws, void* stre
 mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double* u,
                              double* mass_residual_max, void* ws, void* stream);
 
+/* The whole pressure solve: mrcm_factor_local, mrcm_solve_mbf,
+ * mrcm_assemble_interface, mrcm_solve_interface and mrcm_reconstruct in
+ * order (arguments as there).  With flags & MRCM_SOLVE_GRAPH the sequence is
+ * captured into a CUDA graph on the first call (stream must not be NULL; the
+ * library's one-time device set-up runs before the capture) and replayed by
+ * later calls with the same pointers, workspace size and stream; changing any
+ * of them re-captures. */
+enum { MRCM_SOLVE_GRAPH = 1 };
+mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                       double* mass_residual_max, void* ws, size_t ws_bytes, void* stream, int flags);
+
+/* Autotuner (run after mrcm_factor_local): times every variant of the local
+ * solve kernels (threads per CTA x rows per thread of the block products) on
+ * this problem, keeps the fastest first-solve and refinement-sweep variants
+ * for the handle, and appends them to cfg.tune_cache when one was given (a
+ * later mrcm_setup with the same cache and problem shape reuses them without
+ * tuning).  Overwrites the MBF array: call mrcm_solve_mbf afterwards. */
+mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
+                          int* sweep_variant);
+
 /* Device-side status of the last solve, read back synchronously: number of
  * non-positive local pivots, unconverged refinement columns, interface zero
  * pivots and the refinement sweeps used. */
 mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconverged,
                              int* interface_zero_pivots, int* sweeps_used);
+
+/* Work counters of the last solve, read back synchronously: MBF entries
+ * (cell x right-hand side) swept by the FP64-residual refinement sweeps, summed
+ * over sweeps (converged columns drop out of later sweeps). */
+mrcm_status mrcm_read_work(mrcm_handle* h, void* ws, long long* swept_entries);
 
 /* Copy device-resident intermediate results for inspection (device -> host,
  * synchronous).  what: 0 = A^int CSR values (nnz_interface doubles), 1 = b^int

@@ -46,7 +46,7 @@ class mrcm_sizes(C.Structure):
         ("nnz_interface", C.c_longlong), ("n_fronts", C.c_int), ("max_front", C.c_int),
         ("front_flops", C.c_double), ("local_factor_flops", C.c_double),
         ("local_solve_flops", C.c_double), ("max_block", C.c_int),
-        ("mbf_entries", C.c_longlong), ("ldl_flops", C.c_double),
+        ("mbf_entries", C.c_longlong), ("ldl_flops", C.c_double), ("ldl_update_flops", C.c_double),
     ]
 
 
@@ -62,7 +62,10 @@ SIGNATURES = {
     "mrcm_solve_interface": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrcm_reconstruct": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "mrcm_read_status": (C.c_int, [C.c_void_p, C.c_void_p] + [C.POINTER(C.c_int)] * 4),
+    "mrcm_read_work": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "mrcm_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t]),
+    "mrcm_solve": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7 + [C.c_size_t, C.c_void_p, C.c_int]),
+    "mrcm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mrcm_profile_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_longlong)]),
     "mrcm_destroy": (None, [C.c_void_p]),

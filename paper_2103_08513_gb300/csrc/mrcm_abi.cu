@@ -3,6 +3,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <string>
+#include <vector>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -32,8 +35,10 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
     return e;
 }
 
+void load_tune_cache(mrcm_handle* h);
+
 void free_device(mrcm::DeviceTables& d) {
-    void* ptrs[] = {d.subs, d.faces, d.Ilist, d.rowptr, d.colidx, d.src_lo, d.src_hi, d.rhs_src_lo,
+    void* ptrs[] = {d.subs, d.faces, d.Ilist, d.class_list, d.solve_list, d.rowptr, d.colidx, d.src_lo, d.src_hi, d.rhs_src_lo,
                     d.rhs_src_hi, d.fronts, d.front_maps, d.front_inv, d.front_dofs, d.level_ids};
     for (void* p : ptrs) if (p) cudaFree(p);
     d = mrcm::DeviceTables();
@@ -62,6 +67,9 @@ mrcm_status ensure_device(mrcm_handle* h, void* stream) {
     UP(subs, t.subs);
     UP(faces, t.faces);
     UP(Ilist, t.Ilist);
+    UP(class_list, t.class_list);
+    UP(solve_list, t.solve_list);
+    for (int q = 0; q < 3; ++q) d.class_off[q] = t.class_off[q];
     UP(rowptr, t.rowptr);
     UP(colidx, t.colidx);
     UP(src_lo, t.src_lo);
@@ -74,9 +82,64 @@ mrcm_status ensure_device(mrcm_handle* h, void* stream) {
     UP(front_dofs, t.front_dofs);
     UP(level_ids, lvl);
 #undef UP
+    int rc = mrcm::configure_local(t, d);
+    if (!rc) rc = mrcm::configure_interface(t, d);
+    if (!rc) rc = mrcm::configure_reconstruct(t);
+    if (rc) { free_device(d); return cuda_fail(h, (cudaError_t)rc, "kernel configuration"); }
+    load_tune_cache(h);
     d.device = dev;
     d.ready = true;
     return MRCM_OK;
+}
+
+std::string tune_key(const mrcm_handle* h) {
+    const Tables& t = h->t;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "n%lld_s%d_b%d_m%d_N%d_r%lld_p%d", t.n_cells, (int)t.subs.size(), t.max_b, t.max_m,
+             t.max_N, t.total_rhs, t.cfg.precision);
+    return buf;
+}
+
+// Tune cache: text lines "key solve_variant sweep_variant".
+void load_tune_cache(mrcm_handle* h) {
+    if (h->t.tune_cache.empty()) return;
+    FILE* fp = fopen(h->t.tune_cache.c_str(), "r");
+    if (!fp) return;
+    char key[256];
+    int v0, v1;
+    const std::string want = tune_key(h);
+    while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3) {
+        if (want == key && v0 >= 0 && v0 < 6 && v1 >= 0 && v1 < 6) {
+            h->d.solve_variant = v0;
+            h->d.sweep_variant = v1;
+        }
+    }
+    fclose(fp);
+}
+
+void store_tune_cache(mrcm_handle* h) {
+    if (h->t.tune_cache.empty()) return;
+    std::vector<std::string> keep;
+    const std::string want = tune_key(h);
+    if (FILE* fp = fopen(h->t.tune_cache.c_str(), "r")) {
+        char key[256];
+        int v0, v1;
+        while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3)
+            if (want != key) keep.push_back(std::string(key) + " " + std::to_string(v0) + " " + std::to_string(v1));
+        fclose(fp);
+    }
+    if (FILE* fp = fopen(h->t.tune_cache.c_str(), "w")) {
+        for (auto& line : keep) fprintf(fp, "%s\n", line.c_str());
+        fprintf(fp, "%s %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant);
+        fclose(fp);
+    }
+}
+
+void drop_graph(mrcm_handle* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
 }
 
 mrcm_status check_ws(mrcm_handle* h, const void* ws) {
@@ -107,9 +170,11 @@ mrcm_status mrcm_setup(const mrcm_config* cfg, mrcm_handle** out) {
             if (s.N > 4096) { st = MRCM_ERR_NOT_IMPLEMENTED; h->err = "subdomain larger than 4096 cells"; break; }
         }
     }
-    const size_t mpad = (size_t)((t.max_m + 3) & ~3);
-    size_t solve_smem = sizeof(double) * ((size_t)t.max_b * t.max_b + 4 + 3 * (size_t)t.max_b * mpad + 2 * mpad) +
-                        12 * (size_t)t.max_N + 64;
+    const int mpad = (t.max_m + 3) & ~3;
+    size_t solve_smem = 0;
+    for (const auto& sb : t.subs)
+        solve_smem = std::max(solve_smem, t.cfg.precision == MRCM_FP64 ? mrcm::solve_smem_layout<double>(sb.b, mpad, sb.N).total
+                                                                          : mrcm::solve_smem_layout<float>(sb.b, mpad, sb.N).total);
     if (st == MRCM_OK && solve_smem > 227 * 1024) {
         st = MRCM_ERR_NOT_IMPLEMENTED;
         h->err = "slab block and right-hand-side count exceed shared memory";
@@ -150,6 +215,7 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
     o->max_block = t.max_b;
     o->mbf_entries = t.total_x;
     o->ldl_flops = t.ldl_flops;
+    o->ldl_update_flops = t.ldl_update_flops;
     return MRCM_OK;
 }
 
@@ -243,6 +309,18 @@ mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconv
     return MRCM_OK;
 }
 
+mrcm_status mrcm_read_work(mrcm_handle* h, void* ws, long long* swept) {
+    if (!h || !swept) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpy(&v, (char*)ws + h->lay.status + mrcm::ST_SWEPT * sizeof(int), sizeof(v),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_read_work");
+    *swept = (long long)v;
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_export(mrcm_handle* h, void* ws, int what, int sub, void* dst, size_t bytes) {
     if (!h || !dst) return MRCM_ERR_INVALID_ARG;
     mrcm_status st = check_ws(h, ws);
@@ -292,6 +370,77 @@ mrcm_status mrcm_export(mrcm_handle* h, void* ws, int what, int sub, void* dst, 
     return MRCM_OK;
 }
 
+mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
+                          int* sweep_variant) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (!f) return fail(h, MRCM_ERR_INVALID_ARG, "f is NULL");
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
+    int v0 = 0, v1 = 0;
+    float ms[16];
+    int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, ms);
+    if ((st = after_launch(h, rc, "mrcm_autotune")) != MRCM_OK) return st;
+    h->d.solve_variant = v0;
+    h->d.sweep_variant = v1;
+    drop_graph(h);                       // a captured graph holds the old variants
+    store_tune_cache(h);
+    h->stage = 1;                        // the tuning runs overwrote the MBF array
+    if (solve_variant) *solve_variant = v0;
+    if (sweep_variant) *sweep_variant = v1;
+    return MRCM_OK;
+}
+
+static mrcm_status run_all(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                           double* mres, void* ws, size_t ws_bytes, void* stream) {
+    mrcm_status st;
+    if ((st = mrcm_factor_local(h, K, ws, ws_bytes, stream)) != MRCM_OK) return st;
+    if ((st = mrcm_solve_mbf(h, f, ws, stream)) != MRCM_OK) return st;
+    if ((st = mrcm_assemble_interface(h, ws, stream)) != MRCM_OK) return st;
+    if ((st = mrcm_solve_interface(h, X, ws, stream)) != MRCM_OK) return st;
+    return mrcm_reconstruct(h, X, p, u, mres, ws, stream);
+}
+
+mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                       double* mres, void* ws, size_t ws_bytes, void* stream, int flags) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (!(flags & MRCM_SOLVE_GRAPH)) return run_all(h, K, f, X, p, u, mres, ws, ws_bytes, stream);
+    if (!stream) return fail(h, MRCM_ERR_INVALID_ARG, "graph mode needs a non-default stream");
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (ws_bytes < h->lay.total) return fail(h, MRCM_ERR_OOM, "workspace smaller than mrcm_query_workspace");
+    if ((st = ensure_device(h, stream)) != MRCM_OK) return st;
+    const void* key[9] = {K, f, X, p, u, mres, ws, stream, (const void*)(size_t)ws_bytes};
+    bool same = h->graph_exec != nullptr;
+    for (int i = 0; i < 9 && same; ++i) same = key[i] == h->graph_key[i];
+    cudaError_t e;
+    if (!same) {
+        drop_graph(h);
+        const bool prof = h->prof.on;
+        h->prof.on = false;
+        const long long n0 = h->prof.launches;
+        e = cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { h->prof.on = prof; return cuda_fail(h, e, "cudaStreamBeginCapture"); }
+        mrcm_status rs = run_all(h, K, f, X, p, u, mres, ws, ws_bytes, stream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture((cudaStream_t)stream, &g);
+        h->prof.on = prof;
+        h->graph_launches = h->prof.launches - n0;
+        h->prof.launches = n0;
+        if (rs != MRCM_OK) { if (g) cudaGraphDestroy(g); return rs; }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        h->graph = g;
+        e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        if (e != cudaSuccess) { drop_graph(h); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+        for (int i = 0; i < 9; ++i) h->graph_key[i] = key[i];
+    }
+    e = cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    h->prof.launches += h->graph_launches;
+    h->stage = 4;
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_profile(mrcm_handle* h, int enable) {
     if (!h) return MRCM_ERR_INVALID_ARG;
     h->prof.reset();
@@ -336,6 +485,7 @@ mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long
 void mrcm_destroy(mrcm_handle* h) {
     if (!h) return;
     h->prof.release();
+    drop_graph(h);
     free_device(h->d);
     delete h;
 }

@@ -466,16 +466,20 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
     }
 }
 
+int configure_interface(const Tables& t, DeviceTables& d) {
+    d.front_smem = sizeof(double) * (size_t)std::max(t.max_front, 1);
+    if (d.front_smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+        cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+    }
+    return (int)cudaGetLastError();
+}
+
 int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, double* X,
                            void* stream, Prof& P) {
     cudaStream_t st = (cudaStream_t)stream;
     const int nd = 2 * t.NV;
     if (nd == 0) return 0;
-    size_t sm = sizeof(double) * (size_t)std::max(t.max_front, 1);
-    if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    }
     const double* b = (const double*)(ws + L.b_int);
     const double* dscale = (const double*)(ws + L.dscale);
     double* r = (double*)(ws + L.xres);

@@ -9,7 +9,9 @@
 
 namespace mrcm {
 
-constexpr int kMaxBlock = 128;      // largest slab block b handled in shared memory
+constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
+constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
+constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
 
 // One subdomain.  Local cells are numbered slab-major: the slab axis `sa` is
@@ -63,6 +65,7 @@ struct FrontInfo {
 struct Tables {
     // configuration
     mrcm_config cfg;
+    std::string tune_cache;
     std::vector<int> cuts[3];
     int N[3];                      // subdomains per axis
     std::vector<int> starts[3];
@@ -72,6 +75,9 @@ struct Tables {
     std::vector<SubInfo> subs;
     std::vector<FaceInfo> faces;
     std::vector<int> Ilist;        // concatenated sorted I^l (global basis ids)
+    std::vector<int> class_list;   // subdomains grouped by factor class, costliest first
+    std::vector<int> solve_list;   // all subdomains, costliest solve first
+    int class_off[3] = {0, 0, 0};  // class 0: b <= kRegBlock, class 1: larger blocks
     long long n_cells = 0, total_x = 0, total_w = 0, total_el = 0;
     int total_elb = 0;
     int max_m = 0, max_b = 0, max_el = 0, max_N = 0;
@@ -95,7 +101,7 @@ struct Tables {
     long long total_front = 0;
     int total_frhs = 0;
     int max_front = 0;
-    double front_flops = 0, ldl_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
+    double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
     int pin_front = -1;
 };
@@ -111,6 +117,15 @@ struct DeviceTables {
     SubInfo* subs = nullptr;
     FaceInfo* faces = nullptr;
     int* Ilist = nullptr;
+    int* class_list = nullptr;
+    int class_off[3] = {0, 0, 0};
+    int* solve_list = nullptr;                 // all subdomains, costliest solve first
+    int sms = 0;
+    size_t solve_smem = 0;
+    int solve_occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int sweep_occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int solve_variant = 0, sweep_variant = 0;  // chosen by the autotuner (or the tune cache)
+    size_t front_smem = 0;
     int* rowptr = nullptr;
     int* colidx = nullptr;
     long long* src_lo = nullptr;
@@ -127,9 +142,44 @@ struct DeviceTables {
     bool ready = false;
 };
 
+// Shared-memory layout of k_local_solve: Z and Yp (b x mpad of T each, so
+// the column blocks stay 16-byte aligned for vector loads), column norms,
+// active columns, the per-cell Robin-face map (six sides per cell) and, for
+// blocks with b <= kSmemW, the staged block W_s (larger blocks are read from
+// global memory, where they stay L2-resident for the slab).
+constexpr int kSmemW = 128;
+
+struct SolveSmem {
+    size_t yp, nrm, cols, cf, w, total;
+};
+
+template <typename T>
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
+    SolveSmem L;
+    size_t x = sizeof(T) * (size_t)b * mpad;
+    L.yp = x;
+    x += sizeof(T) * (size_t)b * mpad;
+    x = (x + 15) & ~size_t(15);
+    L.nrm = x;
+    x += sizeof(double) * mpad;
+    L.cols = x;
+    x += sizeof(int) * mpad;
+    L.cf = x;
+    x += sizeof(short) * 6 * (size_t)N;
+    x = (x + 15) & ~size_t(15);
+    L.w = x;
+    if (b <= kSmemW) x += sizeof(T) * (size_t)b * b;
+    L.total = (x + 15) & ~size_t(15);
+    return L;
+}
+
 // Device status words at Layout::status.
 enum StatusWord { ST_NOT_SPD = 0, ST_UNCONVERGED = 1, ST_ZERO_PIVOT = 2, ST_SWEEPS = 3,
-                  ST_TIMEOUT = 4, ST_COUNT = 8 };
+                  ST_TIMEOUT = 4, ST_QUEUE = 5 /* work-queue counter */,
+                  ST_SWEPT = 8 /* 64-bit counter at words 8-9 */, ST_COUNT = 16 };
 
 }  // namespace mrcm
 
@@ -140,6 +190,10 @@ struct mrcm_handle {
     mrcm::Prof prof;
     std::string err;
     int stage = 0;     // 0 setup, 1 factored, 2 mbf, 3 assembled, 4 interface solved
+    cudaGraph_t graph = nullptr;          // captured solve (mrcm_solve with MRCM_SOLVE_GRAPH)
+    cudaGraphExec_t graph_exec = nullptr;
+    const void* graph_key[9] = {};
+    long long graph_launches = 0;
     const double* K = nullptr;   // caller's K (kept for reconstruction)
     const double* f = nullptr;   // caller's f
 };
@@ -160,6 +214,11 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
                               void* stream, Prof& P);
 int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                            double* X, void* stream, Prof& P);
+int configure_local(const Tables& t, DeviceTables& d);
+int configure_interface(const Tables& t, DeviceTables& d);
+int configure_reconstruct(const Tables& t);
+int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
+                   void* stream, int reps, int* best_solve, int* best_sweep, float* ms_out);
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P);

@@ -22,7 +22,9 @@
 // matrix drive iterative refinement.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "mrcm_internal.h"
 
@@ -129,92 +131,106 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
 
 // ---------------------------------------------------------------------------
 // Slab block factorisation: W_s = S_s^{-1} by in-place Gauss-Jordan on the
-// SPD block pivot (no pivoting needed for SPD).  One CTA per subdomain; the
-// running block lives in shared memory.
+// SPD block pivot (no pivoting needed for SPD), one CTA per subdomain.
+//
+// Gauss-Jordan on a symmetric matrix keeps M[i][j] = sigma_i sigma_j M[j][i]
+// with sigma = -1 on the indices already pivoted (the "sweep operator"), so
+// only the lower triangle is stored (packed, row i at i(i+1)/2) and updated:
+// step k, with r_j = M[k][j] read from the lower triangle and
+// c_i = M[i][k] = sigma_i r_i,
+//   M[i][j] -= c_i r_j / p  (i, j != k),  M[k][j] = r_j / p,
+//   M[i][k] = -c_i / p,  M[k][k] = 1 / p.
+// After the last pivot every sigma is -1 and the triangle holds S_s^{-1}.
+// W_s is written to global memory as a full b x b matrix.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline size_t packed_len(int b) { return (size_t)b * (b + 1) / 2; }
+
 template <typename T, bool kScaled>
 __global__ void __launch_bounds__(kThreads)
-k_block_factor(const SubInfo* __restrict__ subs, const double* __restrict__ coef,
+k_block_factor(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                const double* __restrict__ scale, T* __restrict__ Wall, int* __restrict__ status,
-               long long nct, int bmax, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
+               long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* A = reinterpret_cast<T*>(smem_raw);          // b x b, row major
-    T* col = A + bmax * bmax;                        // pivot column
-    T* row = col + bmax;                             // pivot row
-    const SubInfo s = subs[blockIdx.x];
+    const SubInfo s = subs[list[blockIdx.x]];
     const int b = s.b, su = s.su;
+    T* Lp = reinterpret_cast<T*>(smem_raw);                  // packed lower triangle
+    T* rk = Lp + ((packed_len(b) + 3) & ~size_t(3));           // row k
+    T* tv = rk + b;                                            // scaled couplings to the previous slab
     const double* cd = coef + s.cell_off;
     const double* cu = coef + nct + s.cell_off;
     const double* cv = coef + 2 * nct + s.cell_off;
     const double* cs = coef + 3 * nct + s.cell_off;
     const double* sc = scale + s.cell_off;
     T* W = Wall + s.w_off;
-    float* scf = scf_all + s.cell_off;
-    float* tsc = tsc_all + s.cell_off;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8 threads
     int bad = 0;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    for (int i = threadIdx.x; i < (int)packed_len(b); i += blockDim.x) Lp[i] = (T)0;
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
-        // S_s = D_s - diag(t) W_{s-1} diag(t), in place over W_{s-1}
+        for (int i = threadIdx.x; i < b; i += blockDim.x) {
+            const int c = base + i;
+            double t = 0.0;
+            if (sl > 0) t = cs[c - b] * (kScaled ? sc[c - b] * sc[c] : 1.0);
+            tv[i] = (T)t;
+            if (kScaled) {
+                scf_all[s.cell_off + c] = (float)sc[c];
+                tsc_all[s.cell_off + c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+            }
+        }
+        __syncthreads();
+        // S_s = D_s - t o W_{s-1} o t on the lower triangle
         for (int i = ty; i < b; i += 8) {
             const int ci = base + i;
             const int ui = i % su;
             const double si = kScaled ? sc[ci] : 1.0;
-            const double ti = sl > 0 ? cs[ci - b] * (kScaled ? sc[ci - b] * si : 1.0) : 0.0;
-            for (int j = tx; j < b; j += 32) {
+            T* row = Lp + packed_len(i);
+            for (int j = tx; j <= i; j += 32) {
                 const int cj = base + j;
                 double dij = 0.0;
                 if (i == j) dij = cd[ci];
-                else if (j == i + 1 && ui + 1 < su) dij = -cu[ci];
-                else if (i == j + 1 && ui > 0) dij = -cu[cj];
-                else if (j == i + su) dij = -cv[ci];
-                else if (i == j + su) dij = -cv[cj];
-                double v = dij;
-                if (kScaled) v *= si * sc[cj];
-                if (sl > 0) {
-                    const double tj = cs[cj - b] * (kScaled ? sc[cj - b] * sc[cj] : 1.0);
-                    v -= ti * tj * (double)A[i * b + j];
-                }
-                A[i * b + j] = (T)v;
+                if (i == j + 1 && ui > 0) dij = -cu[cj];
+                if (i == j + su) dij = -cv[cj];
+                if (kScaled) dij *= si * sc[cj];
+                row[j] = (T)(dij - (double)tv[i] * (double)tv[j] * (double)row[j]);
             }
         }
         __syncthreads();
-        // in-place Gauss-Jordan inversion (row k and column k saved separately:
-        // the intermediate matrices are not symmetric)
+        // sweep operator on the packed triangle
         for (int k = 0; k < b; ++k) {
-            for (int i = threadIdx.x; i < b; i += blockDim.x) { col[i] = A[i * b + k]; row[i] = A[k * b + i]; }
+            for (int j = threadIdx.x; j < b; j += blockDim.x) rk[j] = j <= k ? Lp[packed_len(k) + j] : Lp[packed_len(j) + k];
             __syncthreads();
-            T p = col[k];
+            T p = rk[k];
             if (!(p > (T)0)) { bad = 1; p = (T)1; }
             const T ip = (T)1 / p;
             for (int i = ty; i < b; i += 8) {
-                const T ci = col[i];
-                for (int j = tx; j < b; j += 32) {
+                const T ci = i < k ? -rk[i] : rk[i];
+                T* row = Lp + packed_len(i);
+                for (int j = tx; j <= i; j += 32) {
                     T v;
-                    if (i == k && j == k) v = ip;
-                    else if (i == k) v = row[j] * ip;
+                    if (i == k) v = j == k ? ip : rk[j] * ip;
                     else if (j == k) v = -ci * ip;
-                    else v = A[i * b + j] - ci * row[j] * ip;
-                    A[i * b + j] = v;
+                    else v = row[j] - ci * rk[j] * ip;
+                    row[j] = v;
                 }
             }
             __syncthreads();
         }
-        // W_s (symmetric)
+        // W_s as a full matrix (both triangles)
         T* Ws = W + (long long)sl * b * b;
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) Ws[e] = A[e];
-        if (kScaled) {
-            // FP32 copies for the solves: S and the scaled coupling t^ = t_s S_c S_{c+b}
-            for (int i = threadIdx.x; i < b; i += blockDim.x) {
-                const int c = base + i;
-                scf[c] = (float)sc[c];
-                tsc[c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+        for (int i = ty; i < b; i += 8) {
+            const T* row = Lp + packed_len(i);
+            for (int j = tx; j <= i; j += 32) {
+                Ws[(long long)i * b + j] = row[j];
+                Ws[(long long)j * b + i] = row[j];
             }
         }
         __syncthreads();
     }
     if (bad && threadIdx.x == 0) atomicAdd(&status[ST_NOT_SPD], 1);
 }
+
+template <typename T>
+size_t factor_smem(int b) { return sizeof(T) * (((packed_len(b) + 3) & ~size_t(3)) + 2 * (size_t)b); }
 
 // ---------------------------------------------------------------------------
 // Register-resident variant of the block factorisation for b <= 64 (FP32,
@@ -226,10 +242,10 @@ k_block_factor(const SubInfo* __restrict__ subs, const double* __restrict__ coef
 constexpr int kRegMaxB = 64;
 
 __global__ void __launch_bounds__(kRegMaxB)
-k_block_factor_reg(const SubInfo* __restrict__ subs, const double* __restrict__ coef,
+k_block_factor_reg(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                    const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
                    long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
-    const SubInfo s = subs[blockIdx.x];
+    const SubInfo s = subs[list[blockIdx.x]];
     const int b = s.b, su = s.su;
     const int i = threadIdx.x;
     const bool live = i < b;
@@ -353,30 +369,40 @@ __device__ __forceinline__ typename Vec4<T>::type ld4(const T* p) { return *rein
 
 // Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile 2 rows x 4 columns.
 // Results handed to `store(i, jj, value)`.
-template <typename T, typename Store>
+// Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile RT rows x 4
+// columns (rows i0, i0 + bh, ..., bh = ceil(b / RT)).  Results are handed to
+// `store(i, jj, value)`.
+template <typename T, int RT, typename Store>
 __device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* __restrict__ Z, int b, int na,
                                            int mpad, Store store) {
-    const int bh = (b + 1) >> 1;
+    const int bh = (b + RT - 1) / RT;
     const int mq = (na + 3) >> 2;
     for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
         const int i0 = task % bh, cq = task / bh;
-        const int i1 = i0 + bh;
-        const bool has1 = i1 < b;
-        T a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        T acc[RT][4];
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = (T)0;
         const T* zc = Z + 4 * cq;
         for (int k = 0; k < b; ++k) {
-            const T w0 = Wsm[k * b + i0];
-            const T w1 = has1 ? Wsm[k * b + i1] : (T)0;
             const typename Vec4<T>::type z = ld4(zc + k * mpad);
-            a0[0] += w0 * z.x; a0[1] += w0 * z.y; a0[2] += w0 * z.z; a0[3] += w0 * z.w;
-            a1[0] += w1 * z.x; a1[1] += w1 * z.y; a1[2] += w1 * z.z; a1[3] += w1 * z.w;
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const int i = i0 + r * bh;
+                const T w = i < b ? Wsm[k * b + i] : (T)0;
+                acc[r][0] += w * z.x; acc[r][1] += w * z.y; acc[r][2] += w * z.z; acc[r][3] += w * z.w;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int jj = 4 * cq + q;
             if (jj < na) {
-                store(i0, jj, a0[q]);
-                if (has1) store(i1, jj, a1[q]);
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    const int i = i0 + r * bh;
+                    if (i < b) store(i, jj, acc[r][q]);
+                }
             }
         }
     }
@@ -402,22 +428,10 @@ struct LocalArgs {
     double tol2;
     int* status;
     int mpad;             // row stride of the shared column blocks (multiple of 4)
+    const int* list;      // subdomains in processing order (costliest first)
+    int nlist;
+    int* queue;           // work-queue counter (reset to 0 before each launch)
 };
-
-// Shared-memory layout of k_local_solve: W (b*b rounded up to 4 elements, so
-// that the column blocks stay 16-byte aligned for vector loads), Z and Yp
-// (b x mpad of T each), column norms, active columns and the per-cell
-// Robin-face map (six sides per cell).
-__host__ __device__ inline int wstride(int b) { return (b * b + 3) & ~3; }
-
-template <typename T>
-__host__ __device__ inline size_t local_smem_bytes(int b, int mpad, int N) {
-    size_t x = (sizeof(T) * ((size_t)wstride(b) + 2 * (size_t)b * mpad) + 15) & ~size_t(15);
-    x += sizeof(double) * mpad;
-    x += sizeof(int) * mpad;
-    x += sizeof(short) * 6 * (size_t)N;
-    return (x + 15) & ~size_t(15);
-}
 
 // Coupling between slab cells c and c+b in the solve's arithmetic: the FP32
 // scaled value t^ in mixed mode, the FP64 transmissibility otherwise.
@@ -435,20 +449,21 @@ template <> struct Coupling<double, false> {
     __device__ double out(double x, int) const { return x; }
 };
 
-template <typename T, bool kScaled, bool kSweep>
-__global__ void __launch_bounds__(kThreads)
-k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SubInfo s = g.subs[blockIdx.x];
+template <typename T, bool kScaled, bool kSweep, int NT, int RT>
+__device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restrict__ Wall, int l,
+                                          unsigned char* smem_raw) {
+    constexpr int NY = NT / 32;
+    const SubInfo s = g.subs[l];
     const int b = s.b, m = s.m, N = s.N, su = s.su, nI = s.nI, mpad = g.mpad;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-    T* Wsm = reinterpret_cast<T*>(smem_raw);                 // b x b (symmetric)
-    T* Z = Wsm + wstride(b);                                   // b x mpad, cell-major
-    T* Yp = Z + b * mpad;                                      // b x mpad: Y_{s-1} / x_{s+1}
-    double* nrm = reinterpret_cast<double*>(
-        smem_raw + ((sizeof(T) * ((size_t)wstride(b) + 2 * (size_t)b * mpad) + 15) & ~size_t(15)));
-    int* cols = reinterpret_cast<int*>(nrm + mpad);            // active columns
-    short* cf = reinterpret_cast<short*>(cols + mpad);         // Robin face per (cell, axis, side), -1 = none
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x NY threads
+    const SolveSmem lay = solve_smem_layout<T>(b, mpad, N);
+    const bool wsm = b <= kSmemW;                              // stage W_s in shared memory
+    T* Z = reinterpret_cast<T*>(smem_raw);                     // b x mpad, cell-major
+    T* Yp = reinterpret_cast<T*>(smem_raw + lay.yp);           // b x mpad: Y_{s-1} / x_{s+1}
+    double* nrm = reinterpret_cast<double*>(smem_raw + lay.nrm);
+    int* cols = reinterpret_cast<int*>(smem_raw + lay.cols);   // active columns
+    short* cf = reinterpret_cast<short*>(smem_raw + lay.cf);   // Robin face per (cell, axis, side), -1 = none
+    T* Wst = reinterpret_cast<T*>(smem_raw + lay.w);           // staged b x b block (b <= kSmemW)
     __shared__ int na_s;
 
     const double* cd = g.coef + s.cell_off;
@@ -480,7 +495,7 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     for (int e = threadIdx.x; e < mpad; e += blockDim.x) nrm[e] = 0.0;
     __syncthreads();
     const int na = na_s;
-    if (na == 0) return;
+    if (na == 0) { __syncthreads(); return; }
     for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
         const FaceInfo fi = g.faces[s.face_off + q];
         cf[6 * fi.cell + 2 * fi.axis + (fi.s > 0 ? 1 : 0)] = (short)q;   // one face per cell side
@@ -490,9 +505,10 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     // ---- forward sweep
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wsm[e] = W[(long long)sl * b * b + e];
+        const T* Wsm = wsm ? Wst : W + (long long)sl * b * b;
+        if (wsm) for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wst[e] = W[(long long)sl * b * b + e];
         // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
-        for (int jj = ty; jj < na; jj += 8) {
+        for (int jj = ty; jj < na; jj += NY) {
             const int j = cols[jj];
             const double* x = Xs + (long long)j * N;
             double rr = 0.0;
@@ -535,7 +551,7 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
             if (tx == 0) nrm[jj] += rr;          // column jj belongs to warp ty only: fixed order
         }
         __syncthreads();
-        block_gemm<T>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
+        block_gemm<T, RT>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
             Yp[i * mpad + jj] = v;
             Ys[(long long)cols[jj] * N + base + i] = v;
         });
@@ -554,13 +570,14 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
             if (kSweep) Xs[gi] += xo; else Xs[gi] = xo;
         };
         if (!last) {
-            for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wsm[e] = W[(long long)sl * b * b + e];
-            for (int jj = ty; jj < na; jj += 8)
+            const T* Wsm = wsm ? Wst : W + (long long)sl * b * b;
+            if (wsm) for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wst[e] = W[(long long)sl * b * b + e];
+            for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = cp.t(base + i) * Yp[i * mpad + jj];
             __syncthreads();
-            block_gemm<T>(Wsm, Z, b, na, mpad, finish);
+            block_gemm<T, RT>(Wsm, Z, b, na, mpad, finish);
         } else {
-            for (int jj = ty; jj < na; jj += 8)
+            for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) finish(i, jj, (T)0);
         }
         __syncthreads();
@@ -568,7 +585,10 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     // convergence bookkeeping
     if (kSweep) {
         __shared__ int nbad;
-        if (threadIdx.x == 0) nbad = 0;
+        if (threadIdx.x == 0) {
+            nbad = 0;
+            atomicAdd(reinterpret_cast<unsigned long long*>(g.status + ST_SWEPT), (unsigned long long)na * N);
+        }
         __syncthreads();
         for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
             const int j = cols[jj];
@@ -583,6 +603,41 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
             g.bnorm[s.rhs_off + j] = nrm[jj];
             conv[j] = 0;
         }
+    }
+    __syncthreads();                              // shared memory is reused by the next subdomain
+}
+
+// Persistent local solve: CTAs pull subdomains from a device work queue over
+// the cost-ordered list until it is exhausted (no waits: a plain atomic counter).
+template <typename T, bool kScaled, bool kSweep, int NT, int RT>
+__global__ void __launch_bounds__(NT)
+k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(g.queue, 1);
+        __syncthreads();
+        const int it = item;
+        __syncthreads();
+        if (it >= g.nlist) break;
+        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it], smem_raw);
+    }
+}
+
+// Tunable variants of the local solve (threads per CTA x GEMM rows per thread).
+constexpr int kNumSolveVariants = 6;
+__host__ __device__ inline int variant_threads(int v) { return v < 3 ? 256 : 128; }
+__host__ __device__ inline int variant_rows(int v) { const int r[3] = {2, 1, 4}; return r[v % 3]; }
+
+template <typename T, bool kScaled, bool kSweep>
+const void* solve_kernel(int v) {
+    switch (v) {
+        case 0: return (const void*)k_local_solve<T, kScaled, kSweep, 256, 2>;
+        case 1: return (const void*)k_local_solve<T, kScaled, kSweep, 256, 1>;
+        case 2: return (const void*)k_local_solve<T, kScaled, kSweep, 256, 4>;
+        case 3: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 2>;
+        case 4: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 1>;
+        default: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 4>;
     }
 }
 
@@ -673,60 +728,166 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
                                              c.beta_const, bcm, blo, bhi, coef, scale,
                                              (double*)(ws + L.rhs_part), (double*)(ws + L.face_tr),
                                              (double*)(ws + L.face_beta), t.n_cells));
+    // size classes: register-resident factor for FP32 blocks with b <= 64, packed
+    // shared-memory factor otherwise; each class is one launch over its list
+    const int* lst_small = d.class_list + d.class_off[0];
+    const int* lst_large = d.class_list + d.class_off[1];
+    const int n_small = d.class_off[1] - d.class_off[0];
+    const int n_large = d.class_off[2] - d.class_off[1];
     if (precision == MRCM_FP64) {
-        size_t sm = sizeof(double) * ((size_t)t.max_b * t.max_b + 2 * t.max_b);
-        cudaFuncSetAttribute(k_block_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale, (double*)(ws + L.W),
-                                                                 status, t.n_cells, t.max_b, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        size_t sm = factor_smem<double>(t.max_b);
+        MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<nsub, kThreads, sm, st>>>(d.subs, d.class_list, coef, scale,
+            (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
     } else {
-        if (t.max_b <= kRegMaxB) {
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<nsub, kRegMaxB, 0, st>>>(d.subs, coef, scale, (float*)(ws + L.W),
-                                                              status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
-            return (int)cudaGetLastError();
+        if (n_small > 0)
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, lst_small, coef, scale,
+                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        if (n_large > 0) {
+            size_t sm = factor_smem<float>(t.max_b);
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, lst_large, coef, scale,
+                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
-        size_t sm = sizeof(float) * ((size_t)t.max_b * t.max_b + 2 * t.max_b);
-        cudaFuncSetAttribute(k_block_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<nsub, kThreads, sm, st>>>(d.subs, coef, scale, (float*)(ws + L.W),
-                                                               status, t.n_cells, t.max_b, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
     }
     return (int)cudaGetLastError();
+}
+
+static size_t solve_smem_bytes(const Tables& t, int precision) {
+    const int mpad = (t.max_m + 3) & ~3;
+    size_t sm = 0;
+    for (const SubInfo& sb : t.subs)
+        sm = std::max(sm, precision == MRCM_FP64 ? solve_smem_layout<double>(sb.b, mpad, sb.N).total
+                                                 : solve_smem_layout<float>(sb.b, mpad, sb.N).total);
+    return sm;
+}
+
+// One-time kernel configuration (dynamic shared memory limits, persistent
+// grid sizes); runs outside any stream capture.
+int configure_local(const Tables& t, DeviceTables& d) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool f64 = t.cfg.precision == MRCM_FP64;
+    d.solve_smem = solve_smem_bytes(t, t.cfg.precision);
+    for (int v = 0; v < kNumSolveVariants; ++v) {
+        const void* k0 = f64 ? solve_kernel<double, false, false>(v) : solve_kernel<float, true, false>(v);
+        const void* k1 = f64 ? solve_kernel<double, false, false>(v) : solve_kernel<float, true, true>(v);
+        cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.solve_smem);
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.solve_smem);
+        int occ0 = 0, occ1 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k0, variant_threads(v), d.solve_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k1, variant_threads(v), d.solve_smem);
+        d.solve_occ[v] = std::max(1, occ0);
+        d.sweep_occ[v] = std::max(1, occ1);
+    }
+    cudaFuncSetAttribute(k_block_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem<double>(std::min(t.max_b, kMaxBlock64)));
+    cudaFuncSetAttribute(k_block_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem<float>(t.max_b));
+    return (int)cudaGetLastError();
+}
+
+static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f) {
+    LocalArgs g;
+    g.subs = d.subs; g.faces = d.faces;
+    g.coef = (const double*)(ws + L.coef); g.scale = (const double*)(ws + L.scale);
+    g.scf = (const float*)(ws + L.scf); g.tsc = (const float*)(ws + L.tsc);
+    g.face_tr = (const double*)(ws + L.face_tr); g.face_beta = (const double*)(ws + L.face_beta);
+    g.rhs_dir = (const double*)(ws + L.rhs_part); g.f = f; g.geo = make_geo(t.cfg); g.nct = t.n_cells;
+    g.X = (double*)(ws + L.X); g.Ybuf = (void*)(ws + L.R);
+    g.conv = (int*)(ws + L.conv); g.bnorm = (double*)(ws + L.colnorm);
+    g.tol2 = 0.0; g.status = (int*)(ws + L.status);
+    g.mpad = (t.max_m + 3) & ~3;
+    g.list = d.solve_list; g.nlist = (int)t.subs.size();
+    g.queue = (int*)(ws + L.status) + ST_QUEUE;
+    return g;
+}
+
+// Launch one local-solve pass (first solve or refinement sweep) with variant v.
+static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs& g, const void* W, bool sweep,
+                              int v, cudaStream_t st, Prof& P) {
+    const bool f64 = t.cfg.precision == MRCM_FP64;
+    const void* k = f64 ? solve_kernel<double, false, false>(v)
+                        : (sweep ? solve_kernel<float, true, true>(v) : solve_kernel<float, true, false>(v));
+    const int occ = sweep ? d.sweep_occ[v] : d.solve_occ[v];
+    const int grid = std::max(1, std::min(g.nlist, d.sms * occ));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+    void* args[] = {(void*)&g, (void*)&W};
+    MRCM_LAUNCH(P, sweep ? "k_ir_sweep" : "k_local_solve", st,
+                cudaLaunchKernel(k, dim3(grid), dim3(variant_threads(v)), args, d.solve_smem, st));
 }
 
 int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                      const double* f, int precision, int sweeps, double tol, void* stream, Prof& P) {
     cudaStream_t st = (cudaStream_t)stream;
     const int nsub = (int)t.subs.size();
-    Geo geo = make_geo(t.cfg);
     int* status = (int*)(ws + L.status);
-    LocalArgs g;
-    g.subs = d.subs; g.faces = d.faces;
-    g.coef = (const double*)(ws + L.coef); g.scale = (const double*)(ws + L.scale);
-    g.scf = (const float*)(ws + L.scf); g.tsc = (const float*)(ws + L.tsc);
-    g.face_tr = (const double*)(ws + L.face_tr); g.face_beta = (const double*)(ws + L.face_beta);
-    g.rhs_dir = (const double*)(ws + L.rhs_part); g.f = f; g.geo = geo; g.nct = t.n_cells;
-    g.X = (double*)(ws + L.X); g.Ybuf = (void*)(ws + L.R);
-    g.conv = (int*)(ws + L.conv); g.bnorm = (double*)(ws + L.colnorm);
-    g.tol2 = tol * tol; g.status = status;
-    g.mpad = (t.max_m + 3) & ~3;
+    LocalArgs g = local_args(t, d, L, ws, f);
+    g.tol2 = tol * tol;
+    const void* W = (const void*)(ws + L.W);
+    launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
     if (precision == MRCM_FP64) {
-        size_t sm = local_smem_bytes<double>(t.max_b, g.mpad, t.max_N);
-        cudaFuncSetAttribute(k_local_solve<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_local_solve", st, k_local_solve<double, false, false><<<nsub, kThreads, sm, st>>>(g, (const double*)(ws + L.W)));
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, 0));
     } else {
-        size_t sm = local_smem_bytes<float>(t.max_b, g.mpad, t.max_N);
-        cudaFuncSetAttribute(k_local_solve<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_local_solve<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        MRCM_LAUNCH(P, "k_local_solve", st, k_local_solve<float, true, false><<<nsub, kThreads, sm, st>>>(g, (const float*)(ws + L.W)));
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
         for (int it = 0; it < sweeps; ++it) {
             if (it + 1 == sweeps) MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
-            MRCM_LAUNCH(P, "k_ir_sweep", st, k_local_solve<float, true, true><<<nsub, kThreads, sm, st>>>(g, (const float*)(ws + L.W)));
+            launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
         }
         MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, sweeps));
     }
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
-                                        (const double*)(ws + L.X), geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+    return (int)cudaGetLastError();
+}
+
+// Autotuner: time every local-solve variant on this problem (first solve and
+// one refinement sweep, median of `reps` runs) and return the fastest pair.
+int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
+                   void* stream, int reps, int* best_solve, int* best_sweep, float* ms_out) {
+    cudaStream_t st = (cudaStream_t)stream;
+    LocalArgs g = local_args(t, d, L, ws, f);
+    g.tol2 = 0.0;        // nothing retires: every sweep does the full work
+    const void* W = (const void*)(ws + L.W);
+    Prof dummy;
+    const bool mixed = t.cfg.precision != MRCM_FP64;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best0 = 1e30f, best1 = 1e30f;
+    *best_solve = 0;
+    *best_sweep = 0;
+    for (int v = 0; v < kNumSolveVariants; ++v) {
+        std::vector<float> t0, t1;
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(e0, st);
+            launch_local_pass(t, d, g, W, false, v, st, dummy);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t0.push_back(ms);
+            if (mixed) {
+                cudaEventRecord(e0, st);
+                launch_local_pass(t, d, g, W, true, v, st, dummy);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                t1.push_back(ms);
+            }
+        }
+        std::sort(t0.begin(), t0.end());
+        const float m0 = t0[t0.size() / 2];
+        if (ms_out) ms_out[2 * v] = m0;
+        if (m0 < best0) { best0 = m0; *best_solve = v; }
+        if (mixed) {
+            std::sort(t1.begin(), t1.end());
+            const float m1 = t1[t1.size() / 2];
+            if (ms_out) ms_out[2 * v + 1] = m1;
+            if (m1 < best1) { best1 = m1; *best_sweep = v; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return (int)cudaGetLastError();
 }
 

@@ -165,6 +165,12 @@ __global__ void k_zero_u64(unsigned long long* x) { *x = 0ull; }
 
 }  // namespace
 
+int configure_reconstruct(const Tables& t) {
+    cudaFuncSetAttribute(k_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * ((size_t)kMaxCells + t.max_m)));
+    return (int)cudaGetLastError();
+}
+
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P) {
@@ -186,7 +192,6 @@ int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, 
     unsigned long long* mbits = (unsigned long long*)(psum + nsub + 1);
     MRCM_LAUNCH(P, "k_zero_u64", st, k_zero_u64<<<1, 1, 0, st>>>(mbits));
     size_t sm = sizeof(double) * ((size_t)kMaxCells + t.max_m);
-    cudaFuncSetAttribute(k_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     MRCM_LAUNCH(P, "k_reconstruct", st, k_reconstruct<<<nsub, kThreads, sm, st>>>(d.subs, d.faces, d.Ilist, t.NV, (const double*)(ws + L.X), X,
                                              (const double*)(ws + L.coef), (const double*)(ws + L.face_tr),
                                              (const double*)(ws + L.face_beta), K, f, geo, t.n_cells, p, u,

@@ -86,6 +86,8 @@ struct TreeBuilder {
 mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
     if (!cfg) { err = "config is NULL"; return MRCM_ERR_INVALID_ARG; }
     t.cfg = *cfg;
+    if (cfg->tune_cache) t.tune_cache = cfg->tune_cache;
+    t.cfg.tune_cache = nullptr;
     const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
     const double hh[3] = {cfg->hx, cfg->hy, cfg->hz};
     for (int a = 0; a < 3; ++a) {
@@ -146,8 +148,9 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
                 s.b = s.su * s.sv;
                 s.ns = s.sz[sa];
                 s.N = s.b * s.ns;
-                if (s.b > kMaxBlock) {
-                    err = "subdomain slab block " + std::to_string(s.b) + " exceeds " + std::to_string(kMaxBlock);
+                const int bmax = cfg->precision == MRCM_FP64 ? kMaxBlock64 : kMaxBlock;
+                if (s.b > bmax) {
+                    err = "subdomain slab block " + std::to_string(s.b) + " exceeds " + std::to_string(bmax);
                     return MRCM_ERR_NOT_IMPLEMENTED;
                 }
             }
@@ -236,8 +239,31 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         t.max_el = std::max(t.max_el, s.el_dim);
         t.max_N = std::max(t.max_N, s.N);
         t.total_rhs += s.m;
-        t.local_factor_flops += (double)s.ns * (2.0 * s.b * s.b * s.b + 3.0 * s.b * s.b);
+        t.local_factor_flops += (double)s.N * s.b * s.b;    // banded-Cholesky count of the block factor
         t.local_solve_flops += 4.0 * s.N * (double)s.b * s.m;
+    }
+    // factor classes (register-resident FP32 factor for small blocks), costliest first
+    {
+        std::vector<std::pair<double, int>> c0, c1;
+        for (int l = 0; l < nsub; ++l) {
+            const SubInfo& s = t.subs[l];
+            double cost = (double)s.ns * s.b * s.b * s.b;
+            if (cfg->precision != MRCM_FP64 && s.b <= kRegBlock) c0.push_back({-cost, l}); else c1.push_back({-cost, l});
+        }
+        std::sort(c0.begin(), c0.end());
+        std::sort(c1.begin(), c1.end());
+        for (auto& pr : c0) t.class_list.push_back(pr.second);
+        for (auto& pr : c1) t.class_list.push_back(pr.second);
+        t.class_off[0] = 0;
+        t.class_off[1] = (int)c0.size();
+        t.class_off[2] = (int)(c0.size() + c1.size());
+        std::vector<std::pair<double, int>> sl;
+        for (int l = 0; l < nsub; ++l) {
+            const SubInfo& s = t.subs[l];
+            sl.push_back({-(double)s.N * s.b * s.m, l});
+        }
+        std::sort(sl.begin(), sl.end());
+        for (auto& pr : sl) t.solve_list.push_back(pr.second);
     }
     t.total_x = x_off;
     t.total_w = w_off;
@@ -301,6 +327,11 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
             f.f_off = foff;  foff += (long long)f.n * f.n;
             f.r_off = roff;  roff += f.n;
             t.max_front = std::max(t.max_front, f.n);
+            for (int k0 = 0; k0 < f.ne; k0 += 32) {
+                const double nbk = std::min(32, f.ne - k0);
+                const double mrem = f.n - k0 - nbk;
+                t.ldl_update_flops += nbk * mrem * (mrem + 1.0);
+            }
             for (int kk = 0; kk < f.ne; ++kk) {
                 double rem = f.n - kk - 1;
                 t.front_flops += rem + 2.0 * rem * rem;

@@ -32,7 +32,7 @@ class MRCM:
 
     def __init__(self, n, edges, patch=((0, 0),) * 3, h=(1.0, 1.0, 1.0), beta_mode=0, alpha=1.0,
                  beta_const=1.0, bc_type=((0, 0),) * 3, bc_value=((0.0, 0.0),) * 3,
-                 precision="fp64", ir_max_sweeps=4, ir_tol=1e-14, device=None, allocate=True):
+                 precision="fp64", ir_max_sweeps=4, ir_tol=1e-14, device=None, allocate=True, tune_cache=None):
         self.lib = L.load()
         cfg = L.mrcm_config()
         cfg.nx, cfg.ny, cfg.nz = (int(v) for v in n)
@@ -53,7 +53,8 @@ class MRCM:
         cfg.ir_max_sweeps = int(ir_max_sweeps)
         cfg.ir_tol = float(ir_tol)
         cfg.wave_bytes = 0
-        cfg.tune_cache = None
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        cfg.tune_cache = self._tune_cache
         self.cfg = cfg
         self.n = tuple(int(v) for v in n)
         h_ = C.c_void_p()
@@ -124,8 +125,27 @@ class MRCM:
                                           _stream(stream)), self.handle)
         return p, u, mres
 
-    def solve(self, K, f, out=None, stream=None):
-        """All five device steps of one MRCM pressure solve; returns (p, u, X, mres)."""
+    def outputs(self):
+        """Preallocated (X, p, u, mres) device buffers for solve(..., out=...)."""
+        nx, ny, nz = self.n
+        return (torch.empty(max(self.n_interface, 1), dtype=torch.float64, device=self.device),
+                torch.empty((nz, ny, nx), dtype=torch.float64, device=self.device),
+                torch.empty((6, nz, ny, nx), dtype=torch.float64, device=self.device),
+                torch.empty(1, dtype=torch.float64, device=self.device))
+
+    def solve(self, K, f, out=None, stream=None, graph=False):
+        """All five device steps of one MRCM pressure solve; returns (p, u, X, mres).
+
+        graph=True runs mrcm_solve in CUDA-graph mode (captured on the first call,
+        replayed afterwards); it needs a non-default stream.
+        """
+        if graph:
+            assert K.is_contiguous() and f.is_contiguous()
+            X, p, u, mres = out if out is not None else self.outputs()
+            self._K, self._f = K, f
+            L.check(self.lib.mrcm_solve(self.handle, _ptr(K), _ptr(f), _ptr(X), _ptr(p), _ptr(u), _ptr(mres),
+                                        self.ws_ptr, C.c_size_t(self.ws_bytes), _stream(stream), 1), self.handle)
+            return p, u, X, mres
         self.factor_local(K, stream)
         self.solve_mbf(f, stream)
         self.assemble_interface(stream)
@@ -137,6 +157,13 @@ class MRCM:
             self.solve_interface(X, stream=stream)
             self.reconstruct(X, p, u, mres, stream=stream)
         return p, u, X, mres
+
+    def autotune(self, f, stream=None):
+        """Pick the fastest local-solve kernel variants for this problem (after factor_local)."""
+        v0, v1 = C.c_int(), C.c_int()
+        L.check(self.lib.mrcm_autotune(self.handle, _ptr(f), self.ws_ptr, _stream(stream), C.byref(v0),
+                                       C.byref(v1)), self.handle)
+        return int(v0.value), int(v1.value)
 
     # ------------------------------------------------------------------ profiling
     def profile(self, enable=True):
@@ -160,6 +187,12 @@ class MRCM:
         code = self.lib.mrcm_read_status(self.handle, self.ws_ptr, *[C.byref(x) for x in v])
         return code, {"not_spd": v[0].value, "unconverged": v[1].value, "interface_zero_pivots": v[2].value,
                       "sweeps": v[3].value}
+
+    def read_work(self):
+        """MBF entries swept by the refinement sweeps of the last solve."""
+        v = C.c_longlong()
+        L.check(self.lib.mrcm_read_work(self.handle, self.ws_ptr, C.byref(v)), self.handle)
+        return int(v.value)
 
     def basis(self, i):
         v = [C.c_int() for _ in range(4)]

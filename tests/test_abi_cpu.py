@@ -115,6 +115,21 @@ def test_c2_sizes(lib):
     lib.mrcm_destroy(h)
 
 
+def test_c3_uneven_setup(lib):
+    from paper_2103_08513_gb300._lib import mrcm_sizes
+    w = workload("c3")
+    cfg, keep = _cfg(w, precision=1)
+    h = C.c_void_p()
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 0, lib.mrcm_last_error(None)
+    sz = mrcm_sizes()
+    lib.mrcm_query_sizes(h, C.byref(sz))
+    assert sz.n_sub == w.n_sub and sz.max_block == 256
+    lib.mrcm_destroy(h)
+    # the FP64 factor keeps its packed block in shared memory: 16x16 slabs do not fit
+    cfg, keep = _cfg(w, precision=0)
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 8
+
+
 def test_setup_rejects_bad_configs(lib):
     w = small()
     cfg, keep = _cfg(w)

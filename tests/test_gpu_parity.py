@@ -88,6 +88,34 @@ def test_mixed_precision_matches_oracle(name):
     assert rel_l2(X, r.X) < 1e-8
 
 
+UNEVEN = {
+    # slab blocks b = 64 (register factor), 144 (packed, W staged) and 192/256 (W read from global)
+    "uneven_mix": dict(n=(36, 20, 24), edges=([8, 12, 16], [8, 12], [12, 12]), patch=((4, 4), (4, 6), (6, 4)),
+                       sigma=1.5, lam=5.0),
+    "big_blocks": dict(n=(28, 16, 16), edges=([12, 16], [16], [16]), patch=((4, 4), (0, 0), (0, 0)),
+                       sigma=1.0, lam=4.0),
+}
+
+
+@pytest.mark.parametrize("name", list(UNEVEN))
+def test_uneven_blocks_mixed(name):
+    w = small(**UNEVEN[name])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp32_ir", ir_max_sweeps=8, ir_tol=1e-13)
+    assert st["not_spd"] == 0
+    assert rel_l2(p, r.p) < 1e-8
+    assert rel_l2(u.ravel(), r.u.ravel()) < 1e-8
+
+
+def test_uneven_blocks_fp64():
+    w = small(**UNEVEN["uneven_mix"])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp64")
+    assert code == 0, st
+    assert rel_l2(p, r.p) < 1e-10
+    assert rel_l2(u.ravel(), r.u.ravel()) < 1e-10
+
+
 def test_linear_pressure_dirichlet():
     # homogeneous K, Dirichlet x walls, cuts normal to the gradient: MRCM is exact
     nx, ny, nz = 12, 6, 4
@@ -111,6 +139,48 @@ def test_c1_full_size_fp64_and_mixed():
         assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
         assert rel_l2(p, r.p) < tol, prec
         assert rel_l2(u.ravel(), r.u.ravel()) < tol, prec
+
+
+def test_graph_mode_matches_direct_calls(tmp_path):
+    import torch as T
+    from gpu_helpers import gpu_solver
+    w = small(**CASES["many_tiles"])
+    prob = oracle.from_workload(w)
+    s = gpu_solver(w, "fp32_ir")
+    K = T.from_numpy(prob.K).cuda()
+    f = T.from_numpy(prob.f).cuda()
+    st = T.cuda.Stream()
+    with T.cuda.stream(st):
+        p0, u0, X0, _ = s.solve(K, f)
+        p0, X0 = p0.clone(), X0.clone()
+        out = s.outputs()
+        for _ in range(3):                      # capture, then two replays
+            p1, u1, X1, _ = s.solve(K, f, out=out, stream=st, graph=True)
+    T.cuda.synchronize()
+    assert T.equal(p0, p1) and T.equal(X0, X1)
+
+
+def test_autotune_and_cache(tmp_path):
+    import torch as T
+    from paper_2103_08513_gb300 import MRCM
+    w = small(**CASES["many_tiles"])
+    prob = oracle.from_workload(w)
+    r = oracle.solve_mrcm(prob)
+    cache = str(tmp_path / "tune.txt")
+    K = T.from_numpy(prob.K).cuda()
+    f = T.from_numpy(prob.f).cuda()
+    s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
+    s.factor_local(K)
+    v0, v1 = s.autotune(f)
+    assert 0 <= v0 < 6 and 0 <= v1 < 6
+    line = open(cache).read().split()
+    assert int(line[1]) == v0 and int(line[2]) == v1
+    p, u, X, _ = s.solve(K, f)
+    assert rel_l2(p.cpu().numpy().ravel(), r.p) < 1e-8
+    # a new handle with the same cache picks the stored variants up
+    s2 = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
+    p2, *_ = s2.solve(K, f)
+    assert rel_l2(p2.cpu().numpy().ravel(), r.p) < 1e-8
 
 
 def test_repeat_calls_are_deterministic():
