@@ -243,6 +243,42 @@ mrcm_status mrcm_profile(mrcm_handle* h, int enable);
  * the count.  INVALID_ARG if buf is too small (the text is truncated). */
 mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long* launches);
 
+/* Allocation-free local solve of one box subdomain (the paper has no
+ * counterpart: this is a deployment variant of the local factor and solve).
+ * It is for callers that cannot allocate device memory -- code whose host
+ * application owns every device allocation through its own pool, plug-ins
+ * that may only touch the buffers handed to them, or real-time loops where a
+ * cudaMalloc would stall the device.  It needs no workspace and no handle:
+ * its scratch is a fixed 2.26 MB __device__ array inside the library, held by
+ * every GPU that loads the library until the process exits.
+ *
+ * Solves the TPFA problem of Eq. localomegaint / Eq. localomegapar on a box of
+ * box[0] x box[1] x box[2] cells of size h (FP64, the same discretisation as
+ * mrcm_factor_local / mrcm_solve_mbf): for every cell
+ *   sum_interior T (p_c - p_nb) + sum_Robin T_R (p_c - g) + sum_Dirichlet T_D (p_c - g) = f V.
+ *  side_type[6]  host; sides x-lo, x-hi, y-lo, y-hi, z-lo, z-hi:
+ *                0 no-flow, 1 Robin (-beta u.n + p = g), 2 Dirichlet (p = g)
+ *  K     device FP64 [3][box z][box y][box x];  f device FP64 [z][y][x]
+ *  g, beta  device FP64, one value per boundary face: side by side in the
+ *        order above, each side's faces with its first tangential axis (lower
+ *        axis index) fastest; beta is read on Robin sides only
+ *  p     device FP64 [z][y][x] output
+ *  q_out device FP64, same layout as g: outward integrated flux T (p_c - g)
+ *        on Robin and Dirichlet faces, 0 on no-flow faces
+ *  not_spd  device int output: 1 if a block pivot was not positive
+ * Limits (the fixed scratch): at most 4096 cells, slab block (product of the
+ * two shorter edges) <= 128, longest edge x block^2 <= 262144; larger boxes
+ * return MRCM_ERR_OOM.  At least one side must be Robin or Dirichlet
+ * (MRCM_ERR_INVALID_ARG otherwise).  The first call on a device looks up the
+ * scratch address and sets the kernel's shared-memory limit; make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * scratch array (nothing in it is read before the same call writes it), so
+ * calls that overlap on the GPU (different streams, or host threads) race:
+ * serialise them. */
+mrcm_status mrcm_box_solve_noalloc(const int box[3], const double h[3], const int side_type[6],
+                                   const double* K, const double* f, const double* g, const double* beta,
+                                   double* p, double* q_out, int* not_spd, void* stream);
+
 /* Release the handle and its device tables (not the caller's buffers). */
 void mrcm_destroy(mrcm_handle* h);
 

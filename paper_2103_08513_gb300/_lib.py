@@ -68,6 +68,8 @@ SIGNATURES = {
     "mrcm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mrcm_profile_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_longlong)]),
+    "mrcm_box_solve_noalloc": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+                               + [C.c_void_p] * 6 + [C.c_void_p, C.c_void_p]),
     "mrcm_destroy": (None, [C.c_void_p]),
     "mrcm_last_error": (C.c_char_p, [C.c_void_p]),
 }
