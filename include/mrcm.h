@@ -279,6 +279,61 @@ mrcm_status mrcm_box_solve_noalloc(const int box[3], const double h[3], const in
                                    const double* K, const double* f, const double* g, const double* beta,
                                    double* p, double* q_out, int* not_spd, void* stream);
 
+/* ---- Learned warm start (no counterpart in the paper) -------------------
+ * A small 3-D convolutional network (layers-1 hidden layers of `hidden`
+ * channels, 3x3x3 'same' convolutions, leaky ReLU (slope 1/100), logistic output) maps a
+ * subdomain's fields to a guess of one P-MBF, which seeds an FP32 conjugate-
+ * gradient solve of the local system.  Weights are FP32 (master, Adam
+ * moments) and used as BF16 by the convolutions; accumulation is FP32.
+ * Tensors are [batch][channel][D][H][W] FP32 device arrays (W fastest).
+ * The caller owns every buffer: `state` (mrcm_net_query's state_floats) holds
+ * master weights, Adam moments and the BF16 copy; `ws` (ws_bytes for the
+ * batch) holds activations and gradients. */
+typedef struct mrcm_net mrcm_net;
+
+/* Describe a network for D x H x W boxes (S = D*H*W <= 4096); in_channels
+ * and hidden <= 32, 2 <= layers <= 16.  Host only. */
+mrcm_status mrcm_net_create(int in_channels, int hidden, int layers, int D, int H, int W, mrcm_net** out);
+mrcm_status mrcm_net_query(const mrcm_net* net, int batch, size_t* params, size_t* state_floats,
+                           size_t* ws_bytes);
+/* He-normal weights from a counter-based generator (splitmix64; the output
+ * layer's scaled by 1/10), zero biases and Adam moments.  Synchronises the
+ * stream. */
+mrcm_status mrcm_net_init(mrcm_net* net, float* state, unsigned long long seed, void* stream);
+/* Refresh the BF16 copy after the caller wrote master weights. */
+mrcm_status mrcm_net_sync_weights(mrcm_net* net, float* state, void* stream);
+/* y[batch][1][D][H][W] = net(x[batch][in][D][H][W]). */
+mrcm_status mrcm_net_forward(mrcm_net* net, const float* state, const float* x, float* y, int batch, void* ws,
+                             void* stream);
+/* Mean-squared-error loss against target[batch][1][D][H][W] (*loss, device)
+ * and its gradient with respect to the parameters (grad[params], device). */
+mrcm_status mrcm_net_gradient(mrcm_net* net, const float* state, const float* x, const float* target, int batch,
+                              float* grad, float* loss, void* ws, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1). */
+mrcm_status mrcm_net_train_step(mrcm_net* net, float* state, const float* x, const float* target, int batch,
+                                float lr, int step, float* loss, void* ws, void* stream);
+void mrcm_net_destroy(mrcm_net* net);
+
+/* Training samples from the method itself (after mrcm_solve_mbf): sample s
+ * is P-MBF column c of subdomain l, for the subdomains whose box is the
+ * network's W x H x D, enumerated by subdomain then c.  x[s] has 4 channels:
+ * log(Kx)/4, log(Kz)/4, the cells next to the faces of basis c (1, else 0) and the
+ * cells next to any Robin face; target[s] is the FP64 column rounded to FP32.
+ * *n_samples = min(available, max_samples); x/target may be NULL to count.
+ * The first call per box shape uploads a small sample table owned by the
+ * handle. */
+mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, float* x, float* target,
+                             int max_samples, int* n_samples, void* stream);
+
+/* FP32 conjugate gradients on the Jacobi-scaled local system of each of the
+ * first n_samples samples (order of mrcm_net_samples), from x0[s] (unscaled
+ * guess in the sample layout; NULL = zero), to ||r|| <= tol ||b|| or maxit
+ * iterations.  The result replaces the P-MBF column in the MBF array (so the
+ * FP64 direct solve can judge it first); iters[s] (device int) receives the
+ * iterations, maxit + 1 when the tolerance was not reached. */
+mrcm_status mrcm_pcg_mbf(mrcm_handle* h, const mrcm_net* net, void* ws, const float* x0, int n_samples,
+                         int maxit, double tol, int* iters, void* stream);
+
 /* Release the handle and its device tables (not the caller's buffers). */
 void mrcm_destroy(mrcm_handle* h);
 

@@ -70,6 +70,16 @@ SIGNATURES = {
     "mrcm_profile_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_longlong)]),
     "mrcm_box_solve_noalloc": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
                                + [C.c_void_p] * 6 + [C.c_void_p, C.c_void_p]),
+    "mrcm_net_create": (C.c_int, [C.c_int] * 6 + [C.POINTER(C.c_void_p)]),
+    "mrcm_net_query": (C.c_int, [C.c_void_p, C.c_int] + [C.POINTER(C.c_size_t)] * 3),
+    "mrcm_net_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_ulonglong, C.c_void_p]),
+    "mrcm_net_sync_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrcm_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mrcm_net_gradient": (C.c_int, [C.c_void_p] * 4 + [C.c_int] + [C.c_void_p] * 4),
+    "mrcm_net_train_step": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_float, C.c_int] + [C.c_void_p] * 3),
+    "mrcm_net_destroy": (None, [C.c_void_p]),
+    "mrcm_net_samples": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "mrcm_pcg_mbf": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "mrcm_destroy": (None, [C.c_void_p]),
     "mrcm_last_error": (C.c_char_p, [C.c_void_p]),
 }

@@ -486,6 +486,8 @@ void mrcm_destroy(mrcm_handle* h) {
     if (!h) return;
     h->prof.release();
     drop_graph(h);
+    if (h->samp_off) cudaFree(h->samp_off);
+    if (h->samp_list) cudaFree(h->samp_list);
     free_device(h->d);
     delete h;
 }

@@ -194,6 +194,10 @@ struct mrcm_handle {
     cudaGraphExec_t graph_exec = nullptr;
     const void* graph_key[9] = {};
     long long graph_launches = 0;
+    int* samp_off = nullptr;              // learned-path sample tables (internal)
+    int* samp_list = nullptr;
+    int samp_shape[3] = {0, 0, 0};
+    int samp_count = 0;
     const double* K = nullptr;   // caller's K (kept for reconstruction)
     const double* f = nullptr;   // caller's f
 };

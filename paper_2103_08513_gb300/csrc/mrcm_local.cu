@@ -627,7 +627,6 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
 // Tunable variants of the local solve (threads per CTA x GEMM rows per thread).
 constexpr int kNumSolveVariants = 6;
 __host__ __device__ inline int variant_threads(int v) { return v < 3 ? 256 : 128; }
-__host__ __device__ inline int variant_rows(int v) { const int r[3] = {2, 1, 4}; return r[v % 3]; }
 
 template <typename T, bool kScaled, bool kSweep>
 const void* solve_kernel(int v) {

@@ -1,0 +1,92 @@
+"""Learned warm start on the GPU: gradients against the oracle, training on
+the method's own MBFs, and the warm-start gain judged by the FP64 direct MBFs.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle import conv3d  # noqa: E402
+
+
+def _net(D, H, W, hidden, layers, seed=0, batch=8):
+    from paper_2103_08513_gb300.learned import WarmStartNet
+    return WarmStartNet(D, H, W, hidden=hidden, layers=layers, batch=batch, seed=seed)
+
+
+def test_gpu_gradient_matches_oracle():
+    D, H, W, hidden, layers = 3, 4, 5, 8, 3
+    net = _net(D, H, W, hidden, layers)
+    rng = np.random.default_rng(1)
+    x = torch.from_numpy(rng.normal(size=(3, 4, D, H, W)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.uniform(size=(3, 1, D, H, W)).astype(np.float32)).cuda()
+    grad, loss = net.gradient(x, t)
+    torch.cuda.synchronize()
+    cin = [4] + [hidden] * (layers - 1)
+    cout = [hidden] * (layers - 1) + [1]
+    wb = net.bf16_weights().cpu().numpy().astype(np.float64)
+    # biases are used in FP32: take them from the master copy
+    master = net.master.cpu().numpy().astype(np.float64)
+    flat = wb.copy()
+    off = 0
+    for ci, co in zip(cin, cout):
+        off += co * ci * 27
+        flat[off: off + co] = master[off: off + co]
+        off += co
+    params = conv3d.unflatten(flat, cin, cout)
+    lref, gref = conv3d.loss_and_grad(params, x.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64))
+    gref = conv3d.flatten(gref)
+    g = grad.cpu().numpy()
+    assert abs(float(loss.cpu()[0]) - lref) <= 1e-5 * lref
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def _mrcm_fields(seeds, n=(40, 40, 10)):
+    from synth.fields import lognormal_K
+    from synth.wells import corner_wells
+    nx, ny, nz = n
+    for sd in seeds:
+        yield lognormal_K((nz, ny, nx), 2.0, 8.0, 0.1, seed=sd), corner_wells(nx, ny, nz)
+
+
+def test_training_and_warm_start_gain():
+    """Train on the method's own P-MBFs (config-1-style fields), then warm-start CG
+    on a held-out field: fewer iterations than from zero, and the CG result agrees
+    with the FP64 direct MBFs (the judge) to the CG tolerance."""
+    from paper_2103_08513_gb300 import MRCM
+    n = (40, 40, 10)
+    edges = ([10] * 4, [10] * 4, [5, 5])
+    s = MRCM(n, edges, ((5, 2), (5, 2), (5, 2)), precision="fp64")
+    net = _net(5, 10, 10, 32, 4, seed=0, batch=256)
+    xs, ts = [], []
+    for K, f in _mrcm_fields(range(1, 11)):
+        s.factor_local(torch.from_numpy(K).cuda())
+        s.solve_mbf(torch.from_numpy(f).cuda())
+        x, t = net.samples(s)
+        xs.append(x.clone()); ts.append(t.clone())
+    X = torch.cat(xs)
+    T = torch.cat(ts)
+    floor = float((T ** 2).mean() - T.mean() ** 2)        # loss of the best constant guess
+    net.set_output_bias(float(T.mean()))
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    for step in range(1000):
+        idx = torch.randint(0, X.shape[0], (256,), generator=gen).cuda()
+        loss = net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr=1e-3)
+    assert float(loss.cpu()[0]) < 0.3 * floor
+    # held-out field: CG iterations from the network's guess vs from zero
+    K, f = next(_mrcm_fields([201]))
+    Kd, fd = torch.from_numpy(K).cuda(), torch.from_numpy(f).cuda()
+    s.factor_local(Kd)
+    s.solve_mbf(fd)
+    x, t = net.samples(s)
+    nsm = min(256, x.shape[0])
+    y = net.forward(x[:nsm].contiguous())
+    it_net = net.pcg(s, y, nsm, maxit=500, tol=1e-6).cpu().numpy()
+    _, t_net = net.samples(s)                  # CG results, judged by the direct FP64 MBFs
+    s.solve_mbf(fd)
+    it_zero = net.pcg(s, None, nsm, maxit=500, tol=1e-6).cpu().numpy()
+    assert (it_net <= 500).all() and (it_zero <= 500).all()
+    assert it_net.mean() < it_zero.mean()
+    err = (t_net[:nsm] - t[:nsm]).norm() / t[:nsm].norm()
+    assert float(err) < 1e-4
