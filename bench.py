@@ -155,14 +155,30 @@ def kernel_work(name, sizes, swept, precision, peaks):
     return 8.0 * sizes["mbf_entries"] + 32.0 * sizes["n_cells"], "hbm", "GB/s", peaks["hbm_gbs"]
 
 
-def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks):
+def traffic_per_launch(workload_key, kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu launch-list summary, or None."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload_key}.txt")
+    try:
+        for line in open(path):
+            if line.startswith("#"):
+                continue
+            parts = line.split()
+            if len(parts) >= 2 and parts[0] == kernel:
+                return float(parts[1])
+    except OSError:
+        return None
+    return None
+
+
+def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks, workload_key=None):
     """Achieved rate of a kernel: its algorithmic work per step over its time per step."""
     work, bound, unit, peak = kernel_work(name, sizes, swept, precision, peaks)
     per_step_s = total_ms / 1e3 / steps
     scale = 1e12 if unit == "TFLOP/s" else 1e9
     achieved = work / per_step_s / scale
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": unit,
-            "frac": round(achieved / peak, 4), "traffic": None, "launches": launches,
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic_per_launch(workload_key, name) if workload_key else None, "launches": launches,
             "avg_launch_ms": round(total_ms / max(launches, 1), 4),
             "work_per_step": work, "peak_source": peaks["source"] if bound == "hbm" else "derived"}
 
@@ -361,8 +377,9 @@ def main():
     sizes = s.sizes
     swept = s.read_work()
     ranked = sorted(kprof.items(), key=lambda kv: -kv[1][1])
-    roof = roofline(ranked[0][0], ranked[0][1][1], ranked[0][1][0], args.steps, sizes, swept, args.precision, peaks)
-    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks) for k, v in ranked[1:4]]
+    wkey = args.workload if args.precision == "fp32_ir" else None
+    roof = roofline(ranked[0][0], ranked[0][1][1], ranked[0][1][0], args.steps, sizes, swept, args.precision, peaks, wkey)
+    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks, wkey) for k, v in ranked[1:4]]
     kern_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(sum(x[1] for x in kprof.values()), 1e-9), 4)}
                   for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])}
 
