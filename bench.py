@@ -196,6 +196,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--wave-gb", type=float, default=None,
+                    help="memory budget of the local block factors per wave (GB); default 16 for c5, else none")
     return ap.parse_args()
 
 
@@ -258,9 +260,13 @@ def main():
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(local)
 
+    wave_gb = args.wave_gb if args.wave_gb is not None else (16.0 if args.workload == "c5" else 0.0)
+    wave_bytes = int(wave_gb * (1 << 30))
+
     def make(precision):
         return MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const,
-                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=1e-13, device=dev)
+                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=1e-13, device=dev,
+                    wave_bytes=wave_bytes)
 
     Kd = torch.from_numpy(K).to(dev)
     fd = torch.from_numpy(f).to(dev)
@@ -277,7 +283,7 @@ def main():
             # larger slab blocks are compared against a tightly refined mixed solve
             s64 = MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha,
                        beta_const=w.beta_const, precision=args.precision, ir_max_sweeps=12, ir_tol=1e-15,
-                       device=dev)
+                       device=dev, wave_bytes=wave_bytes)
             ref_kind = "mixed_tight"
     outs = (torch.empty(max(s.n_interface, 1), dtype=torch.float64, device=dev),
             torch.empty((nz, ny, nx), dtype=torch.float64, device=dev),
@@ -400,6 +406,7 @@ def main():
                    "execution": "CUDA graph of the five device calls, replayed per step",
                    "autotuned_variants": {"first_solve": tuned[0], "sweep": tuned[1]},
                    "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
+                   "waves": {"budget_bytes": wave_bytes, "count": s.sizes.get("n_waves", 1)},
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write, outside the events)"},
         "fp64_gpu": ({"value": round(n_sub * steps64 * ws / (ms64 / 1e3), 2), "unit": UNIT,

@@ -93,7 +93,10 @@ enum {
  *  precision          MRCM_FP64 / MRCM_FP32_IR / MRCM_TF32_IR
  *  ir_max_sweeps      refinement sweeps after the first solve (mixed modes)
  *  ir_tol             per-column stop: ||r||_2 <= ir_tol * ||b||_2
- *  wave_bytes         reserved (memory budget for streamed waves); 0
+ *  wave_bytes         memory budget (bytes) of the local block factors: when
+ *                     positive, subdomains are processed in waves whose
+ *                     factors fit the budget (the factors of one wave are
+ *                     dropped before the next is factored); 0 = one wave
  *  tune_cache         path of the autotuner cache (text), or NULL; read at
  *                     the first device call, written by mrcm_autotune      */
 typedef struct {
@@ -131,6 +134,7 @@ typedef struct {
     long long mbf_entries;      /* sum over l of m_l * N_l (MBF array length) */
     double ldl_flops;           /* flops of the interface LDL^T (lower triangle) */
     double ldl_update_flops;    /* part of ldl_flops in the trailing (Schur) updates */
+    int n_waves;                /* memory-bounded waves of the local phase */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;
@@ -151,7 +155,9 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* out);
 /* Basis function i of V_H: normal axis, lower/upper subdomain, fine faces. */
 mrcm_status mrcm_query_basis(const mrcm_handle* h, int i, int* axis, int* sub_lo, int* sub_hi, int* n_faces);
 
-/* Assemble every local matrix A^H_l from K and factor it.
+/* Assemble every local matrix A^H_l from K and factor it (with several
+ * memory-bounded waves the factorisation moves to mrcm_solve_mbf, wave by
+ * wave).
  *  K   device, FP64 [3][nz][ny][nx] (Kxx, Kyy, Kzz), all entries > 0 and finite
  *  ws  device workspace, ws_bytes >= mrcm_query_workspace
  * The local matrices are built in FP64 (Eq. aijk with harmonic means; Robin

@@ -216,6 +216,7 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
     o->mbf_entries = t.total_x;
     o->ldl_flops = t.ldl_flops;
     o->ldl_update_flops = t.ldl_update_flops;
+    o->n_waves = t.n_waves;
     return MRCM_OK;
 }
 

@@ -77,6 +77,13 @@ struct Tables {
     std::vector<int> Ilist;        // concatenated sorted I^l (global basis ids)
     std::vector<int> class_list;   // subdomains grouped by factor class, costliest first
     std::vector<int> solve_list;   // all subdomains, costliest solve first
+    // memory-bounded waves (cfg.wave_bytes): wave w owns solve_list entries
+    // [wave_off[w], wave_off[w+1]); its factor classes are wave_class[w][0..1]
+    // (offsets into class_list); block factors are stored per wave (w_off is
+    // relative to the wave) so one W region serves every wave
+    std::vector<int> wave_off;
+    std::vector<int> wave_class_off;   // 3 entries per wave
+    int n_waves = 1;
     int class_off[3] = {0, 0, 0};  // class 0: b <= kRegBlock, class 1: larger blocks
     long long n_cells = 0, total_x = 0, total_w = 0, total_el = 0;
     int total_elb = 0;
@@ -119,7 +126,7 @@ struct DeviceTables {
     int* Ilist = nullptr;
     int* class_list = nullptr;
     int class_off[3] = {0, 0, 0};
-    int* solve_list = nullptr;                 // all subdomains, costliest solve first
+    int* solve_list = nullptr;                 // all subdomains, costliest solve first (wave by wave)
     int sms = 0;
     size_t solve_smem = 0;
     int solve_occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};

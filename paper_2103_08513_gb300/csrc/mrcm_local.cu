@@ -367,8 +367,6 @@ template <> struct Vec4<double> { using type = double4_16a; };
 template <typename T>
 __device__ __forceinline__ typename Vec4<T>::type ld4(const T* p) { return *reinterpret_cast<const typename Vec4<T>::type*>(p); }
 
-// Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile 2 rows x 4 columns.
-// Results handed to `store(i, jj, value)`.
 // Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile RT rows x 4
 // columns (rows i0, i0 + bh, ..., bh = ceil(b / RT)).  Results are handed to
 // `store(i, jj, value)`.
@@ -431,6 +429,7 @@ struct LocalArgs {
     const int* list;      // subdomains in processing order (costliest first)
     int nlist;
     int* queue;           // work-queue counter (reset to 0 before each launch)
+    int count_unconverged;  // add this sweep's unconverged columns to the status word
 };
 
 // Coupling between slab cells c and c+b in the solve's arithmetic: the FP32
@@ -596,7 +595,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             else atomicAdd(&nbad, 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && nbad) atomicAdd(&g.status[ST_UNCONVERGED], nbad);
+        if (threadIdx.x == 0 && nbad && g.count_unconverged) atomicAdd(&g.status[ST_UNCONVERGED], nbad);
     } else {
         for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
             const int j = cols[jj];
@@ -707,6 +706,33 @@ Geo make_geo(const mrcm_config& c) {
 
 }  // namespace
 
+// Block factors of one wave's subdomains (register-resident FP32 kernel for
+// b <= 64, packed shared-memory kernel otherwise; one launch per class).
+static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, int precision,
+                               int w, cudaStream_t st, Prof& P) {
+    double* coef = (double*)(ws + L.coef);
+    double* scale = (double*)(ws + L.scale);
+    int* status = (int*)(ws + L.status);
+    const int o0 = t.wave_class_off[3 * w], o1 = t.wave_class_off[3 * w + 1], o2 = t.wave_class_off[3 * w + 2];
+    const int n_small = o1 - o0, n_large = o2 - o1;
+    if (precision == MRCM_FP64) {
+        if (n_large > 0) {
+            size_t sm = factor_smem<double>(t.max_b);
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o1, coef, scale,
+                (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        }
+    } else {
+        if (n_small > 0)
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
+                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        if (n_large > 0) {
+            size_t sm = factor_smem<float>(t.max_b);
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o1, coef, scale,
+                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        }
+    }
+}
+
 int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                   const double* K, int precision, void* stream, Prof& P) {
     cudaStream_t st = (cudaStream_t)stream;
@@ -727,26 +753,7 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
                                              c.beta_const, bcm, blo, bhi, coef, scale,
                                              (double*)(ws + L.rhs_part), (double*)(ws + L.face_tr),
                                              (double*)(ws + L.face_beta), t.n_cells));
-    // size classes: register-resident factor for FP32 blocks with b <= 64, packed
-    // shared-memory factor otherwise; each class is one launch over its list
-    const int* lst_small = d.class_list + d.class_off[0];
-    const int* lst_large = d.class_list + d.class_off[1];
-    const int n_small = d.class_off[1] - d.class_off[0];
-    const int n_large = d.class_off[2] - d.class_off[1];
-    if (precision == MRCM_FP64) {
-        size_t sm = factor_smem<double>(t.max_b);
-        MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<nsub, kThreads, sm, st>>>(d.subs, d.class_list, coef, scale,
-            (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
-    } else {
-        if (n_small > 0)
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, lst_small, coef, scale,
-                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
-        if (n_large > 0) {
-            size_t sm = factor_smem<float>(t.max_b);
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, lst_large, coef, scale,
-                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
-        }
-    }
+    if (t.n_waves == 1) launch_factor_wave(t, d, L, ws, precision, 0, st, P);
     return (int)cudaGetLastError();
 }
 
@@ -798,6 +805,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.mpad = (t.max_m + 3) & ~3;
     g.list = d.solve_list; g.nlist = (int)t.subs.size();
     g.queue = (int*)(ws + L.status) + ST_QUEUE;
+    g.count_unconverged = 0;
     return g;
 }
 
@@ -823,17 +831,22 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     LocalArgs g = local_args(t, d, L, ws, f);
     g.tol2 = tol * tol;
     const void* W = (const void*)(ws + L.W);
-    launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
-    if (precision == MRCM_FP64) {
-        MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, 0));
-    } else {
-        MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
-        for (int it = 0; it < sweeps; ++it) {
-            if (it + 1 == sweeps) MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
-            launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
+    for (int w = 0; w < t.n_waves; ++w) {
+        // one memory-bounded wave: factor (when waves share the W region), solve, refine
+        if (t.n_waves > 1) launch_factor_wave(t, d, L, ws, precision, w, st, P);
+        g.list = d.solve_list + t.wave_off[w];
+        g.nlist = t.wave_off[w + 1] - t.wave_off[w];
+        g.count_unconverged = 0;
+        launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
+        if (precision != MRCM_FP64) {
+            for (int it = 0; it < sweeps; ++it) {
+                g.count_unconverged = it + 1 == sweeps ? 1 : 0;
+                launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+            }
         }
-        MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, sweeps));
     }
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 0 : sweeps));
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
     return (int)cudaGetLastError();
@@ -848,6 +861,9 @@ int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char
     g.tol2 = 0.0;        // nothing retires: every sweep does the full work
     const void* W = (const void*)(ws + L.W);
     Prof dummy;
+    g.list = d.solve_list;                      // tune on the first wave
+    g.nlist = t.wave_off[1];
+    if (t.n_waves > 1) launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
     const bool mixed = t.cfg.precision != MRCM_FP64;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -203,7 +203,7 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
     }
 
     // ---- per-subdomain lists and offsets -------------------------------------
-    long long cell_off = 0, x_off = 0, w_off = 0, el_off = 0;
+    long long cell_off = 0, x_off = 0, el_off = 0;
     int elb_off = 0;
     for (int l = 0; l < nsub; ++l) {
         SubInfo& s = t.subs[l];
@@ -230,7 +230,6 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         s.nface = (int)t.faces.size() - s.face_off;
         s.cell_off = cell_off;  cell_off += s.N;
         s.x_off = x_off;        x_off += (long long)s.m * s.N;
-        s.w_off = w_off;        w_off += (long long)s.ns * s.b * s.b;
         s.el_off = el_off;      el_off += (long long)s.el_dim * s.el_dim;
         s.elb_off = elb_off;    elb_off += s.el_dim;
         s.rhs_off = (int)t.total_rhs;
@@ -242,21 +241,9 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         t.local_factor_flops += (double)s.N * s.b * s.b;    // banded-Cholesky count of the block factor
         t.local_solve_flops += 4.0 * s.N * (double)s.b * s.m;
     }
+    // solve order (costliest first), memory-bounded waves over it, and per wave the
     // factor classes (register-resident FP32 factor for small blocks), costliest first
     {
-        std::vector<std::pair<double, int>> c0, c1;
-        for (int l = 0; l < nsub; ++l) {
-            const SubInfo& s = t.subs[l];
-            double cost = (double)s.ns * s.b * s.b * s.b;
-            if (cfg->precision != MRCM_FP64 && s.b <= kRegBlock) c0.push_back({-cost, l}); else c1.push_back({-cost, l});
-        }
-        std::sort(c0.begin(), c0.end());
-        std::sort(c1.begin(), c1.end());
-        for (auto& pr : c0) t.class_list.push_back(pr.second);
-        for (auto& pr : c1) t.class_list.push_back(pr.second);
-        t.class_off[0] = 0;
-        t.class_off[1] = (int)c0.size();
-        t.class_off[2] = (int)(c0.size() + c1.size());
         std::vector<std::pair<double, int>> sl;
         for (int l = 0; l < nsub; ++l) {
             const SubInfo& s = t.subs[l];
@@ -264,9 +251,45 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         }
         std::sort(sl.begin(), sl.end());
         for (auto& pr : sl) t.solve_list.push_back(pr.second);
+        const size_t welem = cfg->precision == MRCM_FP64 ? sizeof(double) : sizeof(float);
+        t.wave_off.assign(1, 0);
+        long long wcur = 0, wmax = 0;
+        for (int q = 0; q < nsub; ++q) {
+            SubInfo& s = t.subs[t.solve_list[q]];
+            const long long need = (long long)s.ns * s.b * s.b;
+            if (cfg->wave_bytes > 0 && q > t.wave_off.back() && (size_t)(wcur + need) * welem > cfg->wave_bytes) {
+                t.wave_off.push_back(q);
+                wcur = 0;
+            }
+            s.w_off = wcur;
+            wcur += need;
+            wmax = std::max(wmax, wcur);
+        }
+        t.wave_off.push_back(nsub);
+        t.n_waves = (int)t.wave_off.size() - 1;
+        t.total_w = wmax;
+        t.class_list.clear();
+        for (int w = 0; w < t.n_waves; ++w) {
+            std::vector<std::pair<double, int>> c0, c1;
+            for (int q = t.wave_off[w]; q < t.wave_off[w + 1]; ++q) {
+                const int l = t.solve_list[q];
+                const SubInfo& s = t.subs[l];
+                const double cost = (double)s.ns * s.b * s.b * s.b;
+                if (cfg->precision != MRCM_FP64 && s.b <= kRegBlock) c0.push_back({-cost, l}); else c1.push_back({-cost, l});
+            }
+            std::sort(c0.begin(), c0.end());
+            std::sort(c1.begin(), c1.end());
+            t.wave_class_off.push_back((int)t.class_list.size());
+            for (auto& pr : c0) t.class_list.push_back(pr.second);
+            t.wave_class_off.push_back((int)t.class_list.size());
+            for (auto& pr : c1) t.class_list.push_back(pr.second);
+            t.wave_class_off.push_back((int)t.class_list.size());
+        }
+        t.class_off[0] = t.wave_class_off[0];
+        t.class_off[1] = t.wave_class_off[1];
+        t.class_off[2] = t.wave_class_off[2];
     }
     t.total_x = x_off;
-    t.total_w = w_off;
     t.total_el = el_off;
     t.total_elb = elb_off;
 
@@ -382,7 +405,7 @@ void compute_layout(const Tables& t, Layout& L) {
     L.rhs_part = take(nc * sizeof(double));
     L.face_tr = take(t.faces.size() * sizeof(double));
     L.face_beta = take(t.faces.size() * sizeof(double));
-    L.W = take((size_t)t.total_w * sizeof(double));
+    L.W = take((size_t)t.total_w * (t.cfg.precision == MRCM_FP64 ? sizeof(double) : sizeof(float)));
     L.X = take((size_t)t.total_x * sizeof(double));
     L.R = take(t.cfg.precision == MRCM_FP64 ? (size_t)t.total_x * sizeof(double) : (size_t)t.total_x * sizeof(float));
     L.colnorm = take((size_t)t.total_rhs * 2 * sizeof(double));

@@ -183,6 +183,24 @@ def test_autotune_and_cache(tmp_path):
     assert rel_l2(p2.cpu().numpy().ravel(), r.p) < 1e-8
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_memory_bounded_waves_match_single_wave(prec):
+    import torch as T
+    from paper_2103_08513_gb300 import MRCM
+    w = small(**UNEVEN["uneven_mix"])
+    prob = oracle.from_workload(w)
+    K = T.from_numpy(prob.K).cuda()
+    f = T.from_numpy(prob.f).cuda()
+    one = MRCM(w.n, w.edges, w.patch, precision=prec, ir_max_sweeps=6, ir_tol=1e-13)
+    p1, u1, X1, _ = one.solve(K, f)
+    p1, X1 = p1.clone(), X1.clone()
+    wav = MRCM(w.n, w.edges, w.patch, precision=prec, ir_max_sweeps=6, ir_tol=1e-13, wave_bytes=2 << 20)
+    assert wav.ws_bytes < one.ws_bytes
+    p2, u2, X2, _ = wav.solve(K, f)
+    T.cuda.synchronize()
+    assert T.equal(p1, p2) and T.equal(X1, X2)
+
+
 def test_repeat_calls_are_deterministic():
     w = small(**CASES["many_tiles"])
     prob = oracle.from_workload(w)
