@@ -109,7 +109,7 @@ void load_tune_cache(mrcm_handle* h) {
     int v0, v1;
     const std::string want = tune_key(h);
     while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3) {
-        if (want == key && v0 >= 0 && v0 < 6 && v1 >= 0 && v1 < 6) {
+        if (want == key && v0 >= 0 && v0 < 8 && v1 >= 0 && v1 < 8) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
         }

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "mrcm_internal.h"
@@ -406,6 +407,76 @@ __device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* _
     }
 }
 
+// Tensor-core variant of block_gemm (FP32 operands): warp-level
+// mma.sync.m16n8k8 with TF32 inputs and FP32 accumulation, each operand split
+// into a TF32 high part and a TF32 remainder, x*y ~ xh*yh + xh*yl + xl*yh
+// ("3xTF32"), which keeps FP32-level accuracy on the tensor pipe.  Warps take
+// (16-row, 8-column) output tiles; rows >= b and K-padding columns are zero.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const uint32_t bb[2]) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(bb[0]), "r"(bb[1]));
+}
+
+template <typename Store>
+__device__ __forceinline__ void block_gemm_tc(const float* __restrict__ Wsm, const float* __restrict__ Z, int b,
+                                              int na, int mpad, Store store) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
+    const int mt = (b + 15) >> 4, nt = (na + 7) >> 3, kt = (b + 7) >> 3;
+    for (int task = warp; task < mt * nt; task += nwarps) {
+        const int m0 = (task % mt) * 16, n0 = (task / mt) * 8;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k8 = 0; k8 < kt; ++k8) {
+            const int k0 = k8 * 8;
+            float av[4], bv[2];
+            const int ar[4] = {m0 + g, m0 + g + 8, m0 + g, m0 + g + 8};
+            const int ac[4] = {k0 + tg, k0 + tg, k0 + tg + 4, k0 + tg + 4};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[q] = (ar[q] < b && ac[q] < b) ? Wsm[ac[q] * b + ar[q]] : 0.0f;
+            const int br[2] = {k0 + tg, k0 + tg + 4};
+            const int bc = n0 + g;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) bv[q] = (br[q] < b && bc < na) ? Z[br[q] * mpad + bc] : 0.0f;
+            uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { ah[q] = tf32_rna(av[q]); al[q] = tf32_rna(av[q] - __uint_as_float(ah[q])); }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) { bh[q] = tf32_rna(bv[q]); bl[q] = tf32_rna(bv[q] - __uint_as_float(bh[q])); }
+            mma_tf32(acc, al, bh);
+            mma_tf32(acc, ah, bl);
+            mma_tf32(acc, ah, bh);
+        }
+        const int r0 = m0 + g, c0 = n0 + 2 * tg;
+        if (r0 < b) {
+            if (c0 < na) store(r0, c0, acc[0]);
+            if (c0 + 1 < na) store(r0, c0 + 1, acc[1]);
+        }
+        if (r0 + 8 < b) {
+            if (c0 < na) store(r0 + 8, c0, acc[2]);
+            if (c0 + 1 < na) store(r0 + 8, c0 + 1, acc[3]);
+        }
+    }
+}
+
+// Dispatch: RT > 0 selects the SIMT tile with RT rows per thread, RT == 0 the
+// 3xTF32 tensor-core path (FP32 operands only).
+template <typename T, int RT, typename Store>
+__device__ __forceinline__ void block_product(const T* Wsm, const T* Z, int b, int na, int mpad, Store store) {
+    if constexpr (RT == 0) {
+        if constexpr (std::is_same<T, float>::value) block_gemm_tc(Wsm, Z, b, na, mpad, store);
+    } else {
+        block_gemm<T, RT>(Wsm, Z, b, na, mpad, store);
+    }
+}
+
 struct LocalArgs {
     const SubInfo* subs;
     const FaceInfo* faces;
@@ -550,7 +621,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             if (tx == 0) nrm[jj] += rr;          // column jj belongs to warp ty only: fixed order
         }
         __syncthreads();
-        block_gemm<T, RT>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
+        block_product<T, RT>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
             Yp[i * mpad + jj] = v;
             Ys[(long long)cols[jj] * N + base + i] = v;
         });
@@ -574,7 +645,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = cp.t(base + i) * Yp[i * mpad + jj];
             __syncthreads();
-            block_gemm<T, RT>(Wsm, Z, b, na, mpad, finish);
+            block_product<T, RT>(Wsm, Z, b, na, mpad, finish);
         } else {
             for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) finish(i, jj, (T)0);
@@ -623,9 +694,10 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     }
 }
 
-// Tunable variants of the local solve (threads per CTA x GEMM rows per thread).
-constexpr int kNumSolveVariants = 6;
-__host__ __device__ inline int variant_threads(int v) { return v < 3 ? 256 : 128; }
+// Tunable variants of the local solve: threads per CTA x block-product path
+// (SIMT with 2, 1 or 4 rows per thread, or 3xTF32 tensor cores for FP32).
+constexpr int kNumSolveVariants = 8;
+__host__ __device__ inline int variant_threads(int v) { return v == 6 ? 256 : v == 7 ? 128 : v < 3 ? 256 : 128; }
 
 template <typename T, bool kScaled, bool kSweep>
 const void* solve_kernel(int v) {
@@ -635,7 +707,13 @@ const void* solve_kernel(int v) {
         case 2: return (const void*)k_local_solve<T, kScaled, kSweep, 256, 4>;
         case 3: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 2>;
         case 4: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 1>;
-        default: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 4>;
+        case 5: return (const void*)k_local_solve<T, kScaled, kSweep, 128, 4>;
+        case 6:
+            if constexpr (std::is_same<T, float>::value) return (const void*)k_local_solve<T, kScaled, kSweep, 256, 0>;
+            else return (const void*)k_local_solve<T, kScaled, kSweep, 256, 2>;
+        default:
+            if constexpr (std::is_same<T, float>::value) return (const void*)k_local_solve<T, kScaled, kSweep, 128, 0>;
+            else return (const void*)k_local_solve<T, kScaled, kSweep, 128, 2>;
     }
 }
 

@@ -172,7 +172,7 @@ def test_autotune_and_cache(tmp_path):
     s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
     s.factor_local(K)
     v0, v1 = s.autotune(f)
-    assert 0 <= v0 < 6 and 0 <= v1 < 6
+    assert 0 <= v0 < 8 and 0 <= v1 < 8
     line = open(cache).read().split()
     assert int(line[1]) == v0 and int(line[2]) == v1
     p, u, X, _ = s.solve(K, f)
@@ -213,3 +213,29 @@ def test_repeat_calls_are_deterministic():
     p1, X1 = p1.clone(), X1.clone()
     p2, u2, X2, _ = s.solve(K, f)
     assert T.equal(p1, p2) and T.equal(X1, X2)
+
+
+@pytest.mark.parametrize("name", ["many_tiles", "uneven_mix"])
+def test_every_solve_variant_matches_oracle(name, tmp_path):
+    """Each local-solve variant (SIMT tiles and the 3xTF32 tensor-core block
+    products), forced through the tune cache, reaches the mixed-mode bar."""
+    import torch as T
+    from paper_2103_08513_gb300 import MRCM
+    w = small(**(CASES.get(name) or UNEVEN[name]))
+    prob = oracle.from_workload(w)
+    r = oracle.solve_mrcm(prob)
+    K = T.from_numpy(prob.K).cuda()
+    f = T.from_numpy(prob.f).cuda()
+    cache = str(tmp_path / "tune.txt")
+    s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
+    s.factor_local(K)
+    s.autotune(f)
+    key = open(cache).read().split()[0]
+    for v in range(8):
+        with open(cache, "w") as fp:
+            fp.write(f"{key} {v} {v}\n")
+        sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
+        p, u, X, _ = sv.solve(K, f)
+        assert rel_l2(X.cpu().numpy(), r.X) < 1e-8, v
+        assert rel_l2(p.cpu().numpy().ravel(), r.p) < 1e-8, v
+        assert rel_l2(u.cpu().numpy().ravel(), r.u.ravel()) < 1e-8, v
