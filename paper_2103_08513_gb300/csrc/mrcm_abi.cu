@@ -69,7 +69,7 @@ mrcm_status ensure_device(mrcm_handle* h, void* stream) {
     UP(Ilist, t.Ilist);
     UP(class_list, t.class_list);
     UP(solve_list, t.solve_list);
-    for (int q = 0; q < 3; ++q) d.class_off[q] = t.class_off[q];
+    for (int q = 0; q < 4; ++q) d.class_off[q] = t.class_off[q];
     UP(rowptr, t.rowptr);
     UP(colidx, t.colidx);
     UP(src_lo, t.src_lo);

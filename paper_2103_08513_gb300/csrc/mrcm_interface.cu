@@ -43,8 +43,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPanel = 32;        // LDL^T panel width
-constexpr int kRowTile = 256;     // rows per panel-solve CTA
-constexpr int kTile = 64;         // trailing-update and assembly tile
+constexpr int kTile = 64;         // assembly tile
 constexpr int kRefine = 1;        // FP64 refinement steps of the interface solve
 
 __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const long long* __restrict__ src_lo,
@@ -74,11 +73,68 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // entries at the same dofs -- J-signed, scaled subdomain blocks for leaves,
 // the lower triangle of the Schur complement otherwise.  64x64 tiles of the
 // lower triangle are spread over the grid; blockIdx.y selects the front.
+// LDL^T of the nbk x nbk (nbk <= 32) diagonal block of a front, in place
+// (strict lower part becomes L11, the diagonal D), together with V = L11^{-1}.
+// Row i of the work array T holds [row i of the block | row i of V]; V starts
+// as I.  Step k, with l_i = T[i][k] / d_k for i > k, applies to every row
+// i > k the single update T[i][:] -= l_i u with
+//   u = [ T[j][k] for j > k, 0 for j <= k  |  V[k][:] ],
+// which is the rank-1 Schur update of the block and V <- (I - l e_k^T) V at
+// once (row k of V is final at step k).  One division per step, done by one
+// thread.  A zero or NaN pivot is replaced by 1 and counted.  Block-wide.
+constexpr int kDiagW = 2 * kPanel + 1;
+__device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
+                                  int* status) {
+    __shared__ double T[kPanel][kDiagW];
+    __shared__ double u[2 * kPanel];
+    __shared__ double lcol[kPanel];
+    __shared__ int zero;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    __syncthreads();                                          // the block's last writes are complete
+    for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
+        const int i = e >> 6, c = e & 63;
+        double v;
+        if (c < kPanel) v = (i < nbk && c <= i) ? A[(long long)(k0 + i) * n + k0 + c] : 0.0;
+        else v = (c - kPanel == i) ? 1.0 : 0.0;
+        T[i][c] = v;
+    }
+    if (tid == 0) zero = 0;
+    for (int k = 0; k < nbk; ++k) {
+        __syncthreads();
+        if (tid < 32) {                                       // pivot, l and u of this step (one warp)
+            double d = T[k][k];
+            if (d == 0.0 || d != d) { d = 1.0; if (tid == 0) { zero = 1; T[k][k] = 1.0; } }
+            double inv = 0.0;
+            if (tid == 0) inv = 1.0 / d;
+            inv = __shfl_sync(0xffffffffu, inv, 0);
+            const int i = tid;
+            const double tik = T[i][k];                       // column k (lower part, i > k)
+            lcol[i] = i > k && i < nbk ? tik * inv : 0.0;
+            u[i] = i > k && i < nbk ? tik : 0.0;
+            u[kPanel + i] = T[k][kPanel + i];
+        }
+        __syncthreads();
+        for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
+            const int i = e >> 6, c = e & 63;
+            if (i > k && i < nbk && (c >= kPanel || c <= i)) T[i][c] = fma(-lcol[i], u[c], T[i][c]);
+        }
+        __syncthreads();
+        if (tid < 32 && tid > k && tid < nbk) T[tid][k] = lcol[tid];
+    }
+    __syncthreads();
+    for (int e = tid; e < kPanel * kPanel; e += nthr) {
+        const int i = e >> 5, c = e & 31;
+        if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = T[i][c];
+        Pinv[e] = T[i][kPanel + c];
+    }
+    if (tid == 0 && zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                  const int* __restrict__ inv, const int* __restrict__ dofs, const SubInfo* __restrict__ subs,
                  const double* __restrict__ elem, const double* __restrict__ dscale, int NV,
-                 double* __restrict__ F) {
+                 double* __restrict__ F, double* __restrict__ P, int* __restrict__ status) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     const int n = fr.n;
     const int nt = (n + kTile - 1) / kTile;
@@ -131,94 +187,64 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
         if (r == fr.pin_row && q == fr.pin_row) v -= 1.0;
         Fm[(long long)r * n + q] = v;
     }
+    if (t == 0 && fr.ne > 0)                // first panel's diagonal block (inside tile (0, 0))
+        factor_diag_block(Fm, n, 0, min(kPanel, fr.ne), P + (long long)fr.p_off * kPanel * kPanel, status);
 }
 
-// Panel step of the blocked LDL^T: every CTA factors the diagonal block
-// [k0, k0+nbk) of its front in shared memory (redundantly: the factored
-// block must not be written to the front while other CTAs of the same launch
-// still read it), then solves its tile of rows below, l = f L11^{-T} D^{-1},
-// one thread per row.  CTA x = 0 leaves the factored block (L11 strict lower,
-// D on the diagonal) in `scratch`; the trailing-update kernel copies it into
-// the front.
-__global__ void __launch_bounds__(kThreads)
-k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0,
-            const double* __restrict__ F, double* __restrict__ Fw, double* __restrict__ scratch,
-            int* __restrict__ status) {
+// Panel step of the blocked LDL^T: the rows below the (already factored)
+// diagonal block, l = a L11^{-T} D^{-1}, i.e. l_j = sum_{k <= j} a_k V[j][k] / d_j
+// with V = L11^{-1}.  One warp per row, lane j computes l_j; kPanelRows rows
+// per CTA so that even one large front spreads over the GPU.
+constexpr int kPanelRows = 8;
+__global__ void __launch_bounds__(128)
+k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
+            const double* __restrict__ P) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
     const int nbk = min(kPanel, fr.ne - k0);
-    const int r0 = k0 + nbk + blockIdx.x * kRowTile;
-    if (blockIdx.x > 0 && r0 >= n) return;
-    const double* A = F + fr.f_off;
-    __shared__ double L[kPanel][kPanel + 1];
+    const int k1 = k0 + nbk;
+    const int r0 = k1 + blockIdx.x * kPanelRows;
+    if (r0 >= n) return;
+    double* A = F + fr.f_off;
+    __shared__ double Vs[kPanel][kPanel + 1];
     __shared__ double Dinv[kPanel];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
-    for (int i = ty; i < kPanel; i += 8) L[i][tx] = (i < nbk && tx <= i) ? A[(long long)(k0 + i) * n + k0 + tx] : 0.0;
+    const double* V = P + (long long)(fr.p_off + k0 / kPanel) * kPanel * kPanel;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
+    if (threadIdx.x < kPanel) Dinv[threadIdx.x] = threadIdx.x < nbk ? 1.0 / A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
     __syncthreads();
-    int zero = 0;
-    for (int k = 0; k < nbk; ++k) {
-        if (threadIdx.x == 0) {
-            double d = L[k][k];
-            if (d == 0.0 || d != d) { zero = 1; d = 1.0; L[k][k] = 1.0; }
-            Dinv[k] = 1.0 / d;
+    for (int q = w; q < kPanelRows; q += 4) {
+        const int r = r0 + q;
+        if (r >= n) break;
+        double* row = A + (long long)r * n + k0;
+        const double a = lane < nbk ? row[lane] : 0.0;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < kPanel; ++k) {
+            const double ak = __shfl_sync(0xffffffffu, a, k);
+            acc = fma(ak, Vs[lane][k], acc);                 // V[j][k] = 0 for k > j
         }
-        __syncthreads();
-        const double inv = Dinv[k];
-        // l_ik for i > k (column k scaled in place after the trailing update below)
-        for (int i = k + 1 + ty; i < nbk; i += 8) {
-            const double lik = L[i][k] * inv;
-            for (int j = k + 1 + tx; j <= i; j += 32) L[i][j] -= lik * L[j][k];
-        }
-        __syncthreads();
-        if (threadIdx.x < 32 && k + 1 + tx < nbk) L[k + 1 + tx][k] *= inv;
-        __syncthreads();
-    }
-    if (blockIdx.x == 0) {
-        double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
-        for (int i = ty; i < nbk; i += 8) sc[i * kPanel + tx] = (tx <= i) ? L[i][tx] : 0.0;
-        if (zero && threadIdx.x == 0) atomicAdd(&status[ST_ZERO_PIVOT], 1);
-    }
-    const int r = r0 + threadIdx.x;
-    if (r < n) {
-        double* row = Fw + fr.f_off + (long long)r * n + k0;
-        double w[kPanel];
-#pragma unroll
-        for (int j = 0; j < kPanel; ++j) w[j] = j < nbk ? row[j] : 0.0;
-#pragma unroll
-        for (int j = 0; j < kPanel; ++j) {
-            double acc = w[j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) acc -= w[k] * L[j][k];
-            w[j] = acc;
-        }
-#pragma unroll
-        for (int j = 0; j < kPanel; ++j)
-            if (j < nbk) row[j] = w[j] * Dinv[j];
+        if (lane < nbk) row[lane] = acc * Dinv[lane];
     }
 }
 
-// Trailing update of the blocked LDL^T: F22 -= L21 D L21^T on 64x64 tiles of
-// the lower triangle; blockIdx.x enumerates the (ti >= tj) tile pairs.
+// Trailing update of the blocked LDL^T: F22 -= L21 D L21^T on 32 x 32 tiles
+// of the lower triangle (FP64 arithmetic bounds this, so small tiles that
+// spread one front's update over many SMs beat register reuse); blockIdx.x
+// enumerates the (ti >= tj) tile pairs.  The CTA of tile (0, 0), which holds
+// the next panel's diagonal block, factors that block afterwards.
 __global__ void __launch_bounds__(kThreads)
 k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
-             const double* __restrict__ scratch) {
+             double* __restrict__ P, int* __restrict__ status) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
     const int nbk = min(kPanel, fr.ne - k0);
     const int k1 = k0 + nbk;
     const int m = n - k1;
-    if (blockIdx.x == 0) {                  // commit the factored diagonal block of this panel
-        const double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
-        double* A0 = F + fr.f_off;
-        for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) {
-            const int i = e >> 5, j = e & 31;
-            if (i < nbk && j <= i) A0[(long long)(k0 + i) * n + k0 + j] = sc[e];
-        }
-    }
     if (m <= 0) return;
-    const int nt = (m + kTile - 1) / kTile;
+    const int nt = (m + kPanel - 1) / kPanel;
     const int T = nt * (nt + 1) / 2;
     const int t = blockIdx.x;
     if (t >= T) return;
@@ -227,58 +253,52 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
     while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
     const int tj = t - ti * (ti + 1) / 2;
     double* A = F + fr.f_off;
-    __shared__ double Li[kTile][kPanel + 1];
-    __shared__ double Lj[kTile][kPanel + 1];
+    __shared__ double Li[kPanel][kPanel + 1];
+    __shared__ double Lj[kPanel][kPanel + 1];
     __shared__ double Dk[kPanel];
-    {
-        const double* sc = scratch + (long long)blockIdx.y * kPanel * kPanel;
-        for (int k = threadIdx.x; k < kPanel; k += blockDim.x) Dk[k] = k < nbk ? sc[k * kPanel + k] : 0.0;
+    if (threadIdx.x < kPanel) Dk[threadIdx.x] = threadIdx.x < nbk ? A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    const int i0 = k1 + ti * kPanel, j0 = k1 + tj * kPanel;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int a = w; a < kPanel; a += kThreads / 32) {
+        const int gi = i0 + a, gj = j0 + a;
+        Li[a][lane] = (gi < n && lane < nbk) ? A[(long long)gi * n + k0 + lane] * Dk[lane] : 0.0;
+        Lj[a][lane] = (gj < n && lane < nbk) ? A[(long long)gj * n + k0 + lane] : 0.0;
     }
     __syncthreads();
-    const int i0 = k1 + ti * kTile, j0 = k1 + tj * kTile;
-    for (int e = threadIdx.x; e < kTile * kPanel; e += blockDim.x) {
-        int a = e / kPanel, k = e % kPanel;
-        int gi = i0 + a, gj = j0 + a;
-        Li[a][k] = (gi < n && k < nbk) ? A[(long long)gi * n + k0 + k] * Dk[k] : 0.0;
-        Lj[a][k] = (gj < n && k < nbk) ? A[(long long)gj * n + k0 + k] : 0.0;
-    }
-    __syncthreads();
-    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    double acc[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;       // 16 x 16 threads, 2 x 2 outputs each
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll 4
     for (int k = 0; k < nbk; ++k) {
-        double a[4], bb[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) a[p] = Li[ty + 16 * p][k];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bb[q] = Lj[tx + 16 * q][k];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * bb[q];
+        const double a0 = Li[ty][k], a1 = Li[ty + 16][k];
+        const double b0 = Lj[tx][k], b1 = Lj[tx + 16][k];
+        acc[0][0] = fma(a0, b0, acc[0][0]); acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]); acc[1][1] = fma(a1, b1, acc[1][1]);
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        int gi = i0 + ty + 16 * p;
+    for (int p = 0; p < 2; ++p) {
+        const int gi = i0 + ty + 16 * p;
         if (gi >= n) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int gj = j0 + tx + 16 * q;
-            if (gj < n && gj <= gi) A[(long long)gi * n + gj] -= acc[p][q];
+        for (int q = 0; q < 2; ++q) {
+            const int gj = j0 + tx + 16 * q;
+            if (gj <= gi) A[(long long)gi * n + gj] -= acc[p][q];
         }
+    }
+    if (t == 0 && k1 < fr.ne) {
+        const int nb2 = min(kPanel, fr.ne - k1);
+        factor_diag_block(A, n, k1, nb2, P + (long long)(fr.p_off + k1 / kPanel) * kPanel * kPanel, status);
     }
 }
 
-// Forward substitution of one front: r = children's reduced rhs + the scaled,
-// J-signed global rhs of its E dofs; then L y = r over the E columns.  y_E is
-// divided by D; the reduced B part stays in frhs for the parent.
+// Forward substitution, eliminated part of one front (one CTA per front):
+// r = children's reduced rhs + the scaled, J-signed global rhs of its E dofs,
+// then L_EE y = r_E panel by panel (y_p = V_p r_p, rows below updated).  y_E
+// and the B part of r (not yet reduced by y_E) go to frhs.
 __global__ void __launch_bounds__(kThreads)
 k_front_forward(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                 const int* __restrict__ maps, const int* __restrict__ dofs,
-                const double* __restrict__ F, const double* __restrict__ bglob,
+                const double* __restrict__ F, const double* __restrict__ P, const double* __restrict__ bglob,
                 const double* __restrict__ dscale, int NV, double* __restrict__ frhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* r = reinterpret_cast<double*>(smem_raw);
@@ -286,6 +306,7 @@ k_front_forward(const FrontInfo* __restrict__ fronts, const int* __restrict__ id
     const int n = fr.n, ne = fr.ne;
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         double v = 0.0;
         if (q < ne) { int d = fd[q]; v = dof_sign(d, NV) * dscale[d] * bglob[d]; }
@@ -300,35 +321,90 @@ k_front_forward(const FrontInfo* __restrict__ fronts, const int* __restrict__ id
         for (int q = threadIdx.x; q < cf.nb; q += blockDim.x) r[mp[q]] += frhs[cf.r_off + cf.ne + q];
         __syncthreads();
     }
+    __shared__ double Vs[kPanel][kPanel + 1];
     for (int k0 = 0; k0 < ne; k0 += kPanel) {
-        const int k1 = min(ne, k0 + kPanel);
-        if (threadIdx.x < 32) {
-            for (int k = k0; k < k1; ++k) {
-                double rk = r[k];
-                __syncwarp();
-                int i = k + 1 + threadIdx.x;
-                if (i < k1) r[i] -= A[(long long)i * n + k] * rk;
-                __syncwarp();
-            }
+        const int nbk = min(kPanel, ne - k0), k1 = k0 + nbk;
+        const double* V = P + (long long)(fr.p_off + k0 / kPanel) * kPanel * kPanel;
+        for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
+        __syncthreads();
+        if (w == 0) {
+            const double rk = lane < nbk ? r[k0 + lane] : 0.0;
+            double y = 0.0;
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) y = fma(Vs[lane][k], __shfl_sync(0xffffffffu, rk, k), y);
+            if (lane < nbk) r[k0 + lane] = y;
         }
         __syncthreads();
-        for (int i = k1 + threadIdx.x; i < n; i += blockDim.x) {
-            double acc = r[i];
-            const double* row = A + (long long)i * n;
-            for (int k = k0; k < k1; ++k) acc -= row[k] * r[k];
-            r[i] = acc;
+        for (int i = k1 + threadIdx.x; i < ne; i += blockDim.x) {       // one thread per row: 32 loads in flight
+            const double* row = A + (long long)i * n + k0;
+            double v = 0.0;
+            if (nbk == kPanel) {
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) v = fma(row[k], r[k0 + k], v);
+            } else {
+                for (int k = 0; k < nbk; ++k) v = fma(row[k], r[k0 + k], v);
+            }
+            r[i] -= v;
         }
         __syncthreads();
     }
     double* out = frhs + fr.r_off;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) out[q] = q < ne ? r[q] / A[(long long)q * n + q] : r[q];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) out[q] = r[q];
 }
 
-// Backward substitution of one front: x_B (scaled) from the ancestors, then
-// L_EE^T x_E = z_E - L_BE^T x_B.
+// Forward substitution, boundary rows: r_B -= L_BE y_E, one warp per row,
+// kSolveRows rows per CTA, many CTAs per front.
+constexpr int kSolveRows = 8;
+__global__ void __launch_bounds__(kThreads)
+k_front_forward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const double* __restrict__ F,
+                  double* __restrict__ frhs) {
+    const FrontInfo fr = fronts[ids[blockIdx.y]];
+    const int n = fr.n, ne = fr.ne;
+    const int i = ne + blockIdx.x * kSolveRows + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int lane = threadIdx.x & 31;
+    const double* row = F + fr.f_off + (long long)i * n;
+    double* rr = frhs + fr.r_off;
+    double v = 0.0;
+    for (int k = lane; k < ne; k += 32) v = fma(row[k], rr[k], v);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) rr[i] -= v;
+}
+
+// Backward substitution, boundary columns: w_E = D^{-1} y_E - L_BE^T x_B, with
+// x_B (scaled) from the ancestors.  32 columns x 8 row groups per CTA.
+__global__ void __launch_bounds__(kThreads)
+k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const int* __restrict__ dofs,
+                   const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs) {
+    const FrontInfo fr = fronts[ids[blockIdx.y]];
+    const int n = fr.n, ne = fr.ne;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= ne) return;
+    const double* A = F + fr.f_off;
+    const int* fd = dofs + fr.e_dof_off;
+    __shared__ double part[kThreads / 32][32];
+    double v = 0.0;
+    if (i < ne) {
+#pragma unroll 4
+        for (int j = ne + g; j < n; j += kThreads / 32) v = fma(A[(long long)j * n + i], xs[fd[j]], v);
+    }
+    part[g][lane] = v;
+    __syncthreads();
+    if (g == 0 && i < ne) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) s += part[q][lane];
+        double* z = frhs + fr.r_off;
+        z[i] = z[i] / A[(long long)i * n + i] - s;
+    }
+}
+
+// Backward substitution, eliminated part (one CTA per front): L_EE^T x_E = w_E
+// panel by panel from the last (x_p = V_p^T w_p, earlier entries updated).
 __global__ void __launch_bounds__(kThreads)
 k_front_backward(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
-                 const int* __restrict__ dofs, const double* __restrict__ F,
+                 const int* __restrict__ dofs, const double* __restrict__ F, const double* __restrict__ P,
                  const double* __restrict__ frhs, double* __restrict__ xs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* w = reinterpret_cast<double*>(smem_raw);
@@ -336,28 +412,32 @@ k_front_backward(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
     const int n = fr.n, ne = fr.ne;
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
-        double acc = frhs[fr.r_off + i];
-        for (int j = ne; j < n; ++j) acc -= A[(long long)j * n + i] * xs[fd[j]];
-        w[i] = acc;
-    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) w[i] = frhs[fr.r_off + i];
     __syncthreads();
+    __shared__ double Vs[kPanel][kPanel + 1];
     const int nblk = (ne + kPanel - 1) / kPanel;
     for (int bk = nblk - 1; bk >= 0; --bk) {
-        const int k0 = bk * kPanel, k1 = min(ne, k0 + kPanel);
-        if (threadIdx.x < 32) {
-            for (int k = k1 - 1; k >= k0; --k) {
-                double xk = w[k];
-                __syncwarp();
-                int i = k0 + threadIdx.x;
-                if (i < k) w[i] -= A[(long long)k * n + i] * xk;
-                __syncwarp();
-            }
+        const int k0 = bk * kPanel, nbk = min(kPanel, ne - k0);
+        const double* V = P + (long long)(fr.p_off + bk) * kPanel * kPanel;
+        for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
+        __syncthreads();
+        if (wp == 0) {
+            const double wk = lane < nbk ? w[k0 + lane] : 0.0;
+            double x = 0.0;
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) x = fma(Vs[k][lane], __shfl_sync(0xffffffffu, wk, k), x);
+            if (lane < nbk) w[k0 + lane] = x;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < k0; i += blockDim.x) {
+        for (int i = threadIdx.x; i < k0; i += blockDim.x) {            // coalesced over i
             double acc = w[i];
-            for (int k = k0; k < k1; ++k) acc -= A[(long long)k * n + i] * w[k];
+            if (nbk == kPanel) {
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) acc = fma(-A[(long long)(k0 + k) * n + i], w[k0 + k], acc);
+            } else {
+                for (int k = 0; k < nbk; ++k) acc = fma(-A[(long long)(k0 + k) * n + i], w[k0 + k], acc);
+            }
             w[i] = acc;
         }
         __syncthreads();
@@ -386,22 +466,24 @@ __global__ void k_unscale(int n, const double* __restrict__ xs, const double* __
     x[i] = accumulate ? x[i] + v : v;
 }
 
-struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; };
+struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols; };
 
 LevelPlan plan_level(const Tables& t, int h) {
     LevelPlan p;
-    int max_ne = 0;
-    for (int id : t.levels[h]) max_ne = std::max(max_ne, t.fronts[id].ne);
+    int max_ne = 0, max_nb = 0;
+    for (int id : t.levels[h]) { max_ne = std::max(max_ne, t.fronts[id].ne); max_nb = std::max(max_nb, t.fronts[id].nb); }
     p.steps = (max_ne + kPanel - 1) / kPanel;
+    p.fwd_rows = std::max(1, (max_nb + kSolveRows - 1) / kSolveRows);
+    p.bwd_cols = std::max(1, (max_ne + 31) / 32);
     for (int s = 0; s < p.steps; ++s) {
-        int k0 = s * kPanel, rt = 1, ut = 0;
+        int k0 = s * kPanel, rt = 1, ut = 1;
         for (int id : t.levels[h]) {
             const FrontInfo& f = t.fronts[id];
             if (k0 >= f.ne) continue;
             int k1 = k0 + std::min(kPanel, f.ne - k0);
             int m = f.n - k1;
-            rt = std::max(rt, (m + kRowTile - 1) / kRowTile);
-            int nt = (m + kTile - 1) / kTile;
+            rt = std::max(rt, (m + kPanelRows - 1) / kPanelRows);
+            int nt = (m + kPanel - 1) / kPanel;
             ut = std::max(ut, nt * (nt + 1) / 2);
         }
         p.row_tiles.push_back(rt);
@@ -423,7 +505,7 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
                                                    (double*)(ws + L.b_int), dscale));
     // numeric multifrontal factorisation, leaves to root
     double* F = (double*)(ws + L.fronts);
-    double* scratch = (double*)(ws + L.panel);
+    double* Pv = (double*)(ws + L.panel);       // inverse diagonal blocks of the panels
     int* status = (int*)(ws + L.status);
     for (size_t h = 1; h < t.levels.size(); ++h) {
         int cnt = (int)t.levels[h].size();
@@ -433,14 +515,13 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
         for (int id : t.levels[h]) { int nt = (t.fronts[id].n + kTile - 1) / kTile; maxT = std::max(maxT, nt * (nt + 1) / 2); }
         dim3 ga(maxT, cnt);
         MRCM_LAUNCH(P, "k_front_assemble", st, k_front_assemble<<<ga, kThreads, 0, st>>>(d.fronts, ids, d.front_inv, d.front_dofs, d.subs,
-                                                  (const double*)(ws + L.elem), dscale, t.NV, F));
+                                                  (const double*)(ws + L.elem), dscale, t.NV, F, Pv, status));
         LevelPlan p = plan_level(t, (int)h);
         for (int s = 0; s < p.steps; ++s) {
             dim3 gp(p.row_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, F,
-                                                                                 scratch, status));
-            dim3 gu(std::max(1, p.upd_tiles[s]), cnt);
-            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, scratch));
+            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, 128, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv));
+            dim3 gu(p.upd_tiles[s], cnt);
+            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, status));
         }
     }
     return (int)cudaGetLastError();
@@ -449,19 +530,26 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
 static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                                const double* rhs, double* xs, cudaStream_t st, Prof& P) {
     double* F = (double*)(ws + L.fronts);
+    const double* Pv = (const double*)(ws + L.panel);
     double* frhs = (double*)(ws + L.frhs);
     const double* dscale = (const double*)(ws + L.dscale);
     size_t sm = sizeof(double) * (size_t)std::max(t.max_front, 1);
     for (size_t h = 1; h < t.levels.size(); ++h) {
         int cnt = (int)t.levels[h].size();
         if (!cnt) continue;
-        MRCM_LAUNCH(P, "k_front_forward", st, k_front_forward<<<cnt, kThreads, sm, st>>>(d.fronts, d.level_ids + d.level_off[h], d.front_maps,
-                                                  d.front_dofs, F, rhs, dscale, t.NV, frhs));
+        const int* ids = d.level_ids + d.level_off[h];
+        const LevelPlan p = plan_level(t, (int)h);
+        MRCM_LAUNCH(P, "k_front_forward", st, k_front_forward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_maps,
+                                                  d.front_dofs, F, Pv, rhs, dscale, t.NV, frhs));
+        MRCM_LAUNCH(P, "k_front_forward_b", st, k_front_forward_b<<<dim3(p.fwd_rows, cnt), kThreads, 0, st>>>(d.fronts, ids, F, frhs));
     }
     for (size_t h = t.levels.size() - 1; h >= 1; --h) {
         int cnt = (int)t.levels[h].size();
         if (!cnt) continue;
-        MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, d.level_ids + d.level_off[h], d.front_dofs, F,
+        const int* ids = d.level_ids + d.level_off[h];
+        const LevelPlan p = plan_level(t, (int)h);
+        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, 0, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
+        MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, Pv,
                                                    frhs, xs));
     }
 }

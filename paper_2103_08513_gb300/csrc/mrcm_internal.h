@@ -12,6 +12,7 @@ namespace mrcm {
 constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
 constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
+constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
 
 // One subdomain.  Local cells are numbered slab-major: the slab axis `sa` is
@@ -58,6 +59,7 @@ struct FrontInfo {
     int inv_off;            // offset (ints) of the front -> child position maps (2 x n, -1 = absent)
     int e_dof_off;          // offset (ints) into the global dof list of E then B
     int pin_row;            // front row of pi^p_0 when it is regularised, or -1
+    int p_off;              // first of its ceil(ne / 32) inverse diagonal blocks (32 x 32 each)
     int height;
     int parent;
 };
@@ -82,9 +84,9 @@ struct Tables {
     // (offsets into class_list); block factors are stored per wave (w_off is
     // relative to the wave) so one W region serves every wave
     std::vector<int> wave_off;
-    std::vector<int> wave_class_off;   // 3 entries per wave
+    std::vector<int> wave_class_off;   // 4 entries per wave (class boundaries)
     int n_waves = 1;
-    int class_off[3] = {0, 0, 0};  // class 0: b <= kRegBlock, class 1: larger blocks
+    int class_off[4] = {0, 0, 0, 0};  // class 0: b <= kRegBlock, 1: b <= kTileBlock, 2: larger (mixed); FP64: all in 2
     long long n_cells = 0, total_x = 0, total_w = 0, total_el = 0;
     int total_elb = 0;
     int max_m = 0, max_b = 0, max_el = 0, max_N = 0;
@@ -107,6 +109,7 @@ struct Tables {
     std::vector<std::vector<int>> levels;      // fronts grouped by height
     long long total_front = 0;
     int total_frhs = 0;
+    int total_panels = 0;          // sum over fronts of ceil(ne / 32)
     int max_front = 0;
     double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
@@ -125,7 +128,7 @@ struct DeviceTables {
     FaceInfo* faces = nullptr;
     int* Ilist = nullptr;
     int* class_list = nullptr;
-    int class_off[3] = {0, 0, 0};
+    int class_off[4] = {0, 0, 0, 0};
     int* solve_list = nullptr;                 // all subdomains, costliest solve first (wave by wave)
     int sms = 0;
     size_t solve_smem = 0;

@@ -343,6 +343,144 @@ k_block_factor_reg(const SubInfo* __restrict__ subs, const int* __restrict__ lis
 }
 
 // ---------------------------------------------------------------------------
+// Register-tiled variant for 64 < b <= 128 (FP32, scaled): 256 threads as a
+// 16 x 16 grid, thread (ty, tx) holds the 8 x 8 tile of rows 8 ty .. 8 ty + 7
+// and columns 8 tx .. 8 tx + 7 of the running block (rows and columns >= b
+// stay zero and are never pivoted).  Same sweep-operator Gauss-Jordan as the
+// kernels above: at step k the pivot row is published in shared memory
+// (double-buffered, one barrier per step) and column k is read back through
+// the sign symmetry M[i][k] = sigma_i M[k][i].  Every entry takes the generic
+// update M[i][j] -= M[i][k] M[k][j] / p; row k and column k are then set
+// exactly (M[k][j] / p, -M[i][k] / p and 1 / p).  W_{s-1} stays in the
+// registers to form S_s = D_s - t o W_{s-1} o t for the next slab.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 2)
+k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
+                    const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
+                    long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
+    constexpr int B = kTileBlock;
+    const SubInfo s = subs[list[blockIdx.x]];
+    const int b = s.b, su = s.su;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = ty * 8, j0 = tx * 8;
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* sc = scale + s.cell_off;
+    float* W = Wall + s.w_off;
+    __shared__ __align__(16) float prow[2][B];
+    __shared__ __align__(16) float sd[B], sup[B], svp[B], st[B];
+    float a[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[r][c] = 0.0f;
+    int bad = 0;
+    for (int sl = 0; sl < s.ns; ++sl) {
+        const int base = sl * b;
+        // scaled diagonal, +u and +v couplings inside the slab, coupling to slab sl - 1
+        for (int i = threadIdx.x; i < B; i += blockDim.x) {
+            float d = 0.f, u = 0.f, v = 0.f, t = 0.f;
+            if (i < b) {
+                const int c = base + i;
+                d = (float)(cd[c] * sc[c] * sc[c]);
+                if ((i % su) + 1 < su) u = (float)(-cu[c] * sc[c] * sc[c + 1]);
+                if (i + su < b) v = (float)(-cv[c] * sc[c] * sc[c + su]);
+                if (sl > 0) t = (float)(cs[c - b] * sc[c - b] * sc[c]);
+                scf_all[s.cell_off + c] = (float)sc[c];
+                tsc_all[s.cell_off + c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+            }
+            sd[i] = d; sup[i] = u; svp[i] = v; st[i] = t;
+        }
+        __syncthreads();
+        // S_s = D_s - t o W_{s-1} o t
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = i0 + r;
+            const float ti = st[i];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + c;
+                float v = -ti * st[j] * a[r][c];
+                if (j == i) v += sd[i];
+                if (j == i + 1) v += sup[i];
+                if (j + 1 == i) v += sup[j];
+                if (j == i + su) v += svp[i];
+                if (j + su == i) v += svp[j];
+                a[r][c] = (i < b && j < b) ? v : 0.0f;
+            }
+        }
+        // Gauss-Jordan sweep over the b pivots
+#pragma unroll 1
+        for (int k = 0; k < b; ++k) {
+            float* pr = prow[k & 1];
+            if (ty == (k >> 3)) {
+                const int rk = k & 7;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (r == rk) {
+                        reinterpret_cast<float4*>(pr + j0)[0] = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
+                        reinterpret_cast<float4*>(pr + j0)[1] = make_float4(a[r][4], a[r][5], a[r][6], a[r][7]);
+                    }
+            }
+            __syncthreads();
+            float p = pr[k];
+            if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+            const float ip = 1.0f / p;
+            const float4 q0 = reinterpret_cast<const float4*>(pr + j0)[0], q1 = reinterpret_cast<const float4*>(pr + j0)[1];
+            const float4 c0 = reinterpret_cast<const float4*>(pr + i0)[0], c1 = reinterpret_cast<const float4*>(pr + i0)[1];
+            const float rkv[8] = {q0.x * ip, q0.y * ip, q0.z * ip, q0.w * ip, q1.x * ip, q1.y * ip, q1.z * ip, q1.w * ip};
+            float ck[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (i0 + r < k) ck[r] = -ck[r];                   // M[i][k] = sigma_i M[k][i]
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-ck[r], rkv[c], a[r][c]);
+            if (ty == (k >> 3)) {                                 // row k: M[k][j] / p
+                const int rk = k & 7;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (r == rk) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) a[r][c] = rkv[c];
+                    }
+            }
+            if (tx == (k >> 3)) {                                 // column k: -M[i][k] / p, (k, k): 1 / p
+                const int ckc = k & 7;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c == ckc) {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) a[r][c] = (i0 + r == k) ? ip : -ck[r] * ip;
+                    }
+            }
+        }
+        // store W_s (full symmetric matrix, row major)
+        float* Ws = W + (long long)sl * b * b;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = i0 + r;
+            if (i < b) {
+                float* row = Ws + (long long)i * b + j0;
+                if ((b & 3) == 0 && j0 + 8 <= b) {
+                    reinterpret_cast<float4*>(row)[0] = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
+                    reinterpret_cast<float4*>(row)[1] = make_float4(a[r][4], a[r][5], a[r][6], a[r][7]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (j0 + c < b) row[c] = a[r][c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad && threadIdx.x == 0) atomicAdd(&status[ST_NOT_SPD], 1);
+}
+
+// ---------------------------------------------------------------------------
 // Multi-RHS block solve, fused with the right-hand sides (first solve) or with
 // the FP64 residual (refinement sweep).  One CTA per subdomain.
 //
@@ -791,21 +929,25 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
     double* coef = (double*)(ws + L.coef);
     double* scale = (double*)(ws + L.scale);
     int* status = (int*)(ws + L.status);
-    const int o0 = t.wave_class_off[3 * w], o1 = t.wave_class_off[3 * w + 1], o2 = t.wave_class_off[3 * w + 2];
-    const int n_small = o1 - o0, n_large = o2 - o1;
+    const int* wc = &t.wave_class_off[4 * w];
+    const int o0 = wc[0], o1 = wc[1], o2 = wc[2], o3 = wc[3];
+    const int n_small = o1 - o0, n_mid = o2 - o1, n_large = o3 - o2;
     if (precision == MRCM_FP64) {
         if (n_large > 0) {
             size_t sm = factor_smem<double>(t.max_b);
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o1, coef, scale,
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
                 (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
     } else {
         if (n_small > 0)
             MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
                 (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        if (n_mid > 0)
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
+                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         if (n_large > 0) {
             size_t sm = factor_smem<float>(t.max_b);
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o1, coef, scale,
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
                 (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
     }

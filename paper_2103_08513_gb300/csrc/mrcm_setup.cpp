@@ -270,24 +270,22 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         t.total_w = wmax;
         t.class_list.clear();
         for (int w = 0; w < t.n_waves; ++w) {
-            std::vector<std::pair<double, int>> c0, c1;
+            std::vector<std::pair<double, int>> cls[3];
             for (int q = t.wave_off[w]; q < t.wave_off[w + 1]; ++q) {
                 const int l = t.solve_list[q];
                 const SubInfo& s = t.subs[l];
                 const double cost = (double)s.ns * s.b * s.b * s.b;
-                if (cfg->precision != MRCM_FP64 && s.b <= kRegBlock) c0.push_back({-cost, l}); else c1.push_back({-cost, l});
+                const int k = cfg->precision == MRCM_FP64 ? 2 : s.b <= kRegBlock ? 0 : s.b <= kTileBlock ? 1 : 2;
+                cls[k].push_back({-cost, l});
             }
-            std::sort(c0.begin(), c0.end());
-            std::sort(c1.begin(), c1.end());
-            t.wave_class_off.push_back((int)t.class_list.size());
-            for (auto& pr : c0) t.class_list.push_back(pr.second);
-            t.wave_class_off.push_back((int)t.class_list.size());
-            for (auto& pr : c1) t.class_list.push_back(pr.second);
+            for (int k = 0; k < 3; ++k) {
+                std::sort(cls[k].begin(), cls[k].end());
+                t.wave_class_off.push_back((int)t.class_list.size());
+                for (auto& pr : cls[k]) t.class_list.push_back(pr.second);
+            }
             t.wave_class_off.push_back((int)t.class_list.size());
         }
-        t.class_off[0] = t.wave_class_off[0];
-        t.class_off[1] = t.wave_class_off[1];
-        t.class_off[2] = t.wave_class_off[2];
+        for (int k = 0; k < 4; ++k) t.class_off[k] = t.wave_class_off[k];
     }
     t.total_x = x_off;
     t.total_el = el_off;
@@ -349,6 +347,7 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
             t.levels[f.height].push_back(id);
             f.f_off = foff;  foff += (long long)f.n * f.n;
             f.r_off = roff;  roff += f.n;
+            f.p_off = t.total_panels;  t.total_panels += (f.ne + 31) / 32;
             t.max_front = std::max(t.max_front, f.n);
             for (int k0 = 0; k0 < f.ne; k0 += 32) {
                 const double nbk = std::min(32, f.ne - k0);
@@ -417,11 +416,7 @@ void compute_layout(const Tables& t, Layout& L) {
     L.dscale = take((size_t)2 * t.NV * sizeof(double));
     L.fronts = take((size_t)t.total_front * sizeof(double));
     L.frhs = take((size_t)t.total_frhs * sizeof(double));
-    {
-        size_t maxcnt = 1;
-        for (const auto& lv : t.levels) maxcnt = std::max(maxcnt, lv.size());
-        L.panel = take(maxcnt * 32 * 32 * sizeof(double));
-    }
+    L.panel = take((size_t)t.total_panels * 32 * 32 * sizeof(double));
     L.xres = take((size_t)2 * t.NV * sizeof(double));
     L.xtmp = take((size_t)2 * t.NV * sizeof(double));
     L.psum = take(((size_t)t.subs.size() + 64) * sizeof(double));

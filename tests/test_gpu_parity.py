@@ -94,6 +94,9 @@ UNEVEN = {
                        sigma=1.5, lam=5.0),
     "big_blocks": dict(n=(28, 16, 16), edges=([12, 16], [16], [16]), patch=((4, 4), (0, 0), (0, 0)),
                        sigma=1.0, lam=4.0),
+    # 16 x 16 x 8 subdomains with whole-face patches (b = 128, register-tiled factor), high contrast
+    "blocks_128": dict(n=(32, 16, 16), edges=([16, 16], [16], [8, 8]), patch=((0, 0), (0, 0), (0, 0)),
+                       sigma=3.0, lam=8.0),
 }
 
 
