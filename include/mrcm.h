@@ -98,7 +98,9 @@ enum {
  *                     factors fit the budget (the factors of one wave are
  *                     dropped before the next is factored); 0 = one wave
  *  tune_cache         path of the autotuner cache (text), or NULL; read at
- *                     the first device call, written by mrcm_autotune      */
+ *                     the first device call, written by mrcm_autotune
+ *  interface_refine   FP64 refinement steps of the interface solve after the
+ *                     LDL^T solve: 0 = default (1), -1 = none, k > 0 = k   */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -114,6 +116,7 @@ typedef struct {
     double ir_tol;
     size_t wave_bytes;
     const char* tune_cache;
+    int interface_refine;
 } mrcm_config;
 
 /* Sizes derived by mrcm_setup (host-side; no GPU needed). */

@@ -36,6 +36,7 @@ class mrcm_config(C.Structure):
         ("ir_tol", C.c_double),
         ("wave_bytes", C.c_size_t),
         ("tune_cache", C.c_char_p),
+        ("interface_refine", C.c_int),
     ]
 
 

@@ -31,9 +31,11 @@
 // factored by a blocked right-looking LDL^T (32-column panels, 64x64 update
 // tiles spread over the whole GPU), and leave the Schur complement on B for
 // their parent.  The solution is refined once in FP64 with CSR residuals.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "mrcm_internal.h"
 
@@ -44,7 +46,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPanel = 32;        // LDL^T panel width
 constexpr int kTile = 64;         // assembly tile
-constexpr int kRefine = 1;        // FP64 refinement steps of the interface solve
 
 __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const long long* __restrict__ src_lo,
                                const long long* __restrict__ src_hi, const int* __restrict__ rsl,
@@ -83,12 +84,13 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // once (row k of V is final at step k).  One division per step, done by one
 // thread.  A zero or NaN pivot is replaced by 1 and counted.  Block-wide.
 constexpr int kDiagW = 2 * kPanel + 1;
+constexpr int kDiagWork = kPanel * kDiagW + 3 * kPanel + 2;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
-                                  int* status) {
-    __shared__ double T[kPanel][kDiagW];
-    __shared__ double u[2 * kPanel];
-    __shared__ double lcol[kPanel];
-    __shared__ int zero;
+                                  int* status, double* work) {
+    double (*T)[kDiagW] = reinterpret_cast<double (*)[kDiagW]>(work);
+    double* u = work + kPanel * kDiagW;
+    double* lcol = u + 2 * kPanel;
+    int& zero = *reinterpret_cast<int*>(lcol + kPanel);
     const int tid = threadIdx.x, nthr = blockDim.x;
     __syncthreads();                                          // the block's last writes are complete
     for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
@@ -187,8 +189,10 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
         if (r == fr.pin_row && q == fr.pin_row) v -= 1.0;
         Fm[(long long)r * n + q] = v;
     }
-    if (t == 0 && fr.ne > 0)                // first panel's diagonal block (inside tile (0, 0))
-        factor_diag_block(Fm, n, 0, min(kPanel, fr.ne), P + (long long)fr.p_off * kPanel * kPanel, status);
+    if (t == 0 && fr.ne > 0) {              // first panel's diagonal block (inside tile (0, 0))
+        __shared__ double work[kDiagWork];
+        factor_diag_block(Fm, n, 0, min(kPanel, fr.ne), P + (long long)fr.p_off * kPanel * kPanel, status, work);
+    }
 }
 
 // Panel step of the blocked LDL^T: the rows below the (already factored)
@@ -196,9 +200,67 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
 // with V = L11^{-1}.  One warp per row, lane j computes l_j; kPanelRows rows
 // per CTA so that even one large front spreads over the GPU.
 constexpr int kPanelRows = 8;
+
+// Tensor-core emulation of the FP64 trailing update (Ozaki-type splitting
+// with exact integer arithmetic).  For each panel row x (of L21 D for the left
+// operand, of L21 for the right one) let E be the smallest power of two with
+// |x_k| < 2^E for every k of the row; |x_k| 2^{-E} is cut into S = 8 slices of
+// 7 bits, x_k = 2^E sum_t s_t 2^{-7(t+1)} + r with integer |s_t| <= 127 and
+// |r| < 2^{E-56} (sign carried by every slice), extracted from the bits of
+// the double with integer operations.  Then
+//   sum_k x_ik y_jk = 2^{E_i + F_j} sum_d P_d 2^{-7(d+2)},
+//   P_d = sum_{t+u=d} sum_k s_t(x_ik) s_u(y_jk),   d = 0 .. S-1
+// (terms with t + u >= S are below the FP64 rounding of the result).  Each
+// P_d is a BF16 MMA with FP32 accumulation whose every partial sum is an
+// integer below 2^22, hence exact; the P_d are combined exactly in 64-bit
+// integers and converted to FP64 once.  An update then costs about five FP64
+// operations per entry instead of one FMA per panel column.
+constexpr int kOzS = 8;                     // slices per operand
+constexpr int kOzRowWords = 2 * kOzS * kPanel / 2;   // u32 words per slice row (2 operands x 8 slices x 32 bf16)
+constexpr int kOzMinM = 64;                 // emulate when the trailing block has >= kOzMinM rows
+constexpr int kOzMinK = 16;                 // and the panel >= kOzMinK columns
+
+__device__ __forceinline__ bool oz_step(const FrontInfo& fr, int m, int nbk) {
+    return fr.s_off >= 0 && m >= kOzMinM && nbk >= kOzMinK;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Slices of x (one lane per column) into row `dst` (kOzS x 32 bf16) and its
+// exponent E into *exp_out (lane 0).
+__device__ __forceinline__ void oz_slice_row(double x, __nv_bfloat16* dst, int* exp_out) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;          // orders like |x|
+    const unsigned long long mx = warp_max_u64(mag);
+    const int emax = (int)(mx >> 52);
+    const int E = mx == 0 ? 0 : emax - 1023 + 1;                           // max |x| < 2^E
+    const int ex = (int)(mag >> 52);
+    unsigned long long Fx = 0;                                             // floor(|x| 2^{56-E})
+    if (ex != 0) {
+        const unsigned long long mant = (mag & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = ex - 1023 + 4 - E;                                  // <= 3
+        Fx = sh >= 0 ? (mant << sh) : (-sh < 64 ? (mant >> -sh) : 0ull);
+    }
+    const bool neg = (bits >> 63) != 0;
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t) {
+        int v = (int)((Fx >> (49 - 7 * t)) & 127ull);
+        dst[t * kPanel + lane] = __float2bfloat16_rn((float)(neg ? -v : v));
+    }
+    if (lane == 0) *exp_out = E;
+}
+
 __global__ void __launch_bounds__(128)
 k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
-            const double* __restrict__ P) {
+            const double* __restrict__ P, __nv_bfloat16* __restrict__ oz, int* __restrict__ oz_exp) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
@@ -208,11 +270,15 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
     if (r0 >= n) return;
     double* A = F + fr.f_off;
     __shared__ double Vs[kPanel][kPanel + 1];
-    __shared__ double Dinv[kPanel];
+    __shared__ double Dinv[kPanel], Dd[kPanel];
     const double* V = P + (long long)(fr.p_off + k0 / kPanel) * kPanel * kPanel;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
-    if (threadIdx.x < kPanel) Dinv[threadIdx.x] = threadIdx.x < nbk ? 1.0 / A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
+    if (threadIdx.x < kPanel) {
+        const double d = threadIdx.x < nbk ? A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
+        Dd[threadIdx.x] = d;
+        Dinv[threadIdx.x] = threadIdx.x < nbk ? 1.0 / d : 0.0;
+    }
     __syncthreads();
     for (int q = w; q < kPanelRows; q += 4) {
         const int r = r0 + q;
@@ -225,18 +291,38 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
             const double ak = __shfl_sync(0xffffffffu, a, k);
             acc = fma(ak, Vs[lane][k], acc);                 // V[j][k] = 0 for k > j
         }
-        if (lane < nbk) row[lane] = acc * Dinv[lane];
+        const double l = lane < nbk ? acc * Dinv[lane] : 0.0;
+        if (lane < nbk) row[lane] = l;
+        if (oz_step(fr, n - k1, nbk)) {
+            const long long sr = (long long)fr.s_off + r;
+            oz_slice_row(l * Dd[lane], oz + sr * (2 * kOzS * kPanel), oz_exp + 2 * sr);
+            oz_slice_row(l, oz + sr * (2 * kOzS * kPanel) + kOzS * kPanel, oz_exp + 2 * sr + 1);
+        }
     }
 }
 
+// BF16 m16n8k16 tensor-core MMA with FP32 accumulation (the emulated update
+// feeds it small integers, for which it is exact).
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
 // Trailing update of the blocked LDL^T: F22 -= L21 D L21^T on 32 x 32 tiles
-// of the lower triangle (FP64 arithmetic bounds this, so small tiles that
-// spread one front's update over many SMs beat register reuse); blockIdx.x
-// enumerates the (ti >= tj) tile pairs.  The CTA of tile (0, 0), which holds
-// the next panel's diagonal block, factors that block afterwards.
+// of the lower triangle (small tiles spread one front's update over many
+// SMs); blockIdx.x enumerates the (ti >= tj) tile pairs.  Large steps take
+// the tensor-core emulation above, the others plain FP64 FMAs.  The CTA of
+// tile (0, 0), which holds the next panel's diagonal block, factors that
+// block afterwards.
+constexpr int kOzLd = kOzRowWords / 2 + 4;  // u32 words per staged operand row (one operand, padded)
 __global__ void __launch_bounds__(kThreads)
 k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
-             double* __restrict__ P, int* __restrict__ status) {
+             double* __restrict__ P, int* __restrict__ status, const __nv_bfloat16* __restrict__ oz,
+             const int* __restrict__ oz_exp) {
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
@@ -253,41 +339,100 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
     while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
     const int tj = t - ti * (ti + 1) / 2;
     double* A = F + fr.f_off;
-    __shared__ double Li[kPanel][kPanel + 1];
-    __shared__ double Lj[kPanel][kPanel + 1];
-    __shared__ double Dk[kPanel];
-    if (threadIdx.x < kPanel) Dk[threadIdx.x] = threadIdx.x < nbk ? A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
-    __syncthreads();
+    __shared__ __align__(16) uint32_t sbuf[2 * kPanel * kOzLd];             // 33.8 KB, reused below
     const int i0 = k1 + ti * kPanel, j0 = k1 + tj * kPanel;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int a = w; a < kPanel; a += kThreads / 32) {
-        const int gi = i0 + a, gj = j0 + a;
-        Li[a][lane] = (gi < n && lane < nbk) ? A[(long long)gi * n + k0 + lane] * Dk[lane] : 0.0;
-        Lj[a][lane] = (gj < n && lane < nbk) ? A[(long long)gj * n + k0 + lane] : 0.0;
-    }
-    __syncthreads();
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;       // 16 x 16 threads, 2 x 2 outputs each
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    if (oz_step(fr, m, nbk)) {
+        uint32_t* Sa = sbuf;                                               // rows i: slices of L21 D
+        uint32_t* Sb = sbuf + kPanel * kOzLd;                              // rows j: slices of L21
+        const uint4* src = reinterpret_cast<const uint4*>(oz);
+        for (int e = threadIdx.x; e < 2 * kPanel * (kOzLd - 4) / 4; e += blockDim.x) {
+            const int op = e / (kPanel * (kOzLd - 4) / 4);
+            const int rem = e % (kPanel * (kOzLd - 4) / 4);
+            const int rr = rem / ((kOzLd - 4) / 4), q = rem % ((kOzLd - 4) / 4);
+            const int gr = (op == 0 ? i0 : j0) + rr;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gr < n) v = src[((long long)fr.s_off + gr) * (kOzRowWords / 4) + op * ((kOzLd - 4) / 4) + q];
+            reinterpret_cast<uint4*>((op == 0 ? Sa : Sb) + rr * kOzLd)[q] = v;
+        }
+        __syncthreads();
+        const int g = lane >> 2, tg = lane & 3;
+        const int mr = (w >> 2) * 16, nc = (w & 3) * 8;                   // this warp's 16 x 8 output block
+        long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < kOzS; ++d) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ts = 0; ts <= d; ++ts) {
+                const int us = d - ts;
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    const int wa = ts * (kPanel / 2) + kc * 8 + tg;
+                    const int wb = us * (kPanel / 2) + kc * 8 + tg;
+                    uint32_t af[4], bf[2];
+                    af[0] = Sa[(mr + g) * kOzLd + wa];
+                    af[1] = Sa[(mr + g + 8) * kOzLd + wa];
+                    af[2] = Sa[(mr + g) * kOzLd + wa + 4];
+                    af[3] = Sa[(mr + g + 8) * kOzLd + wa + 4];
+                    bf[0] = Sb[(nc + g) * kOzLd + wb];
+                    bf[1] = Sb[(nc + g) * kOzLd + wb + 4];
+                    mma_bf16(acc, af, bf);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long pv = (long long)__float2ll_rn(acc[q]);
+                if (d < 4) hi[q] += pv << (7 * (3 - d));
+                else lo[q] += pv << (7 * (7 - d));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gi = i0 + mr + g + (q >> 1) * 8;
+            const int gj = j0 + nc + 2 * tg + (q & 1);
+            if (gi < n && gj <= gi) {
+                const int e = oz_exp[2 * ((long long)fr.s_off + gi)] + oz_exp[2 * ((long long)fr.s_off + gj) + 1];
+                const double v = fma((double)lo[q], pow2(e - 63), (double)hi[q] * pow2(e - 35));
+                A[(long long)gi * n + gj] -= v;
+            }
+        }
+    } else {
+        double (*Li)[kPanel + 1] = reinterpret_cast<double (*)[kPanel + 1]>(sbuf);
+        double (*Lj)[kPanel + 1] = Li + kPanel;
+        __shared__ double Dk[kPanel];
+        if (threadIdx.x < kPanel) Dk[threadIdx.x] = threadIdx.x < nbk ? A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
+        __syncthreads();
+        for (int a = w; a < kPanel; a += kThreads / 32) {
+            const int gi = i0 + a, gj = j0 + a;
+            Li[a][lane] = (gi < n && lane < nbk) ? A[(long long)gi * n + k0 + lane] * Dk[lane] : 0.0;
+            Lj[a][lane] = (gj < n && lane < nbk) ? A[(long long)gj * n + k0 + lane] : 0.0;
+        }
+        __syncthreads();
+        const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;       // 16 x 16 threads, 2 x 2 outputs each
+        double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll 4
-    for (int k = 0; k < nbk; ++k) {
-        const double a0 = Li[ty][k], a1 = Li[ty + 16][k];
-        const double b0 = Lj[tx][k], b1 = Lj[tx + 16][k];
-        acc[0][0] = fma(a0, b0, acc[0][0]); acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]); acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
+        for (int k = 0; k < nbk; ++k) {
+            const double a0 = Li[ty][k], a1 = Li[ty + 16][k];
+            const double b0 = Lj[tx][k], b1 = Lj[tx + 16][k];
+            acc[0][0] = fma(a0, b0, acc[0][0]); acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]); acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int gi = i0 + ty + 16 * p;
-        if (gi >= n) continue;
+        for (int p = 0; p < 2; ++p) {
+            const int gi = i0 + ty + 16 * p;
+            if (gi >= n) continue;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int gj = j0 + tx + 16 * q;
-            if (gj <= gi) A[(long long)gi * n + gj] -= acc[p][q];
+            for (int q = 0; q < 2; ++q) {
+                const int gj = j0 + tx + 16 * q;
+                if (gj <= gi) A[(long long)gi * n + gj] -= acc[p][q];
+            }
         }
     }
     if (t == 0 && k1 < fr.ne) {
         const int nb2 = min(kPanel, fr.ne - k1);
-        factor_diag_block(A, n, k1, nb2, P + (long long)(fr.p_off + k1 / kPanel) * kPanel * kPanel, status);
+        __syncthreads();                                                   // shared buffer free for reuse
+        factor_diag_block(A, n, k1, nb2, P + (long long)(fr.p_off + k1 / kPanel) * kPanel * kPanel, status,
+                          reinterpret_cast<double*>(sbuf));
     }
 }
 
@@ -506,6 +651,8 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
     // numeric multifrontal factorisation, leaves to root
     double* F = (double*)(ws + L.fronts);
     double* Pv = (double*)(ws + L.panel);       // inverse diagonal blocks of the panels
+    __nv_bfloat16* oz = (__nv_bfloat16*)(ws + L.oz);
+    int* oz_exp = (int*)(ws + L.oz_exp);
     int* status = (int*)(ws + L.status);
     for (size_t h = 1; h < t.levels.size(); ++h) {
         int cnt = (int)t.levels[h].size();
@@ -519,9 +666,10 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
         LevelPlan p = plan_level(t, (int)h);
         for (int s = 0; s < p.steps; ++s) {
             dim3 gp(p.row_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, 128, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv));
+            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, 128, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, oz, oz_exp));
             dim3 gu(p.upd_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, status));
+            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, status,
+                                                                                   oz, oz_exp));
         }
     }
     return (int)cudaGetLastError();
@@ -575,7 +723,8 @@ int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout&
     const int pin = t.has_dirichlet ? 0 : 1;
     multifrontal_solve(t, d, L, ws, b, xs, st, P);
     MRCM_LAUNCH(P, "k_unscale", st, k_unscale<<<(nd + 255) / 256, 256, 0, st>>>(nd, xs, dscale, X, 0));
-    for (int it = 0; it < kRefine; ++it) {
+    const int refine = t.cfg.interface_refine == 0 ? 1 : std::max(0, t.cfg.interface_refine);
+    for (int it = 0; it < refine; ++it) {
         MRCM_LAUNCH(P, "k_csr_residual", st, k_csr_residual<<<(nd + 127) / 128, 128, 0, st>>>(nd, d.rowptr, d.colidx, (const double*)(ws + L.csr_val),
                                                        b, X, dscale, pin, r));
         multifrontal_solve(t, d, L, ws, r, xs, st, P);

@@ -12,6 +12,7 @@ namespace mrcm {
 constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
 constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
+constexpr int kOzMinN = 64;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
 constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
 
@@ -60,6 +61,7 @@ struct FrontInfo {
     int e_dof_off;          // offset (ints) into the global dof list of E then B
     int pin_row;            // front row of pi^p_0 when it is regularised, or -1
     int p_off;              // first of its ceil(ne / 32) inverse diagonal blocks (32 x 32 each)
+    int s_off;              // first row of its slice rows in the emulated-update buffer, or -1
     int height;
     int parent;
 };
@@ -110,6 +112,7 @@ struct Tables {
     long long total_front = 0;
     int total_frhs = 0;
     int total_panels = 0;          // sum over fronts of ceil(ne / 32)
+    long long oz_rows = 0;         // slice rows of the emulated trailing update (max over levels)
     int max_front = 0;
     double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
@@ -119,7 +122,7 @@ struct Tables {
 // Workspace layout (byte offsets into the caller's workspace).
 struct Layout {
     size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, W, X, R, colnorm, conv;
-    size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, xres, xtmp, psum, status;
+    size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t total;
 };
 

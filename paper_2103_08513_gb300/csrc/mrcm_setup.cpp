@@ -85,6 +85,7 @@ struct TreeBuilder {
 
 mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
     if (!cfg) { err = "config is NULL"; return MRCM_ERR_INVALID_ARG; }
+    if (cfg->interface_refine < -1) { err = "interface_refine must be >= -1"; return MRCM_ERR_INVALID_ARG; }
     t.cfg = *cfg;
     if (cfg->tune_cache) t.tune_cache = cfg->tune_cache;
     t.cfg.tune_cache = nullptr;
@@ -384,6 +385,15 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
                 if (it != pos.end() && it->second < f.ne) { f.pin_row = it->second; t.pin_front = id; }
             }
         }
+        for (const auto& lv : t.levels) {
+            long long rows = 0;
+            for (int id : lv) {
+                FrontInfo& f = t.fronts[id];
+                f.s_off = -1;
+                if (f.n >= kOzMinN) { f.s_off = (int)rows; rows += f.n; }
+            }
+            t.oz_rows = std::max(t.oz_rows, rows);
+        }
         t.total_front = foff;
         t.total_frhs = roff;
         if (t.root < 0 || t.fronts[t.root].nb != 0) { err = "internal: elimination tree root keeps boundary dofs"; return MRCM_ERR_INVALID_ARG; }
@@ -417,6 +427,8 @@ void compute_layout(const Tables& t, Layout& L) {
     L.fronts = take((size_t)t.total_front * sizeof(double));
     L.frhs = take((size_t)t.total_frhs * sizeof(double));
     L.panel = take((size_t)t.total_panels * 32 * 32 * sizeof(double));
+    L.oz = take((size_t)t.oz_rows * 1024);                 // 2 operands x 8 slices x 32 bf16 per row
+    L.oz_exp = take((size_t)t.oz_rows * 2 * sizeof(int));
     L.xres = take((size_t)2 * t.NV * sizeof(double));
     L.xtmp = take((size_t)2 * t.NV * sizeof(double));
     L.psum = take(((size_t)t.subs.size() + 64) * sizeof(double));

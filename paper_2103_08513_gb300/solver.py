@@ -33,7 +33,7 @@ class MRCM:
     def __init__(self, n, edges, patch=((0, 0),) * 3, h=(1.0, 1.0, 1.0), beta_mode=0, alpha=1.0,
                  beta_const=1.0, bc_type=((0, 0),) * 3, bc_value=((0.0, 0.0),) * 3,
                  precision="fp64", ir_max_sweeps=4, ir_tol=1e-14, device=None, allocate=True, tune_cache=None,
-                 wave_bytes=0):
+                 wave_bytes=0, interface_refine=0):
         self.lib = L.load()
         cfg = L.mrcm_config()
         cfg.nx, cfg.ny, cfg.nz = (int(v) for v in n)
@@ -54,6 +54,7 @@ class MRCM:
         cfg.ir_max_sweeps = int(ir_max_sweeps)
         cfg.ir_tol = float(ir_tol)
         cfg.wave_bytes = int(wave_bytes)
+        cfg.interface_refine = int(interface_refine)
         self._tune_cache = tune_cache.encode() if tune_cache else None
         cfg.tune_cache = self._tune_cache
         self.cfg = cfg

@@ -145,6 +145,10 @@ def test_setup_rejects_bad_configs(lib):
     cfg, keep = _cfg(w)
     cfg.precision = 3
     assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 8
+    cfg, keep = _cfg(w)
+    cfg.interface_refine = -2
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
+    assert b"interface_refine" in lib.mrcm_last_error(None)
 
 
 def test_device_calls_reject_bad_arguments_without_gpu(lib):

@@ -242,3 +242,18 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
         assert rel_l2(X.cpu().numpy(), r.X) < 1e-8, v
         assert rel_l2(p.cpu().numpy().ravel(), r.p) < 1e-8, v
         assert rel_l2(u.cpu().numpy().ravel(), r.u.ravel()) < 1e-8, v
+
+
+@pytest.mark.parametrize("name", ["C1", "many_tiles"])
+def test_interface_ldl_without_refinement(name):
+    """The interface LDL^T solve alone (no FP64 refinement step) reaches the
+    oracle's X at FP64 accuracy.  The C1 workload's larger fronts take the
+    tensor-core emulated trailing update, so this pins that update to FP64
+    accuracy (a refinement step would hide an inexact factor)."""
+    w = workload("c1") if name == "C1" else small(**CASES[name])
+    prob, r = _oracle(w)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp64", interface_refine=-1)
+    assert code == 0, st
+    assert st["interface_zero_pivots"] == 0
+    assert rel_l2(X, r.X) < 1e-11
+    assert rel_l2(p, r.p) < 1e-11
