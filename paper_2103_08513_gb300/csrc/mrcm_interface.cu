@@ -74,24 +74,52 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // entries at the same dofs -- J-signed, scaled subdomain blocks for leaves,
 // the lower triangle of the Schur complement otherwise.  64x64 tiles of the
 // lower triangle are spread over the grid; blockIdx.y selects the front.
+// 1 / d by Newton-Raphson iteration y <- y + y (1 - d y) from an FP32 seed
+// (FP32 reciprocal of d truncated to FP32, both conversions done with bit
+// operations): each step squares the relative error, so two steps take the
+// seed's ~2^-22 to the FP64 rounding level.  On this GPU an FP64 division is
+// a ~470-cycle dependent chain on the FP64 unit, this one four FMAs.  Values
+// whose reciprocal leaves the FP32 range fall back to the division.
+__device__ __forceinline__ double rcp64(double d) {
+    const unsigned long long bd = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((bd >> 52) & 0x7FF) - 1023;
+    if (e < -125 || e > 125) return 1.0 / d;
+    const float df = __uint_as_float((unsigned int)(bd >> 32) & 0x80000000u |
+                                     (unsigned int)(e + 127) << 23 | (unsigned int)((bd >> 29) & 0x7FFFFFu));
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(df));
+    const unsigned int fy = __float_as_uint(yf);
+    const int ey = (int)((fy >> 23) & 0xFF);
+    double y = __longlong_as_double((long long)((unsigned long long)(fy & 0x80000000u) << 32 |
+                                                (unsigned long long)(ey - 127 + 1023) << 52 |
+                                                (unsigned long long)(fy & 0x7FFFFFu) << 29));
+    double r = fma(-d, y, 1.0);
+    y = fma(y, r, y);
+    r = fma(-d, y, 1.0);
+    return fma(y, r, y);
+}
+
 // LDL^T of the nbk x nbk (nbk <= 32) diagonal block of a front, in place
 // (strict lower part becomes L11, the diagonal D), together with V = L11^{-1}.
 // Row i of the work array T holds [row i of the block | row i of V]; V starts
-// as I.  Step k, with l_i = T[i][k] / d_k for i > k, applies to every row
-// i > k the single update T[i][:] -= l_i u with
-//   u = [ T[j][k] for j > k, 0 for j <= k  |  V[k][:] ],
-// which is the rank-1 Schur update of the block and V <- (I - l e_k^T) V at
-// once (row k of V is final at step k).  One division per step, done by one
-// thread.  A zero or NaN pivot is replaced by 1 and counted.  Block-wide.
+// as I.  Step k, with l_i = T[i][k] / d_k for i > k, updates every row i > k
+// by T[i][c] -= l_i u_c with u_c = T[c][k] on the block part (k < c <= i) and
+// u_c = V[k][c] on the V part (c <= k): the rank-1 Schur update of the block
+// and V <- (I - l e_k^T) V at once (row k of V is final at step k).  One lane
+// per column, so a row costs one FP64 instruction per step.  The warp that
+// updates row k + 1 first computes 1 / d_{k+1} right away, overlapping the
+// other rows' updates.  A zero or NaN pivot is replaced by 1 and counted.
+// Block-wide.
 constexpr int kDiagW = 2 * kPanel + 1;
-constexpr int kDiagWork = kPanel * kDiagW + 3 * kPanel + 2;   // doubles of shared work space
+constexpr int kDiagWork = kPanel * kDiagW + 3 * kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
                                   int* status, double* work) {
     double (*T)[kDiagW] = reinterpret_cast<double (*)[kDiagW]>(work);
     double* u = work + kPanel * kDiagW;
     double* lcol = u + 2 * kPanel;
-    int& zero = *reinterpret_cast<int*>(lcol + kPanel);
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    double* sinv = lcol + kPanel;
+    int* zero = reinterpret_cast<int*>(sinv + 1);
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
     __syncthreads();                                          // the block's last writes are complete
     for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
         const int i = e >> 6, c = e & 63;
@@ -100,28 +128,42 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
         else v = (c - kPanel == i) ? 1.0 : 0.0;
         T[i][c] = v;
     }
-    if (tid == 0) zero = 0;
+    __syncthreads();
+    if (tid == 0) {
+        *zero = 0;
+        double d = T[0][0];
+        if (d == 0.0 || d != d) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
+        *sinv = rcp64(d);
+    }
     for (int k = 0; k < nbk; ++k) {
-        __syncthreads();
-        if (tid < 32) {                                       // pivot, l and u of this step (one warp)
-            double d = T[k][k];
-            if (d == 0.0 || d != d) { d = 1.0; if (tid == 0) { zero = 1; T[k][k] = 1.0; } }
-            double inv = 0.0;
-            if (tid == 0) inv = 1.0 / d;
-            inv = __shfl_sync(0xffffffffu, inv, 0);
+        __syncthreads();                                      // rows updated, 1 / d_k ready
+        if (tid < 32) {
             const int i = tid;
-            const double tik = T[i][k];                       // column k (lower part, i > k)
-            lcol[i] = i > k && i < nbk ? tik * inv : 0.0;
-            u[i] = i > k && i < nbk ? tik : 0.0;
+            const bool below = i > k && i < nbk;
+            const double tik = T[i][k];
+            const double l = below ? tik * *sinv : 0.0;
+            lcol[i] = l;
+            u[i] = below ? tik : 0.0;
             u[kPanel + i] = T[k][kPanel + i];
+            if (below) T[i][k] = l;                            // column k of L is final
         }
         __syncthreads();
-        for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
-            const int i = e >> 6, c = e & 63;
-            if (i > k && i < nbk && (c >= kPanel || c <= i)) T[i][c] = fma(-lcol[i], u[c], T[i][c]);
+        for (int i = k + 1 + w; i < nbk; i += nw) {
+            const int c = lane;
+            if (c <= i) {
+                double* dst = c <= k ? &T[i][kPanel + c] : &T[i][c];
+                const double uu = c <= k ? u[kPanel + c] : u[c];
+                *dst = fma(-lcol[i], uu, *dst);
+            }
+            if (i == k + 1) {
+                __syncwarp();
+                if (lane == 0) {
+                    double d = T[i][i];
+                    if (d == 0.0 || d != d) { d = 1.0; T[i][i] = 1.0; *zero = 1; }
+                    *sinv = rcp64(d);
+                }
+            }
         }
-        __syncthreads();
-        if (tid < 32 && tid > k && tid < nbk) T[tid][k] = lcol[tid];
     }
     __syncthreads();
     for (int e = tid; e < kPanel * kPanel; e += nthr) {
@@ -129,7 +171,7 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
         if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = T[i][c];
         Pinv[e] = T[i][kPanel + c];
     }
-    if (tid == 0 && zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
+    if (tid == 0 && *zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -277,7 +319,7 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
     if (threadIdx.x < kPanel) {
         const double d = threadIdx.x < nbk ? A[(long long)(k0 + threadIdx.x) * n + k0 + threadIdx.x] : 0.0;
         Dd[threadIdx.x] = d;
-        Dinv[threadIdx.x] = threadIdx.x < nbk ? 1.0 / d : 0.0;
+        Dinv[threadIdx.x] = threadIdx.x < nbk ? rcp64(d) : 0.0;
     }
     __syncthreads();
     for (int q = w; q < kPanelRows; q += 4) {

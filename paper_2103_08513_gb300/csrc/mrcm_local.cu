@@ -74,7 +74,8 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
                int4 bc_lo_hi /* x: mask of Dirichlet low walls, y: high walls */,
                double3 bc_lo, double3 bc_hi,
                double* __restrict__ coef, double* __restrict__ scale, double* __restrict__ rhs_dir,
-               double* __restrict__ face_tr, double* __restrict__ face_beta, long long ncell_total) {
+               double* __restrict__ face_tr, double* __restrict__ face_beta, double* __restrict__ face_u,
+               long long ncell_total) {
     const SubInfo s = subs[blockIdx.x];
     const long long ncells = (long long)geo.n[0] * geo.n[1] * geo.n[2];
     const double* Kc[3] = {K, K + ncells, K + 2 * ncells};
@@ -125,8 +126,10 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
         int a = fi.axis;
         double ka = Kc[a][g];
         double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-        face_tr[s.face_off + q] = geo.area[a] / (geo.h[a] / (2.0 * ka) + beta);
+        const double tr = geo.area[a] / (geo.h[a] / (2.0 * ka) + beta);
+        face_tr[s.face_off + q] = tr;
         face_beta[s.face_off + q] = beta;
+        face_u[s.face_off + q] = -beta * fi.s * tr;     // U-MBF right-hand side on this face
     }
 }
 
@@ -624,6 +627,7 @@ struct LocalArgs {
     const float* tsc;      // FP32 scaled slab coupling (mixed mode)
     const double* face_tr;
     const double* face_beta;
+    const double* face_u;
     const double* rhs_dir;
     const double* f;
     Geo geo;
@@ -641,14 +645,43 @@ struct LocalArgs {
     int count_unconverged;  // add this sweep's unconverged columns to the status word
 };
 
+// FP64 <-> FP32 conversions on the integer pipe.  On this GPU a conversion
+// instruction occupies the FP64 unit as long as an FMA does, and the local
+// solve is bound by that unit, so the refinement loop converts with bit
+// operations instead: FP64 -> FP32 truncates the significand (round toward
+// zero; the FP32 value only feeds the low-precision correction solve),
+// flushes magnitudes below the FP32 normal range to zero and saturates to
+// infinity above it; FP32 -> FP64 is exact for normal numbers (FP32
+// subnormals, which the correction never needs, become zero).
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    unsigned int f;
+    if (e <= 0) f = sign;
+    else if (e >= 255) f = sign | 0x7F800000u;
+    else f = sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned int f = __float_as_uint(x);
+    const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
+    const int e = (int)((f >> 23) & 0xFF);
+    unsigned long long b;
+    if (e == 0) b = sign;
+    else if (e == 255) b = sign | 0x7FF0000000000000ull | ((unsigned long long)(f & 0x7FFFFFu) << 29);
+    else b = sign | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(f & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 // Coupling between slab cells c and c+b in the solve's arithmetic: the FP32
 // scaled value t^ in mixed mode, the FP64 transmissibility otherwise.
 template <typename T, bool kScaled> struct Coupling;
 template <> struct Coupling<float, true> {
     const float* tsc; const float* scf;
     __device__ float t(int c) const { return tsc[c]; }
-    __device__ float in(double r, int c) const { return (float)r * scf[c]; }
-    __device__ double out(float x, int c) const { return (double)(x * scf[c]); }
+    __device__ float in(double r, int c) const { return f64_to_f32_rz(r) * scf[c]; }
+    __device__ double out(float x, int c) const { return f32_to_f64(x * scf[c]); }
 };
 template <> struct Coupling<double, false> {
     const double* cs;
@@ -728,27 +761,27 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                     local_coords(s, c, lc);
                     r = g.rhs_dir[s.cell_off + c] + g.f[global_cell(s, lc, g.geo.n)] * vol;
                 } else {
+                    // MBF column: the value on the one Robin face of this cell that carries
+                    // basis j, if any (faces of one cell belong to different bases); moves only
                     r = 0.0;
 #pragma unroll
                     for (int a = 0; a < 6; ++a) {
                         const int q = cf[6 * c + a];
                         if (q < 0) continue;
-                        const FaceInfo fi = g.faces[s.face_off + q];
-                        const double tr = g.face_tr[s.face_off + q];
-                        if (j == fi.col) r += tr;
-                        else if (j == nI + fi.col) r -= g.face_beta[s.face_off + q] * fi.s * tr;
+                        const int col = g.faces[s.face_off + q].col;
+                        if (j == col) r = g.face_tr[s.face_off + q];
+                        else if (j == nI + col) r = g.face_u[s.face_off + q];
                     }
                 }
-                if (kSweep) {
+                if (kSweep) {                     // r - A x as one FMA chain
                     const int u = i % su;
-                    double ax = cd[c] * x[c];
-                    if (u + 1 < su) ax = fma(-cu[c], x[c + 1], ax);
-                    if (u > 0) ax = fma(-cu[c - 1], x[c - 1], ax);
-                    if (i + su < b) ax = fma(-cv[c], x[c + su], ax);
-                    if (i >= su) ax = fma(-cv[c - su], x[c - su], ax);
-                    if (c + b < N) ax = fma(-cs[c], x[c + b], ax);
-                    if (c >= b) ax = fma(-cs[c - b], x[c - b], ax);
-                    r -= ax;
+                    r = fma(-cd[c], x[c], r);
+                    if (u + 1 < su) r = fma(cu[c], x[c + 1], r);
+                    if (u > 0) r = fma(cu[c - 1], x[c - 1], r);
+                    if (i + su < b) r = fma(cv[c], x[c + su], r);
+                    if (i >= su) r = fma(cv[c - su], x[c - su], r);
+                    if (c + b < N) r = fma(cs[c], x[c + b], r);
+                    if (c >= b) r = fma(cs[c - b], x[c - b], r);
                 }
                 rr = fma(r, r, rr);
                 T z = cp.in(r, c);
@@ -972,7 +1005,7 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
     MRCM_LAUNCH(P, "k_coefficients", st, k_coefficients<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, K, make_geo(c), c.beta_mode, c.alpha,
                                              c.beta_const, bcm, blo, bhi, coef, scale,
                                              (double*)(ws + L.rhs_part), (double*)(ws + L.face_tr),
-                                             (double*)(ws + L.face_beta), t.n_cells));
+                                             (double*)(ws + L.face_beta), (double*)(ws + L.face_u), t.n_cells));
     if (t.n_waves == 1) launch_factor_wave(t, d, L, ws, precision, 0, st, P);
     return (int)cudaGetLastError();
 }
@@ -1018,6 +1051,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.coef = (const double*)(ws + L.coef); g.scale = (const double*)(ws + L.scale);
     g.scf = (const float*)(ws + L.scf); g.tsc = (const float*)(ws + L.tsc);
     g.face_tr = (const double*)(ws + L.face_tr); g.face_beta = (const double*)(ws + L.face_beta);
+    g.face_u = (const double*)(ws + L.face_u);
     g.rhs_dir = (const double*)(ws + L.rhs_part); g.f = f; g.geo = make_geo(t.cfg); g.nct = t.n_cells;
     g.X = (double*)(ws + L.X); g.Ybuf = (void*)(ws + L.R);
     g.conv = (int*)(ws + L.conv); g.bnorm = (double*)(ws + L.colnorm);
