@@ -237,11 +237,7 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
     }
 }
 
-// Panel step of the blocked LDL^T: the rows below the (already factored)
-// diagonal block, l = a L11^{-T} D^{-1}, i.e. l_j = sum_{k <= j} a_k V[j][k] / d_j
-// with V = L11^{-1}.  One warp per row, lane j computes l_j; kPanelRows rows
-// per CTA so that even one large front spreads over the GPU.
-constexpr int kPanelRows = 8;
+constexpr int kPanelRows = 8;           // warp passes per panel-kernel CTA
 
 // Tensor-core emulation of the FP64 trailing update (Ozaki-type splitting
 // with exact integer arithmetic).  For each panel row x (of L21 D for the left
@@ -259,31 +255,30 @@ constexpr int kPanelRows = 8;
 // operations per entry instead of one FMA per panel column.
 constexpr int kOzS = 8;                     // slices per operand
 constexpr int kOzRowWords = 2 * kOzS * kPanel / 2;   // u32 words per slice row (2 operands x 8 slices x 32 bf16)
-constexpr int kOzMinM = 64;                 // emulate when the trailing block has >= kOzMinM rows
-constexpr int kOzMinK = 16;                 // and the panel >= kOzMinK columns
+constexpr int kOzMinM = 24;                 // emulate when the trailing block has >= kOzMinM rows
+constexpr int kOzMinK = 4;                  // and the panel >= kOzMinK columns
 
 __device__ __forceinline__ bool oz_step(const FrontInfo& fr, int m, int nbk) {
     return fr.s_off >= 0 && m >= kOzMinM && nbk >= kOzMinK;
 }
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+// Maximum over the aligned segment of W lanes (W a power of two) holding this lane.
+__device__ __forceinline__ unsigned long long seg_max_u64(unsigned long long v, int W) {
+    for (int o = W >> 1; o > 0; o >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
         v = w > v ? w : v;
     }
     return v;
 }
 
-// Slices of x (one lane per column) into row `dst` (kOzS x 32 bf16) and its
-// exponent E into *exp_out (lane 0).
-__device__ __forceinline__ void oz_slice_row(double x, __nv_bfloat16* dst, int* exp_out) {
-    const int lane = threadIdx.x & 31;
+// Slices of one panel row held by a segment of W lanes (lane j of the segment
+// holds column j; columns W .. 31 are zero) into `dst` (kOzS x 32 bf16) and
+// its exponent E into *exp_out.  Integer operations only.
+__device__ __forceinline__ void oz_slice_row(double x, int j, int W, bool store, __nv_bfloat16* dst, int* exp_out) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;          // orders like |x|
-    const unsigned long long mx = warp_max_u64(mag);
-    const int emax = (int)(mx >> 52);
-    const int E = mx == 0 ? 0 : emax - 1023 + 1;                           // max |x| < 2^E
+    const unsigned long long mx = seg_max_u64(mag, W);
+    const int E = mx == 0 ? 0 : (int)(mx >> 52) - 1023 + 1;                // max |x| < 2^E
     const int ex = (int)(mag >> 52);
     unsigned long long Fx = 0;                                             // floor(|x| 2^{56-E})
     if (ex != 0) {
@@ -292,14 +287,22 @@ __device__ __forceinline__ void oz_slice_row(double x, __nv_bfloat16* dst, int* 
         Fx = sh >= 0 ? (mant << sh) : (-sh < 64 ? (mant >> -sh) : 0ull);
     }
     const bool neg = (bits >> 63) != 0;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    if (!store) return;                                                    // after the segment reduction
 #pragma unroll
     for (int t = 0; t < kOzS; ++t) {
-        int v = (int)((Fx >> (49 - 7 * t)) & 127ull);
-        dst[t * kPanel + lane] = __float2bfloat16_rn((float)(neg ? -v : v));
+        const int v = (int)((Fx >> (49 - 7 * t)) & 127ull);
+        dst[t * kPanel + j] = __float2bfloat16_rn((float)(neg ? -v : v));
+        for (int c = j + W; c < kPanel; c += W) dst[t * kPanel + c] = zero;
     }
-    if (lane == 0) *exp_out = E;
+    if (j == 0) *exp_out = E;
 }
 
+// Panel step of the blocked LDL^T: the rows below the (already factored)
+// diagonal block, l = a L11^{-T} D^{-1}, i.e. l_j = sum_{k <= j} a_k V[j][k] / d_j
+// with V = L11^{-1}.  A warp holds 32 / W rows at once, W = the panel width
+// rounded up to a power of two (one lane per column), so narrow panels do
+// not waste FP64 issue slots; kPanelRows x 32 / W rows per CTA.
 __global__ void __launch_bounds__(128)
 k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
             const double* __restrict__ P, __nv_bfloat16* __restrict__ oz, int* __restrict__ oz_exp) {
@@ -308,8 +311,12 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
     const int n = fr.n;
     const int nbk = min(kPanel, fr.ne - k0);
     const int k1 = k0 + nbk;
-    const int r0 = k1 + blockIdx.x * kPanelRows;
+    const int W = nbk <= 1 ? 1 : 1 << (32 - __clz(nbk - 1));
+    const int R = kPanel / W;                                   // rows per warp pass
+    const int rows = kPanelRows * R;                            // rows of this CTA
+    const int r0 = k1 + blockIdx.x * rows;
     if (r0 >= n) return;
+    const int r_end = min(n, r0 + rows);
     double* A = F + fr.f_off;
     __shared__ double Vs[kPanel][kPanel + 1];
     __shared__ double Dinv[kPanel], Dd[kPanel];
@@ -322,23 +329,24 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
         Dinv[threadIdx.x] = threadIdx.x < nbk ? rcp64(d) : 0.0;
     }
     __syncthreads();
-    for (int q = w; q < kPanelRows; q += 4) {
-        const int r = r0 + q;
-        if (r >= n) break;
+    const int rs = lane / W, j = lane % W;
+    const bool oz_on = oz_step(fr, n - k1, nbk);
+    for (int base = r0 + w * R; base < r_end; base += 4 * R) {
+        const int r = base + rs;
+        const bool live = r < r_end && j < nbk;
         double* row = A + (long long)r * n + k0;
-        const double a = lane < nbk ? row[lane] : 0.0;
+        const double a = live ? row[j] : 0.0;
         double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < kPanel; ++k) {
-            const double ak = __shfl_sync(0xffffffffu, a, k);
-            acc = fma(ak, Vs[lane][k], acc);                 // V[j][k] = 0 for k > j
+        for (int k = 0; k < nbk; ++k) {
+            const double ak = __shfl_sync(0xffffffffu, a, rs * W + k);
+            acc = fma(ak, Vs[j][k], acc);                        // V[j][k] = 0 for k > j
         }
-        const double l = lane < nbk ? acc * Dinv[lane] : 0.0;
-        if (lane < nbk) row[lane] = l;
-        if (oz_step(fr, n - k1, nbk)) {
-            const long long sr = (long long)fr.s_off + r;
-            oz_slice_row(l * Dd[lane], oz + sr * (2 * kOzS * kPanel), oz_exp + 2 * sr);
-            oz_slice_row(l, oz + sr * (2 * kOzS * kPanel) + kOzS * kPanel, oz_exp + 2 * sr + 1);
+        const double l = live ? acc * Dinv[j] : 0.0;
+        if (live) row[j] = l;
+        if (oz_on) {                                              // all lanes: segment reductions inside
+            const long long sr = (long long)fr.s_off + min(r, r_end - 1);
+            oz_slice_row(l * Dd[j], j, W, r < r_end, oz + sr * (2 * kOzS * kPanel), oz_exp + 2 * sr);
+            oz_slice_row(l, j, W, r < r_end, oz + sr * (2 * kOzS * kPanel) + kOzS * kPanel, oz_exp + 2 * sr + 1);
         }
     }
 }
@@ -346,13 +354,28 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
 // BF16 m16n8k16 tensor-core MMA with FP32 accumulation (the emulated update
 // feeds it small integers, for which it is exact).
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
                  "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
                  : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// v 2^e as an FP64 value built with integer operations (exact for |v| < 2^53;
+// results below the normal range become 0).
+__device__ __forceinline__ double i64_scaled(long long v, int e) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long m = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int top = 63 - __clzll((long long)m);                         // m in [2^top, 2^(top+1)), top <= 52
+    const int ex = top + e + 1023;
+    if (ex <= 0) return 0.0;
+    const unsigned long long frac = (m << (52 - top)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | frac));
+}
+
+// Exact integer value (|v| < 2^22) of an FP32 holding one: add 1.5 2^23 and
+// read the significand (FP32 add and integer subtract, no conversion).
+__device__ __forceinline__ int f32_int(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
 
 // Trailing update of the blocked LDL^T: F22 -= L21 D L21^T on 32 x 32 tiles
 // of the lower triangle (small tiles spread one front's update over many
@@ -400,42 +423,49 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
         __syncthreads();
         const int g = lane >> 2, tg = lane & 3;
         const int mr = (w >> 2) * 16, nc = (w & 3) * 8;                   // this warp's 16 x 8 output block
-        long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+        float acc[kOzS][4];
 #pragma unroll
-        for (int d = 0; d < kOzS; ++d) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int d = 0; d < kOzS; ++d)
 #pragma unroll
-            for (int ts = 0; ts <= d; ++ts) {
-                const int us = d - ts;
+            for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
+        // P_d accumulates every slice pair (ts, us) with ts + us = d; consecutive
+        // MMAs go to different accumulators
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    const int wa = ts * (kPanel / 2) + kc * 8 + tg;
-                    const int wb = us * (kPanel / 2) + kc * 8 + tg;
-                    uint32_t af[4], bf[2];
-                    af[0] = Sa[(mr + g) * kOzLd + wa];
-                    af[1] = Sa[(mr + g + 8) * kOzLd + wa];
-                    af[2] = Sa[(mr + g) * kOzLd + wa + 4];
-                    af[3] = Sa[(mr + g + 8) * kOzLd + wa + 4];
-                    bf[0] = Sb[(nc + g) * kOzLd + wb];
-                    bf[1] = Sb[(nc + g) * kOzLd + wb + 4];
-                    mma_bf16(acc, af, bf);
-                }
+        for (int ts = 0; ts < kOzS; ++ts) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc) {
+                const int wa = ts * (kPanel / 2) + kc * 8 + tg;
+                af[kc][0] = Sa[(mr + g) * kOzLd + wa];
+                af[kc][1] = Sa[(mr + g + 8) * kOzLd + wa];
+                af[kc][2] = Sa[(mr + g) * kOzLd + wa + 4];
+                af[kc][3] = Sa[(mr + g + 8) * kOzLd + wa + 4];
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const long long pv = (long long)__float2ll_rn(acc[q]);
-                if (d < 4) hi[q] += pv << (7 * (3 - d));
-                else lo[q] += pv << (7 * (7 - d));
+            for (int us = 0; us < kOzS - ts; ++us) {
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    const int wb = us * (kPanel / 2) + kc * 8 + tg;
+                    const uint32_t bf[2] = {Sb[(nc + g) * kOzLd + wb], Sb[(nc + g) * kOzLd + wb + 4]};
+                    mma_bf16(acc[ts + us], af[kc], bf);
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            long long hi = 0, lo = 0;
+#pragma unroll
+            for (int d = 0; d < kOzS; ++d) {
+                const long long pv = f32_int(acc[d][q]);
+                if (d < 4) hi += pv << (7 * (3 - d));
+                else lo += pv << (7 * (7 - d));
+            }
             const int gi = i0 + mr + g + (q >> 1) * 8;
             const int gj = j0 + nc + 2 * tg + (q & 1);
             if (gi < n && gj <= gi) {
                 const int e = oz_exp[2 * ((long long)fr.s_off + gi)] + oz_exp[2 * ((long long)fr.s_off + gj) + 1];
-                const double v = fma((double)lo[q], pow2(e - 63), (double)hi[q] * pow2(e - 35));
-                A[(long long)gi * n + gj] -= v;
+                double* c = A + (long long)gi * n + gj;
+                *c = (*c - i64_scaled(hi, e - 35)) - i64_scaled(lo, e - 63);
             }
         }
     } else {

@@ -12,7 +12,7 @@ namespace mrcm {
 constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
 constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
-constexpr int kOzMinN = 64;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
+constexpr int kOzMinN = 32;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
 constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
 
