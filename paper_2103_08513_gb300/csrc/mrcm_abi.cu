@@ -175,7 +175,7 @@ mrcm_status mrcm_setup(const mrcm_config* cfg, mrcm_handle** out) {
     for (const auto& sb : t.subs)
         solve_smem = std::max(solve_smem, t.cfg.precision == MRCM_FP64 ? mrcm::solve_smem_layout<double>(sb.b, mpad, sb.N).total
                                                                           : mrcm::solve_smem_layout<float>(sb.b, mpad, sb.N).total);
-    if (st == MRCM_OK && solve_smem > 227 * 1024) {
+    if (st == MRCM_OK && solve_smem + 16 > 227 * 1024) {
         st = MRCM_ERR_NOT_IMPLEMENTED;
         h->err = "slab block and right-hand-side count exceed shared memory";
     }

@@ -160,10 +160,27 @@ struct DeviceTables {
 // active columns, the per-cell Robin-face map (six sides per cell) and, for
 // blocks with b <= kSmemW, the staged block W_s (larger blocks are read from
 // global memory, where they stay L2-resident for the slab).
-constexpr int kSmemW = 128;
+// Slab block W_s storage: b x b entries padded to a multiple of 16 bytes, so
+// that every block starts 16-byte aligned (bulk-copy rule).
+template <typename T>
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline long long wstride(int b) {
+    const long long q = 16 / (long long)sizeof(T);
+    return ((long long)b * b + q - 1) / q * q;
+}
+
+// Shared memory of the local solve for one subdomain.  W blocks are staged by
+// bulk copies into nbuf buffers (2: the next block streams in while the
+// current one is used; 1 when two would not leave room for two CTAs per SM;
+// 0: too large to stage, read from global memory).
+constexpr size_t kSolveSmemBudget = 220 * 1024;   // dynamic shared memory per CTA
+constexpr size_t kSolveTwoCta = 113 * 1024;       // two CTAs per SM fit below this
 
 struct SolveSmem {
-    size_t yp, nrm, cols, cf, w, total;
+    size_t w, z, yp, nrm, cols, cf, total;
+    int nbuf;
 };
 
 template <typename T>
@@ -172,7 +189,20 @@ __host__ __device__
 #endif
 inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     SolveSmem L;
-    size_t x = sizeof(T) * (size_t)b * mpad;
+    const size_t wb = sizeof(T) * (size_t)wstride<T>(b);
+    size_t rest = 0;
+    rest += 2 * sizeof(T) * (size_t)b * mpad;              // Z, Yp
+    rest = (rest + 15) & ~size_t(15);
+    rest += sizeof(double) * mpad + sizeof(int) * mpad;    // nrm, cols
+    rest += sizeof(short) * 6 * (size_t)N;                 // cf
+    rest = (rest + 15) & ~size_t(15);
+    rest += 16;                                            // mbarriers (after the largest layout)
+    L.nbuf = (2 * wb + rest + 128 <= kSolveTwoCta) ? 2 : (wb + rest + 128 <= kSolveSmemBudget ? 1 : 0);
+    size_t x = 0;
+    L.w = 0;
+    x += L.nbuf * ((wb + 127) & ~size_t(127));
+    L.z = x;
+    x += sizeof(T) * (size_t)b * mpad;
     L.yp = x;
     x += sizeof(T) * (size_t)b * mpad;
     x = (x + 15) & ~size_t(15);
@@ -182,10 +212,7 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     x += sizeof(int) * mpad;
     L.cf = x;
     x += sizeof(short) * 6 * (size_t)N;
-    x = (x + 15) & ~size_t(15);
-    L.w = x;
-    if (b <= kSmemW) x += sizeof(T) * (size_t)b * b;
-    L.total = (x + 15) & ~size_t(15);
+    L.total = (x + 127) & ~size_t(127);
     return L;
 }
 

@@ -220,7 +220,7 @@ k_block_factor(const SubInfo* __restrict__ subs, const int* __restrict__ list, c
             __syncthreads();
         }
         // W_s as a full matrix (both triangles)
-        T* Ws = W + (long long)sl * b * b;
+        T* Ws = W + (long long)sl * wstride<T>(b);
         for (int i = ty; i < b; i += 8) {
             const T* row = Lp + packed_len(i);
             for (int j = tx; j <= i; j += 32) {
@@ -334,7 +334,7 @@ k_block_factor_reg(const SubInfo* __restrict__ subs, const int* __restrict__ lis
             }
         }
         // store W_s (symmetric: thread i writes column i = row i), coalesced over threads
-        float* Ws = W + (long long)sl * b * b;
+        float* Ws = W + (long long)sl * wstride<float>(b);
         if (live) {
 #pragma unroll
             for (int j = 0; j < kRegMaxB; ++j)
@@ -462,7 +462,7 @@ k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ li
             }
         }
         // store W_s (full symmetric matrix, row major)
-        float* Ws = W + (long long)sl * b * b;
+        float* Ws = W + (long long)sl * wstride<float>(b);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int i = i0 + r;
@@ -643,6 +643,7 @@ struct LocalArgs {
     int nlist;
     int* queue;           // work-queue counter (reset to 0 before each launch)
     int count_unconverged;  // add this sweep's unconverged columns to the status word
+    int bar_off;          // shared-memory offset of the two mbarriers (after the largest layout)
 };
 
 // FP64 <-> FP32 conversions on the integer pipe.  On this GPU a conversion
@@ -690,22 +691,67 @@ template <> struct Coupling<double, false> {
     __device__ double out(double x, int) const { return x; }
 };
 
+// ---- bulk-copy staging of the W blocks (TMA unit, completion on an mbarrier)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One thread: expect `bytes` on the barrier and start the copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // earlier generic reads of dst done
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after about two seconds
+// (then the status word records a timeout and the caller stops using the buffer).
+constexpr long long kWaitCycles = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+// Per-CTA state of the W staging pipeline, kept across subdomains (the same
+// in every thread).
+struct WPipe {
+    uint32_t phase[2];     // parity of the next completion of each buffer
+    int pending[2];        // a copy into the buffer has been issued and not waited for
+    int abort;             // a wait timed out: stop staging
+};
+
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
 __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restrict__ Wall, int l,
-                                          unsigned char* smem_raw) {
+                                          unsigned char* smem_raw, WPipe& pipe) {
     constexpr int NY = NT / 32;
     const SubInfo s = g.subs[l];
     const int b = s.b, m = s.m, N = s.N, su = s.su, nI = s.nI, mpad = g.mpad;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x NY threads
     const SolveSmem lay = solve_smem_layout<T>(b, mpad, N);
-    const bool wsm = b <= kSmemW;                              // stage W_s in shared memory
-    T* Z = reinterpret_cast<T*>(smem_raw);                     // b x mpad, cell-major
+    const int nbuf = lay.nbuf;                                 // W buffers (0: read W from global memory)
+    const long long wsd = wstride<T>(b);
+    const size_t wbytes = sizeof(T) * (size_t)wsd;
+    T* Wb[2] = {reinterpret_cast<T*>(smem_raw + lay.w), reinterpret_cast<T*>(smem_raw + lay.w + ((wbytes + 127) & ~size_t(127)))};
+    T* Z = reinterpret_cast<T*>(smem_raw + lay.z);             // b x mpad, cell-major
     T* Yp = reinterpret_cast<T*>(smem_raw + lay.yp);           // b x mpad: Y_{s-1} / x_{s+1}
     double* nrm = reinterpret_cast<double*>(smem_raw + lay.nrm);
     int* cols = reinterpret_cast<int*>(smem_raw + lay.cols);   // active columns
     short* cf = reinterpret_cast<short*>(smem_raw + lay.cf);   // Robin face per (cell, axis, side), -1 = none
-    T* Wst = reinterpret_cast<T*>(smem_raw + lay.w);           // staged b x b block (b <= kSmemW)
-    __shared__ int na_s;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + g.bar_off);
+    __shared__ int na_s, abort_s;
 
     const double* cd = g.coef + s.cell_off;
     const double* cu = g.coef + g.nct + s.cell_off;
@@ -741,13 +787,44 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         const FaceInfo fi = g.faces[s.face_off + q];
         cf[6 * fi.cell + 2 * fi.axis + (fi.s > 0 ? 1 : 0)] = (short)q;   // one face per cell side
     }
+    // W block sequence: forward W_0 .. W_{ns-1}, backward W_{ns-2} .. W_0
+    const int nq = 2 * s.ns - 1;
+    auto blk = [&](int q) { return q < s.ns ? q : 2 * s.ns - 2 - q; };
+    const bool staged = nbuf > 0 && !pipe.abort;
+    if (threadIdx.x == 0) abort_s = 0;
+    if (staged) {
+        for (int q = 0; q < nbuf && q < nq; ++q) {
+            if (threadIdx.x == 0) bulk_load(Wb[q], W + blk(q) * wsd, (uint32_t)wbytes, &bar[q]);
+            pipe.pending[q] = 1;
+        }
+    }
     __syncthreads();
+    // The block of step q (staged: wait for its copy), and the refill after use.
+    auto wblock = [&](int q) -> const T* {
+        if (!staged) return W + blk(q) * wsd;
+        const int bi = q % nbuf;
+        if (pipe.pending[bi]) {
+            if (mbar_wait(&bar[bi], pipe.phase[bi])) {
+                pipe.phase[bi] ^= 1u;
+                pipe.pending[bi] = 0;
+            } else {
+                if (threadIdx.x == 0) atomicAdd(&g.status[ST_TIMEOUT], 1);
+                abort_s = 1;
+            }
+        }
+        return Wb[bi];
+    };
+    auto refill = [&](int q) {                     // after the block of step q has been used (post-barrier)
+        const int bi = q % nbuf;
+        if (staged && q + nbuf < nq && !abort_s && !pipe.pending[bi]) {
+            if (threadIdx.x == 0) bulk_load(Wb[bi], W + blk(q + nbuf) * wsd, (uint32_t)wbytes, &bar[bi]);
+            pipe.pending[bi] = 1;
+        }
+    };
 
     // ---- forward sweep
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
-        const T* Wsm = wsm ? Wst : W + (long long)sl * b * b;
-        if (wsm) for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wst[e] = W[(long long)sl * b * b + e];
         // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
         for (int jj = ty; jj < na; jj += NY) {
             const int j = cols[jj];
@@ -791,12 +868,14 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
             if (tx == 0) nrm[jj] += rr;          // column jj belongs to warp ty only: fixed order
         }
+        const T* Wsm = wblock(sl);
         __syncthreads();
         block_product<T, RT>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
             Yp[i * mpad + jj] = v;
             Ys[(long long)cols[jj] * N + base + i] = v;
         });
         __syncthreads();
+        refill(sl);
     }
     // ---- backward sweep (Yp holds x_{s+1})
     for (int sl = s.ns - 1; sl >= 0; --sl) {
@@ -811,17 +890,19 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             if (kSweep) Xs[gi] += xo; else Xs[gi] = xo;
         };
         if (!last) {
-            const T* Wsm = wsm ? Wst : W + (long long)sl * b * b;
-            if (wsm) for (int e = threadIdx.x; e < b * b; e += blockDim.x) Wst[e] = W[(long long)sl * b * b + e];
+            const int q = 2 * s.ns - 2 - sl;
             for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = cp.t(base + i) * Yp[i * mpad + jj];
+            const T* Wsm = wblock(q);
             __syncthreads();
             block_product<T, RT>(Wsm, Z, b, na, mpad, finish);
+            __syncthreads();
+            refill(q);
         } else {
             for (int jj = ty; jj < na; jj += NY)
                 for (int i = tx; i < b; i += 32) finish(i, jj, (T)0);
+            __syncthreads();
         }
-        __syncthreads();
     }
     // convergence bookkeeping
     if (kSweep) {
@@ -846,6 +927,14 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         }
     }
     __syncthreads();                              // shared memory is reused by the next subdomain
+    pipe.abort = abort_s;
+}
+
+// Before a CTA leaves: wait (bounded) for copies still in flight into its
+// buffers, which only a timed-out wait can leave behind.
+__device__ __forceinline__ void drain_pipe(WPipe& pipe, unsigned long long* bar) {
+    for (int bi = 0; bi < 2; ++bi)
+        if (pipe.pending[bi]) mbar_wait(&bar[bi], pipe.phase[bi]);
 }
 
 // Persistent local solve: CTAs pull subdomains from a device work queue over
@@ -853,16 +942,26 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
 __global__ void __launch_bounds__(NT)
 k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int item;
+    // mbarriers at the end of the largest layout (every subdomain's layout places them below)
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + g.bar_off);
+    if (threadIdx.x == 0) { mbar_init(&bar[0]); mbar_init(&bar[1]); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    WPipe pipe;
+    pipe.phase[0] = pipe.phase[1] = 0u;
+    pipe.pending[0] = pipe.pending[1] = 0;
+    pipe.abort = 0;
     for (;;) {
         if (threadIdx.x == 0) item = atomicAdd(g.queue, 1);
         __syncthreads();
         const int it = item;
         __syncthreads();
-        if (it >= g.nlist) break;
-        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it], smem_raw);
+        if (it >= g.nlist || pipe.abort) break;
+        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it], smem_raw, pipe);
     }
+    drain_pipe(pipe, bar);
 }
 
 // Tunable variants of the local solve: threads per CTA x block-product path
@@ -1016,7 +1115,7 @@ static size_t solve_smem_bytes(const Tables& t, int precision) {
     for (const SubInfo& sb : t.subs)
         sm = std::max(sm, precision == MRCM_FP64 ? solve_smem_layout<double>(sb.b, mpad, sb.N).total
                                                  : solve_smem_layout<float>(sb.b, mpad, sb.N).total);
-    return sm;
+    return sm + 16;                                // + the two mbarriers, after the largest layout
 }
 
 // One-time kernel configuration (dynamic shared memory limits, persistent
@@ -1060,6 +1159,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.list = d.solve_list; g.nlist = (int)t.subs.size();
     g.queue = (int*)(ws + L.status) + ST_QUEUE;
     g.count_unconverged = 0;
+    g.bar_off = (int)d.solve_smem - 16;
     return g;
 }
 

@@ -257,7 +257,7 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         long long wcur = 0, wmax = 0;
         for (int q = 0; q < nsub; ++q) {
             SubInfo& s = t.subs[t.solve_list[q]];
-            const long long need = (long long)s.ns * s.b * s.b;
+            const long long need = (long long)s.ns * (t.cfg.precision == MRCM_FP64 ? wstride<double>(s.b) : wstride<float>(s.b));
             if (cfg->wave_bytes > 0 && q > t.wave_off.back() && (size_t)(wcur + need) * welem > cfg->wave_bytes) {
                 t.wave_off.push_back(q);
                 wcur = 0;
