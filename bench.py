@@ -193,7 +193,7 @@ def parse():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir"])
     ap.add_argument("--ir-sweeps", type=int, default=None,
-                    help="FP64 refinement sweeps of the mixed local solve (default 6 for c5, else 4)")
+                    help="FP64 refinement sweeps of the mixed local solve (default 6 for the C5 layouts, else 4)")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -262,7 +262,7 @@ def main():
     props = torch.cuda.get_device_properties(local)
 
     if args.ir_sweeps is None:
-        args.ir_sweeps = 6 if args.workload == "c5" else 4
+        args.ir_sweeps = 6 if args.workload in ("c5", "c5_slab") else 4
     wave_gb = args.wave_gb if args.wave_gb is not None else (16.0 if args.workload == "c5" else 0.0)
     wave_bytes = int(wave_gb * (1 << 30))
 

@@ -214,7 +214,8 @@ mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double*
                        double* mass_residual_max, void* ws, size_t ws_bytes, void* stream, int flags);
 
 /* Autotuner (run after mrcm_factor_local): times every variant of the local
- * solve kernels (threads per CTA x rows per thread of the block products) on
+ * solve kernels (128, 256 or 512 threads per CTA x SIMT block products with
+ * 1, 2 or 4 rows per thread or 3xTF32 tensor-core block products) on
  * this problem, keeps the fastest first-solve and refinement-sweep variants
  * for the handle, and appends them to cfg.tune_cache when one was given (a
  * later mrcm_setup with the same cache and problem shape reuses them without

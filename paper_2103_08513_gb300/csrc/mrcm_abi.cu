@@ -109,7 +109,7 @@ void load_tune_cache(mrcm_handle* h) {
     int v0, v1;
     const std::string want = tune_key(h);
     while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3) {
-        if (want == key && v0 >= 0 && v0 < 8 && v1 >= 0 && v1 < 8) {
+        if (want == key && v0 >= 0 && v0 < 10 && v1 >= 0 && v1 < 10) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
         }
@@ -379,7 +379,7 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
     if (st != MRCM_OK) return st;
     if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
     int v0 = 0, v1 = 0;
-    float ms[16];
+    float ms[2 * mrcm::kMaxSolveVariants];
     int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, ms);
     if ((st = after_launch(h, rc, "mrcm_autotune")) != MRCM_OK) return st;
     h->d.solve_variant = v0;

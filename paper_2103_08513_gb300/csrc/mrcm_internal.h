@@ -12,6 +12,7 @@ namespace mrcm {
 constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
 constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
+constexpr int kMaxSolveVariants = 16;  // capacity of the per-variant tables
 constexpr int kOzMinN = 32;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
 constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
@@ -135,8 +136,8 @@ struct DeviceTables {
     int* solve_list = nullptr;                 // all subdomains, costliest solve first (wave by wave)
     int sms = 0;
     size_t solve_smem = 0;
-    int solve_occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-    int sweep_occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int solve_occ[kMaxSolveVariants] = {};
+    int sweep_occ[kMaxSolveVariants] = {};
     int solve_variant = 0, sweep_variant = 0;  // chosen by the autotuner (or the tune cache)
     size_t front_smem = 0;
     int* rowptr = nullptr;

@@ -682,12 +682,14 @@ template <> struct Coupling<float, true> {
     const float* tsc; const float* scf;
     __device__ float t(int c) const { return tsc[c]; }
     __device__ float in(double r, int c) const { return f64_to_f32_rz(r) * scf[c]; }
+    __device__ float in(double, float rf, int c) const { return rf * scf[c]; }
     __device__ double out(float x, int c) const { return f32_to_f64(x * scf[c]); }
 };
 template <> struct Coupling<double, false> {
     const double* cs;
     __device__ double t(int c) const { return cs[c]; }
     __device__ double in(double r, int) const { return r; }
+    __device__ double in(double r, float, int) const { return r; }
     __device__ double out(double x, int) const { return x; }
 };
 
@@ -747,7 +749,9 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     T* Wb[2] = {reinterpret_cast<T*>(smem_raw + lay.w), reinterpret_cast<T*>(smem_raw + lay.w + ((wbytes + 127) & ~size_t(127)))};
     T* Z = reinterpret_cast<T*>(smem_raw + lay.z);             // b x mpad, cell-major
     T* Yp = reinterpret_cast<T*>(smem_raw + lay.yp);           // b x mpad: Y_{s-1} / x_{s+1}
-    double* nrm = reinterpret_cast<double*>(smem_raw + lay.nrm);
+    // per active column: squared norm (FP32) of b (first solve) or of r / ||b|| (sweep), and 1 / ||b||
+    float* nrm = reinterpret_cast<float*>(smem_raw + lay.nrm);
+    float* rsb = nrm + mpad;
     int* cols = reinterpret_cast<int*>(smem_raw + lay.cols);   // active columns
     short* cf = reinterpret_cast<short*>(smem_raw + lay.cf);   // Robin face per (cell, axis, side), -1 = none
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + g.bar_off);
@@ -779,9 +783,17 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         if (threadIdx.x == 0) na_s = base;
     }
     for (int e = threadIdx.x; e < 6 * N; e += blockDim.x) cf[e] = -1;
-    for (int e = threadIdx.x; e < mpad; e += blockDim.x) nrm[e] = 0.0;
     __syncthreads();
     const int na = na_s;
+    for (int e = threadIdx.x; e < mpad; e += blockDim.x) {
+        nrm[e] = 0.0f;
+        float sc = 1.0f;
+        if (kSweep && e < na) {
+            const float bn = (float)g.bnorm[s.rhs_off + cols[e]];
+            if (bn > 0.0f) sc = rsqrtf(bn);
+        }
+        rsb[e] = sc;
+    }
     if (na == 0) { __syncthreads(); return; }
     for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
         const FaceInfo fi = g.faces[s.face_off + q];
@@ -829,7 +841,8 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         for (int jj = ty; jj < na; jj += NY) {
             const int j = cols[jj];
             const double* x = Xs + (long long)j * N;
-            double rr = 0.0;
+            const float rscale = rsb[jj];
+            float rr = 0.0f;
             for (int i = tx; i < b; i += 32) {
                 const int c = base + i;
                 double r;
@@ -860,8 +873,10 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                     if (c + b < N) r = fma(cs[c], x[c + b], r);
                     if (c >= b) r = fma(cs[c - b], x[c - b], r);
                 }
-                rr = fma(r, r, rr);
-                T z = cp.in(r, c);
+                const float rf = f64_to_f32_rz(r);
+                const float rn = rf * rscale;
+                rr = fmaf(rn, rn, rr);
+                T z = cp.in(r, rf, c);
                 if (sl > 0) z += cp.t(c - b) * Yp[i * mpad + jj];
                 Z[i * mpad + jj] = z;
             }
@@ -914,7 +929,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         __syncthreads();
         for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
             const int j = cols[jj];
-            if (nrm[jj] <= g.tol2 * g.bnorm[s.rhs_off + j]) conv[j] = 1;
+            if (nrm[jj] <= (float)g.tol2) conv[j] = 1;          // ||r||^2 / ||b||^2 <= tol^2
             else atomicAdd(&nbad, 1);
         }
         __syncthreads();
@@ -922,7 +937,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     } else {
         for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
             const int j = cols[jj];
-            g.bnorm[s.rhs_off + j] = nrm[jj];
+            g.bnorm[s.rhs_off + j] = (double)nrm[jj];
             conv[j] = 0;
         }
     }
@@ -940,7 +955,7 @@ __device__ __forceinline__ void drain_pipe(WPipe& pipe, unsigned long long* bar)
 // Persistent local solve: CTAs pull subdomains from a device work queue over
 // the cost-ordered list until it is exhausted (no waits: a plain atomic counter).
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 1280 / NT)       // <= 51 (64 at 512 threads) registers per thread
 k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int item;
@@ -966,8 +981,11 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
 
 // Tunable variants of the local solve: threads per CTA x block-product path
 // (SIMT with 2, 1 or 4 rows per thread, or 3xTF32 tensor cores for FP32).
-constexpr int kNumSolveVariants = 8;
-__host__ __device__ inline int variant_threads(int v) { return v == 6 ? 256 : v == 7 ? 128 : v < 3 ? 256 : 128; }
+constexpr int kNumSolveVariants = 10;
+static_assert(kNumSolveVariants <= kMaxSolveVariants, "per-variant tables are too small");
+__host__ __device__ inline int variant_threads(int v) {
+    return v >= 8 ? 512 : v == 6 ? 256 : v == 7 ? 128 : v < 3 ? 256 : 128;
+}
 
 template <typename T, bool kScaled, bool kSweep>
 const void* solve_kernel(int v) {
@@ -981,9 +999,11 @@ const void* solve_kernel(int v) {
         case 6:
             if constexpr (std::is_same<T, float>::value) return (const void*)k_local_solve<T, kScaled, kSweep, 256, 0>;
             else return (const void*)k_local_solve<T, kScaled, kSweep, 256, 2>;
-        default:
+        case 7:
             if constexpr (std::is_same<T, float>::value) return (const void*)k_local_solve<T, kScaled, kSweep, 128, 0>;
             else return (const void*)k_local_solve<T, kScaled, kSweep, 128, 2>;
+        case 8: return (const void*)k_local_solve<T, kScaled, kSweep, 512, 2>;
+        default: return (const void*)k_local_solve<T, kScaled, kSweep, 512, 1>;
     }
 }
 
@@ -1206,13 +1226,16 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     return (int)cudaGetLastError();
 }
 
-// Autotuner: time every local-solve variant on this problem (first solve and
-// one refinement sweep, median of `reps` runs) and return the fastest pair.
+// Autotuner: (1) time every variant's first solve (median of `reps`) and keep
+// the fastest; (2) for every variant, after an untimed first solve, time the
+// whole refinement sequence as the solve runs it (ir_max_sweeps sweeps with
+// the configured tolerance, so retired columns shrink the later sweeps) and
+// keep the fastest.  Tuned on the first wave.
 int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
                    void* stream, int reps, int* best_solve, int* best_sweep, float* ms_out) {
     cudaStream_t st = (cudaStream_t)stream;
     LocalArgs g = local_args(t, d, L, ws, f);
-    g.tol2 = 0.0;        // nothing retires: every sweep does the full work
+    g.tol2 = t.cfg.ir_tol * t.cfg.ir_tol;
     const void* W = (const void*)(ws + L.W);
     Prof dummy;
     g.list = d.solve_list;                      // tune on the first wave
@@ -1222,11 +1245,12 @@ int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    auto median = [](std::vector<float>& v) { std::sort(v.begin(), v.end()); return v[v.size() / 2]; };
     float best0 = 1e30f, best1 = 1e30f;
     *best_solve = 0;
     *best_sweep = 0;
     for (int v = 0; v < kNumSolveVariants; ++v) {
-        std::vector<float> t0, t1;
+        std::vector<float> t0;
         for (int r = 0; r < reps; ++r) {
             cudaEventRecord(e0, st);
             launch_local_pass(t, d, g, W, false, v, st, dummy);
@@ -1235,22 +1259,25 @@ int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             t0.push_back(ms);
-            if (mixed) {
+        }
+        const float m0 = median(t0);
+        if (ms_out) ms_out[2 * v] = m0;
+        if (m0 < best0) { best0 = m0; *best_solve = v; }
+    }
+    if (mixed) {
+        for (int v = 0; v < kNumSolveVariants; ++v) {
+            std::vector<float> t1;
+            for (int r = 0; r < reps; ++r) {
+                launch_local_pass(t, d, g, W, false, *best_solve, st, dummy);
                 cudaEventRecord(e0, st);
-                launch_local_pass(t, d, g, W, true, v, st, dummy);
+                for (int it = 0; it < t.cfg.ir_max_sweeps; ++it) launch_local_pass(t, d, g, W, true, v, st, dummy);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
+                float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 t1.push_back(ms);
             }
-        }
-        std::sort(t0.begin(), t0.end());
-        const float m0 = t0[t0.size() / 2];
-        if (ms_out) ms_out[2 * v] = m0;
-        if (m0 < best0) { best0 = m0; *best_solve = v; }
-        if (mixed) {
-            std::sort(t1.begin(), t1.end());
-            const float m1 = t1[t1.size() / 2];
+            const float m1 = median(t1);
             if (ms_out) ms_out[2 * v + 1] = m1;
             if (m1 < best1) { best1 = m1; *best_sweep = v; }
         }

@@ -134,6 +134,23 @@ def _c5():
     )
 
 
+def _c5_slab():
+    """A 128 x 256 x 128 slab of the C5 layout (2048 subdomains of 16 x 16 x 8):
+    the same kernels and block shapes at a size a full profiler capture handles."""
+    nx, ny, nz = 128, 256, 128
+    return Workload(
+        name="mrcm_128x256x128_sub16x16x8",
+        n=(nx, ny, nz),
+        edges=(uniform_edges(nx, 16), uniform_edges(ny, 16), uniform_edges(nz, 8)),
+        patch=((0, 0), (0, 0), (0, 0)),
+        beta_mode=BETA_CONST, beta_const=1.0,
+        make_K=lambda: lognormal_K((nz, ny, nx), 3.0, 8.0, 0.05, seed=0),
+        make_f=lambda: five_spot_wells(nx, ny, nz),
+        note="128x256x128 cells, 2048 subdomains of 16x16x8, whole-face patches, "
+             "sigma=3 lambda=8 Kz=0.05Kx",
+    )
+
+
 def small(n=(8, 8, 4), edges=None, patch=((0, 0), (0, 0), (0, 0)), sigma=1.0, lam=3.0,
           kz_ratio=0.3, seed=1, beta_mode=BETA_CONST, beta_const=1.0, alpha=1.0,
           wells="corner", h=(1.0, 1.0, 1.0)):
@@ -156,6 +173,7 @@ WORKLOADS = {
     "c2_betaHK": lambda: _c2(BETA_ALPHA_H_OVER_K),
     "c3": _c3,
     "c5": _c5,
+    "c5_slab": _c5_slab,
 }
 
 

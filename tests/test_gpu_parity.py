@@ -175,7 +175,7 @@ def test_autotune_and_cache(tmp_path):
     s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
     s.factor_local(K)
     v0, v1 = s.autotune(f)
-    assert 0 <= v0 < 8 and 0 <= v1 < 8
+    assert 0 <= v0 < 10 and 0 <= v1 < 10
     line = open(cache).read().split()
     assert int(line[1]) == v0 and int(line[2]) == v1
     p, u, X, _ = s.solve(K, f)
@@ -234,7 +234,7 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
     s.factor_local(K)
     s.autotune(f)
     key = open(cache).read().split()[0]
-    for v in range(8):
+    for v in range(10):
         with open(cache, "w") as fp:
             fp.write(f"{key} {v} {v}\n")
         sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
