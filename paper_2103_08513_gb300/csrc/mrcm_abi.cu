@@ -100,18 +100,20 @@ std::string tune_key(const mrcm_handle* h) {
     return buf;
 }
 
-// Tune cache: text lines "key solve_variant sweep_variant".
+// Tune cache: text lines "key solve_variant sweep_variant factor_variant".
 void load_tune_cache(mrcm_handle* h) {
     if (h->t.tune_cache.empty()) return;
     FILE* fp = fopen(h->t.tune_cache.c_str(), "r");
     if (!fp) return;
     char key[256];
-    int v0, v1;
+    int v0, v1, v2;
     const std::string want = tune_key(h);
-    while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3) {
-        if (want == key && v0 >= 0 && v0 < 10 && v1 >= 0 && v1 < 10) {
+    while (fscanf(fp, "%255s %d %d %d", key, &v0, &v1, &v2) == 4) {
+        if (want == key && v0 >= 0 && v0 < mrcm::kMaxSolveVariants && v1 >= 0 && v1 < mrcm::kMaxSolveVariants &&
+            v2 >= 0 && v2 < mrcm::kNumFactorVariants) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
+            h->d.factor_variant = v2;
         }
     }
     fclose(fp);
@@ -123,14 +125,16 @@ void store_tune_cache(mrcm_handle* h) {
     const std::string want = tune_key(h);
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "r")) {
         char key[256];
-        int v0, v1;
-        while (fscanf(fp, "%255s %d %d", key, &v0, &v1) == 3)
-            if (want != key) keep.push_back(std::string(key) + " " + std::to_string(v0) + " " + std::to_string(v1));
+        int v0, v1, v2;
+        while (fscanf(fp, "%255s %d %d %d", key, &v0, &v1, &v2) == 4)
+            if (want != key)
+                keep.push_back(std::string(key) + " " + std::to_string(v0) + " " + std::to_string(v1) + " " +
+                               std::to_string(v2));
         fclose(fp);
     }
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "w")) {
         for (auto& line : keep) fprintf(fp, "%s\n", line.c_str());
-        fprintf(fp, "%s %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant);
+        fprintf(fp, "%s %d %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant, h->d.factor_variant);
         fclose(fp);
     }
 }
@@ -378,12 +382,13 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
     mrcm_status st = check_ws(h, ws);
     if (st != MRCM_OK) return st;
     if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
-    int v0 = 0, v1 = 0;
+    int v0 = 0, v1 = 0, v2 = h->d.factor_variant;
     float ms[2 * mrcm::kMaxSolveVariants];
-    int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, ms);
+    int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, &v2, ms);
     if ((st = after_launch(h, rc, "mrcm_autotune")) != MRCM_OK) return st;
     h->d.solve_variant = v0;
     h->d.sweep_variant = v1;
+    h->d.factor_variant = v2;
     drop_graph(h);                       // a captured graph holds the old variants
     store_tune_cache(h);
     h->stage = 1;                        // the tuning runs overwrote the MBF array

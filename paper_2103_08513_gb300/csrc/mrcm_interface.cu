@@ -102,23 +102,24 @@ __device__ __forceinline__ double rcp64(double d) {
 // LDL^T of the nbk x nbk (nbk <= 32) diagonal block of a front, in place
 // (strict lower part becomes L11, the diagonal D), together with V = L11^{-1}.
 // Row i of the work array T holds [row i of the block | row i of V]; V starts
-// as I.  Step k, with l_i = T[i][k] / d_k for i > k, updates every row i > k
-// by T[i][c] -= l_i u_c with u_c = T[c][k] on the block part (k < c <= i) and
-// u_c = V[k][c] on the V part (c <= k): the rank-1 Schur update of the block
-// and V <- (I - l e_k^T) V at once (row k of V is final at step k).  One lane
-// per column, so a row costs one FP64 instruction per step.  The warp that
-// updates row k + 1 first computes 1 / d_{k+1} right away, overlapping the
-// other rows' updates.  A zero or NaN pivot is replaced by 1 and counted.
-// Block-wide.
+// as I.  Step k: with w_c = T[c][k] / d_k on the block part (k < c) and
+// w_c = V[k][c] / d_k on the V part (c <= k), every row i > k takes
+//   T[i][c] -= T[i][k] w_c   (k < c <= i, and all c <= k of V),
+// the rank-1 Schur update of the block and V <- (I - l e_k^T) V at once (row k
+// of V is final at step k), and l_i = T[i][k] / d_k goes to a separate column
+// store, so column k stays readable during the step: one barrier per pivot.
+// One lane per column: a row costs one FP64 FMA per step.  Warp 0 updates
+// row k + 1 alone and then computes 1 / d_{k+1} (Newton iteration), while
+// warps 1.. update the other rows.  A zero or NaN pivot is replaced by 1 and
+// counted.  Block-wide, >= 2 warps.
 constexpr int kDiagW = 2 * kPanel + 1;
-constexpr int kDiagWork = kPanel * kDiagW + 3 * kPanel + 4;   // doubles of shared work space
+constexpr int kDiagWork = kPanel * kDiagW + kPanel * (kPanel + 1) + kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
                                   int* status, double* work) {
     double (*T)[kDiagW] = reinterpret_cast<double (*)[kDiagW]>(work);
-    double* u = work + kPanel * kDiagW;
-    double* lcol = u + 2 * kPanel;
-    double* sinv = lcol + kPanel;
-    int* zero = reinterpret_cast<int*>(sinv + 1);
+    double (*Lc)[kPanel + 1] = reinterpret_cast<double (*)[kPanel + 1]>(work + kPanel * kDiagW);
+    double* sinv = work + kPanel * kDiagW + kPanel * (kPanel + 1);      // 1 / d_k for every k
+    int* zero = reinterpret_cast<int*>(sinv + kPanel);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
     __syncthreads();                                          // the block's last writes are complete
     for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
@@ -133,34 +134,35 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
         *zero = 0;
         double d = T[0][0];
         if (d == 0.0 || d != d) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
-        *sinv = rcp64(d);
+        sinv[0] = rcp64(d);
     }
     for (int k = 0; k < nbk; ++k) {
-        __syncthreads();                                      // rows updated, 1 / d_k ready
-        if (tid < 32) {
-            const int i = tid;
-            const bool below = i > k && i < nbk;
-            const double tik = T[i][k];
-            const double l = below ? tik * *sinv : 0.0;
-            lcol[i] = l;
-            u[i] = below ? tik : 0.0;
-            u[kPanel + i] = T[k][kPanel + i];
-            if (below) T[i][k] = l;                            // column k of L is final
-        }
-        __syncthreads();
-        for (int i = k + 1 + w; i < nbk; i += nw) {
-            const int c = lane;
-            if (c <= i) {
-                double* dst = c <= k ? &T[i][kPanel + c] : &T[i][c];
-                const double uu = c <= k ? u[kPanel + c] : u[c];
-                *dst = fma(-lcol[i], uu, *dst);
-            }
-            if (i == k + 1) {
+        __syncthreads();                                      // rows of step k - 1 done, 1 / d_k ready
+        const double inv = sinv[k];
+        const int c = lane;
+        // this lane's multiplier and target column
+        const bool vpart = c <= k;
+        const double wc = (vpart ? T[k][kPanel + c] : T[c][k]) * inv;
+        if (w == 0) {
+            if (k + 1 < nbk) {
+                const int i = k + 1;
+                if (c <= i) {
+                    double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
+                    *dst = fma(-T[i][k], wc, *dst);
+                }
                 __syncwarp();
                 if (lane == 0) {
                     double d = T[i][i];
                     if (d == 0.0 || d != d) { d = 1.0; T[i][i] = 1.0; *zero = 1; }
-                    *sinv = rcp64(d);
+                    sinv[i] = rcp64(d);
+                }
+            }
+            if (lane > k && lane < nbk) Lc[lane][k] = T[lane][k] * inv;   // column k of L
+        } else {
+            for (int i = k + 1 + w; i < nbk; i += nw - 1) {
+                if (c <= i) {
+                    double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
+                    *dst = fma(-T[i][k], wc, *dst);
                 }
             }
         }
@@ -168,7 +170,7 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
     __syncthreads();
     for (int e = tid; e < kPanel * kPanel; e += nthr) {
         const int i = e >> 5, c = e & 31;
-        if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = T[i][c];
+        if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = c == i ? T[i][i] : Lc[i][c];
         Pinv[e] = T[i][kPanel + c];
     }
     if (tid == 0 && *zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
@@ -184,7 +186,7 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
     const int nt = (n + kTile - 1) / kTile;
     const int t = blockIdx.x;
     if (t >= nt * (nt + 1) / 2) return;
-    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // FP32 estimate, fixed below
     while (ti * (ti + 1) / 2 > t) --ti;
     while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
     const int tj = t - ti * (ti + 1) / 2;
@@ -360,17 +362,29 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const 
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// v 2^e as an FP64 value built with integer operations (exact for |v| < 2^53;
-// results below the normal range become 0).
-__device__ __forceinline__ double i64_scaled(long long v, int e) {
+// The 128-bit integer v, times 2^e, rounded to the nearest FP64 value with
+// integer operations only (ties away from zero; results below the normal
+// range become 0).
+__device__ __forceinline__ double i128_scaled(__int128 v, int e) {
     if (v == 0) return 0.0;
     const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long m = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int top = 63 - __clzll((long long)m);                         // m in [2^top, 2^(top+1)), top <= 52
-    const int ex = top + e + 1023;
-    if (ex <= 0) return 0.0;
-    const unsigned long long frac = (m << (52 - top)) & 0x000FFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | frac));
+    const unsigned __int128 m = v < 0 ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long mh = (unsigned long long)(m >> 64), ml = (unsigned long long)m;
+    const int top = mh ? 127 - __clzll((long long)mh) : 63 - __clzll((long long)ml);   // m in [2^top, 2^(top+1))
+    unsigned long long mant;                                   // top 53 bits, rounded
+    int ex = top + e;
+    if (top <= 52) {
+        mant = ml << (52 - top);
+    } else {
+        const int sh = top - 52;
+        const unsigned __int128 q = m >> sh;
+        const bool up = (m >> (sh - 1)) & 1;                   // first dropped bit
+        mant = (unsigned long long)q + (up ? 1ull : 0ull);
+        if (mant >> 53) { mant >>= 1; ++ex; }                  // rounding carried into a new bit
+    }
+    const int be = ex + 1023;
+    if (be <= 0) return 0.0;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
 }
 
 // Exact integer value (|v| < 2^22) of an FP32 holding one: add 1.5 2^23 and
@@ -399,7 +413,7 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
     const int T = nt * (nt + 1) / 2;
     const int t = blockIdx.x;
     if (t >= T) return;
-    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);   // FP32 estimate, fixed below
     while (ti * (ti + 1) / 2 > t) --ti;
     while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
     const int tj = t - ti * (ti + 1) / 2;
@@ -410,6 +424,12 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
     if (oz_step(fr, m, nbk)) {
         uint32_t* Sa = sbuf;                                               // rows i: slices of L21 D
         uint32_t* Sb = sbuf + kPanel * kOzLd;                              // rows j: slices of L21
+        __shared__ int ez[2 * kPanel];                                     // row exponents E_i, F_j
+        if (threadIdx.x < 2 * kPanel) {
+            const int op = threadIdx.x / kPanel, rr = threadIdx.x % kPanel;
+            const int gr = (op == 0 ? i0 : j0) + rr;
+            ez[threadIdx.x] = gr < n ? oz_exp[2 * ((long long)fr.s_off + gr) + op] : 0;
+        }
         const uint4* src = reinterpret_cast<const uint4*>(oz);
         for (int e = threadIdx.x; e < 2 * kPanel * (kOzLd - 4) / 4; e += blockDim.x) {
             const int op = e / (kPanel * (kOzLd - 4) / 4);
@@ -453,19 +473,16 @@ k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, 
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            long long hi = 0, lo = 0;
+            // S = sum_d P_d 2^{7(7-d)} exactly (|S| < 2^72), then one rounding to FP64
+            __int128 sum = 0;
 #pragma unroll
-            for (int d = 0; d < kOzS; ++d) {
-                const long long pv = f32_int(acc[d][q]);
-                if (d < 4) hi += pv << (7 * (3 - d));
-                else lo += pv << (7 * (7 - d));
-            }
+            for (int d = 0; d < kOzS; ++d) sum += (__int128)f32_int(acc[d][q]) << (7 * (7 - d));
             const int gi = i0 + mr + g + (q >> 1) * 8;
             const int gj = j0 + nc + 2 * tg + (q & 1);
             if (gi < n && gj <= gi) {
-                const int e = oz_exp[2 * ((long long)fr.s_off + gi)] + oz_exp[2 * ((long long)fr.s_off + gj) + 1];
+                const int e = ez[mr + g + (q >> 1) * 8] + ez[kPanel + nc + 2 * tg + (q & 1)];
                 double* c = A + (long long)gi * n + gj;
-                *c = (*c - i64_scaled(hi, e - 35)) - i64_scaled(lo, e - 63);
+                *c -= i128_scaled(sum, e - 63);
             }
         }
     } else {

@@ -13,6 +13,7 @@ constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 f
 constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
 constexpr int kMaxSolveVariants = 16;  // capacity of the per-variant tables
+constexpr int kNumFactorVariants = 3;  // factor kernels for blocks with b <= 64
 constexpr int kOzMinN = 32;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
 constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
@@ -136,6 +137,7 @@ struct DeviceTables {
     int* solve_list = nullptr;                 // all subdomains, costliest solve first (wave by wave)
     int sms = 0;
     size_t solve_smem = 0;
+    int factor_variant = 1;                    // blocks with b <= 64: 0 row per thread, 1 8x8 tiles, 2 4x4 tiles
     int solve_occ[kMaxSolveVariants] = {};
     int sweep_occ[kMaxSolveVariants] = {};
     int solve_variant = 0, sweep_variant = 0;  // chosen by the autotuner (or the tune cache)
@@ -262,8 +264,8 @@ int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout&
 int configure_local(const Tables& t, DeviceTables& d);
 int configure_interface(const Tables& t, DeviceTables& d);
 int configure_reconstruct(const Tables& t);
-int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
-                   void* stream, int reps, int* best_solve, int* best_sweep, float* ms_out);
+int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, const double* f,
+                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, float* ms_out);
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P);

@@ -357,15 +357,18 @@ k_block_factor_reg(const SubInfo* __restrict__ subs, const int* __restrict__ lis
 // exactly (M[k][j] / p, -M[i][k] / p and 1 / p).  W_{s-1} stays in the
 // registers to form S_s = D_s - t o W_{s-1} o t for the next slab.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2)
+template <int TPT, int G>
+__global__ void __launch_bounds__(G * G, G == 16 ? 2 : 8)
 k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                     const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
                     long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
-    constexpr int B = kTileBlock;
+    // G x G threads, TPT x TPT entries each
+    constexpr int B = TPT * G;                              // largest block covered
+    constexpr int NV = TPT / 4;                             // float4 per tile row
     const SubInfo s = subs[list[blockIdx.x]];
     const int b = s.b, su = s.su;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int i0 = ty * 8, j0 = tx * 8;
+    const int tx = threadIdx.x % G, ty = threadIdx.x / G;
+    const int i0 = ty * TPT, j0 = tx * TPT;
     const double* cd = coef + s.cell_off;
     const double* cu = coef + nct + s.cell_off;
     const double* cv = coef + 2 * nct + s.cell_off;
@@ -374,11 +377,11 @@ k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ li
     float* W = Wall + s.w_off;
     __shared__ __align__(16) float prow[2][B];
     __shared__ __align__(16) float sd[B], sup[B], svp[B], st[B];
-    float a[8][8];
+    float a[TPT][TPT];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < TPT; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) a[r][c] = 0.0f;
+        for (int c = 0; c < TPT; ++c) a[r][c] = 0.0f;
     int bad = 0;
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
@@ -399,11 +402,11 @@ k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ li
         __syncthreads();
         // S_s = D_s - t o W_{s-1} o t
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < TPT; ++r) {
             const int i = i0 + r;
             const float ti = st[i];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < TPT; ++c) {
                 const int j = j0 + c;
                 float v = -ti * st[j] * a[r][c];
                 if (j == i) v += sd[i];
@@ -418,62 +421,69 @@ k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ li
 #pragma unroll 1
         for (int k = 0; k < b; ++k) {
             float* pr = prow[k & 1];
-            if (ty == (k >> 3)) {
-                const int rk = k & 7;
+            if (ty == k / TPT) {
+                const int rk = k % TPT;
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
+                for (int r = 0; r < TPT; ++r)
                     if (r == rk) {
-                        reinterpret_cast<float4*>(pr + j0)[0] = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
-                        reinterpret_cast<float4*>(pr + j0)[1] = make_float4(a[r][4], a[r][5], a[r][6], a[r][7]);
+#pragma unroll
+                        for (int q = 0; q < NV; ++q)
+                            reinterpret_cast<float4*>(pr + j0)[q] =
+                                make_float4(a[r][4 * q], a[r][4 * q + 1], a[r][4 * q + 2], a[r][4 * q + 3]);
                     }
             }
             __syncthreads();
             float p = pr[k];
             if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
             const float ip = 1.0f / p;
-            const float4 q0 = reinterpret_cast<const float4*>(pr + j0)[0], q1 = reinterpret_cast<const float4*>(pr + j0)[1];
-            const float4 c0 = reinterpret_cast<const float4*>(pr + i0)[0], c1 = reinterpret_cast<const float4*>(pr + i0)[1];
-            const float rkv[8] = {q0.x * ip, q0.y * ip, q0.z * ip, q0.w * ip, q1.x * ip, q1.y * ip, q1.z * ip, q1.w * ip};
-            float ck[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            float rkv[TPT], ck[TPT];
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int q = 0; q < NV; ++q) {
+                const float4 qv = reinterpret_cast<const float4*>(pr + j0)[q];
+                const float4 cv4 = reinterpret_cast<const float4*>(pr + i0)[q];
+                rkv[4 * q] = qv.x * ip; rkv[4 * q + 1] = qv.y * ip; rkv[4 * q + 2] = qv.z * ip; rkv[4 * q + 3] = qv.w * ip;
+                ck[4 * q] = cv4.x; ck[4 * q + 1] = cv4.y; ck[4 * q + 2] = cv4.z; ck[4 * q + 3] = cv4.w;
+            }
+#pragma unroll
+            for (int r = 0; r < TPT; ++r)
                 if (i0 + r < k) ck[r] = -ck[r];                   // M[i][k] = sigma_i M[k][i]
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < TPT; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-ck[r], rkv[c], a[r][c]);
-            if (ty == (k >> 3)) {                                 // row k: M[k][j] / p
-                const int rk = k & 7;
+                for (int c = 0; c < TPT; ++c) a[r][c] = fmaf(-ck[r], rkv[c], a[r][c]);
+            if (ty == k / TPT) {                                  // row k: M[k][j] / p
+                const int rk = k % TPT;
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
+                for (int r = 0; r < TPT; ++r)
                     if (r == rk) {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) a[r][c] = rkv[c];
+                        for (int c = 0; c < TPT; ++c) a[r][c] = rkv[c];
                     }
             }
-            if (tx == (k >> 3)) {                                 // column k: -M[i][k] / p, (k, k): 1 / p
-                const int ckc = k & 7;
+            if (tx == k / TPT) {                                  // column k: -M[i][k] / p, (k, k): 1 / p
+                const int ckc = k % TPT;
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
+                for (int c = 0; c < TPT; ++c)
                     if (c == ckc) {
 #pragma unroll
-                        for (int r = 0; r < 8; ++r) a[r][c] = (i0 + r == k) ? ip : -ck[r] * ip;
+                        for (int r = 0; r < TPT; ++r) a[r][c] = (i0 + r == k) ? ip : -ck[r] * ip;
                     }
             }
         }
         // store W_s (full symmetric matrix, row major)
         float* Ws = W + (long long)sl * wstride<float>(b);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < TPT; ++r) {
             const int i = i0 + r;
             if (i < b) {
                 float* row = Ws + (long long)i * b + j0;
-                if ((b & 3) == 0 && j0 + 8 <= b) {
-                    reinterpret_cast<float4*>(row)[0] = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
-                    reinterpret_cast<float4*>(row)[1] = make_float4(a[r][4], a[r][5], a[r][6], a[r][7]);
+                if ((b & 3) == 0 && j0 + TPT <= b) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q)
+                        reinterpret_cast<float4*>(row)[q] = make_float4(a[r][4 * q], a[r][4 * q + 1], a[r][4 * q + 2], a[r][4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
+                    for (int c = 0; c < TPT; ++c)
                         if (j0 + c < b) row[c] = a[r][c];
                 }
             }
@@ -1091,11 +1101,19 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
                 (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
     } else {
-        if (n_small > 0)
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
-                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        if (n_small > 0) {
+            if (d.factor_variant == 0)
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_reg<<<n_small, kRegMaxB, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
+                    (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+            else if (d.factor_variant == 1)
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 8><<<n_small, 64, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
+                    (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+            else
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<4, 16><<<n_small, 256, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
+                    (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        }
         if (n_mid > 0)
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
+            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 16><<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
                 (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         if (n_large > 0) {
             size_t sm = factor_smem<float>(t.max_b);
@@ -1226,13 +1244,14 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     return (int)cudaGetLastError();
 }
 
-// Autotuner: (1) time every variant's first solve (median of `reps`) and keep
+// Autotuner: (0) time the factor kernels for blocks with b <= 64 and keep
+// the faster (the factor is then recomputed with it); (1) time every variant's first solve (median of `reps`) and keep
 // the fastest; (2) for every variant, after an untimed first solve, time the
 // whole refinement sequence as the solve runs it (ir_max_sweeps sweeps with
 // the configured tolerance, so retired columns shrink the later sweeps) and
 // keep the fastest.  Tuned on the first wave.
-int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
-                   void* stream, int reps, int* best_solve, int* best_sweep, float* ms_out) {
+int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, const double* f,
+                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, float* ms_out) {
     cudaStream_t st = (cudaStream_t)stream;
     LocalArgs g = local_args(t, d, L, ws, f);
     g.tol2 = t.cfg.ir_tol * t.cfg.ir_tol;
@@ -1246,6 +1265,27 @@ int autotune_local(const Tables& t, const DeviceTables& d, const Layout& L, char
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     auto median = [](std::vector<float>& v) { std::sort(v.begin(), v.end()); return v[v.size() / 2]; };
+    // (0) factor kernel for the blocks with b <= 64 (mixed precision): a row per thread, 8 x 8 or 4 x 4 tiles
+    if (mixed && t.wave_class_off[1] > t.wave_class_off[0]) {
+        float bestf = 1e30f;
+        for (int fv = 0; fv < kNumFactorVariants; ++fv) {
+            d.factor_variant = fv;
+            std::vector<float> tf;
+            for (int r = 0; r < reps; ++r) {
+                cudaEventRecord(e0, st);
+                launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tf.push_back(ms);
+            }
+            const float mf = median(tf);
+            if (mf < bestf) { bestf = mf; *best_factor = fv; }
+        }
+        d.factor_variant = *best_factor;
+        launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
+    }
     float best0 = 1e30f, best1 = 1e30f;
     *best_solve = 0;
     *best_sweep = 0;

@@ -233,10 +233,11 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
     s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
     s.factor_local(K)
     s.autotune(f)
-    key = open(cache).read().split()[0]
-    for v in range(10):
+    key, _, _, fv = open(cache).read().split()[:4]
+    # every solve variant with the tuned small-block factor, and both small-block factor kernels
+    for v, fvv in [(v, fv) for v in range(10)] + [(0, 0), (0, 1), (0, 2)]:
         with open(cache, "w") as fp:
-            fp.write(f"{key} {v} {v}\n")
+            fp.write(f"{key} {v} {v} {fvv}\n")
         sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
         p, u, X, _ = sv.solve(K, f)
         assert rel_l2(X.cpu().numpy(), r.X) < 1e-8, v
