@@ -283,7 +283,10 @@ def parse():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir"])
     ap.add_argument("--ir-sweeps", type=int, default=None,
-                    help="FP64 refinement sweeps of the mixed local solve (default 6 for the C5 layouts, else 4)")
+                    help="FP64 refinement sweeps of the mixed local solve (default 6 for the C5 layouts, else 3: "
+                         "the fewest that keep p and u within 1e-8 of the FP64 form with margin)")
+    ap.add_argument("--ir-tol", type=float, default=1e-11,
+                    help="per-column refinement stop ||r|| <= tol ||b|| (columns retire early)")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -353,13 +356,13 @@ def main():
     props = torch.cuda.get_device_properties(local)
 
     if args.ir_sweeps is None:
-        args.ir_sweeps = 6 if args.workload in ("c5", "c5_slab") else 4
+        args.ir_sweeps = 6 if args.workload in ("c5", "c5_slab") else 3
     wave_gb = args.wave_gb if args.wave_gb is not None else (16.0 if args.workload == "c5" else 0.0)
     wave_bytes = int(wave_gb * (1 << 30))
 
     def make(precision):
         return MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const,
-                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=1e-13, device=dev,
+                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=args.ir_tol, device=dev,
                     wave_bytes=wave_bytes)
 
     Kd = torch.from_numpy(K).to(dev)
@@ -502,6 +505,7 @@ def main():
                    "execution": "CUDA graph of the five device calls, replayed per step",
                    "autotuned_variants": {"first_solve": tuned[0], "sweep": tuned[1]},
                    "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
+                   "ir_tol": args.ir_tol if args.precision != "fp64" else None,
                    "waves": {"budget_bytes": wave_bytes, "count": s.sizes.get("n_waves", 1)},
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write, outside the events)"},
