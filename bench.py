@@ -515,7 +515,7 @@ def main():
         "config": {"workload": w.name, "cells": w.cells, "subdomains": n_sub,
                    "interface_unknowns": s.n_interface, "precision": args.precision,
                    "execution": "CUDA graph of the five device calls, replayed per step",
-                   "autotuned_variants": {"first_solve": tuned[0], "sweep": tuned[1]},
+                   "autotuned_variants": s.tuning(),
                    "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
                    "ir_tol": args.ir_tol if args.precision != "fp64" else None,
                    "waves": {"budget_bytes": wave_bytes, "count": s.sizes.get("n_waves", 1)},

@@ -223,6 +223,14 @@ mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double*
 mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
                           int* sweep_variant);
 
+/* The kernel variants the handle uses (host only; after mrcm_autotune or a
+ * tune-cache hit, else the defaults): local solve first pass and refinement
+ * sweep (0-9), factor for blocks with b <= 64 (0 a row per thread, 1 8x8
+ * register tiles, 2 4x4 tiles) and for 64 < b <= 128 (0 register tiles,
+ * 1 tensor cores with the block in tensor memory).  Any pointer may be NULL. */
+mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* sweep_variant, int* factor_small,
+                              int* factor_mid);
+
 /* Device-side status of the last solve, read back synchronously: number of
  * non-positive local pivots, unconverged refinement columns, interface zero
  * pivots and the refinement sweeps used. */

@@ -100,20 +100,21 @@ std::string tune_key(const mrcm_handle* h) {
     return buf;
 }
 
-// Tune cache: text lines "key solve_variant sweep_variant factor_variant".
+// Tune cache: text lines "key solve_variant sweep_variant factor_variant factor_mid_variant".
 void load_tune_cache(mrcm_handle* h) {
     if (h->t.tune_cache.empty()) return;
     FILE* fp = fopen(h->t.tune_cache.c_str(), "r");
     if (!fp) return;
     char key[256];
-    int v0, v1, v2;
+    int v0, v1, v2, v3;
     const std::string want = tune_key(h);
-    while (fscanf(fp, "%255s %d %d %d", key, &v0, &v1, &v2) == 4) {
+    while (fscanf(fp, "%255s %d %d %d %d", key, &v0, &v1, &v2, &v3) == 5) {
         if (want == key && v0 >= 0 && v0 < mrcm::kMaxSolveVariants && v1 >= 0 && v1 < mrcm::kMaxSolveVariants &&
-            v2 >= 0 && v2 < mrcm::kNumFactorVariants) {
+            v2 >= 0 && v2 < mrcm::kNumFactorVariants && (v3 == 0 || v3 == 1)) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
             h->d.factor_variant = v2;
+            h->d.factor_mid_variant = v3;
         }
     }
     fclose(fp);
@@ -125,16 +126,17 @@ void store_tune_cache(mrcm_handle* h) {
     const std::string want = tune_key(h);
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "r")) {
         char key[256];
-        int v0, v1, v2;
-        while (fscanf(fp, "%255s %d %d %d", key, &v0, &v1, &v2) == 4)
+        int v0, v1, v2, v3;
+        while (fscanf(fp, "%255s %d %d %d %d", key, &v0, &v1, &v2, &v3) == 5)
             if (want != key)
                 keep.push_back(std::string(key) + " " + std::to_string(v0) + " " + std::to_string(v1) + " " +
-                               std::to_string(v2));
+                               std::to_string(v2) + " " + std::to_string(v3));
         fclose(fp);
     }
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "w")) {
         for (auto& line : keep) fprintf(fp, "%s\n", line.c_str());
-        fprintf(fp, "%s %d %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant, h->d.factor_variant);
+        fprintf(fp, "%s %d %d %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant, h->d.factor_variant,
+                h->d.factor_mid_variant);
         fclose(fp);
     }
 }
@@ -375,6 +377,16 @@ mrcm_status mrcm_export(mrcm_handle* h, void* ws, int what, int sub, void* dst, 
     return MRCM_OK;
 }
 
+mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* sweep_variant, int* factor_small,
+                              int* factor_mid) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    if (solve_variant) *solve_variant = h->d.solve_variant;
+    if (sweep_variant) *sweep_variant = h->d.sweep_variant;
+    if (factor_small) *factor_small = h->d.factor_variant;
+    if (factor_mid) *factor_mid = h->d.factor_mid_variant;
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
                           int* sweep_variant) {
     if (!h) return MRCM_ERR_INVALID_ARG;
@@ -382,13 +394,14 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
     mrcm_status st = check_ws(h, ws);
     if (st != MRCM_OK) return st;
     if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
-    int v0 = 0, v1 = 0, v2 = h->d.factor_variant;
+    int v0 = 0, v1 = 0, v2 = h->d.factor_variant, v3 = h->d.factor_mid_variant;
     float ms[2 * mrcm::kMaxSolveVariants];
-    int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, &v2, ms);
+    int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, &v2, &v3, ms);
     if ((st = after_launch(h, rc, "mrcm_autotune")) != MRCM_OK) return st;
     h->d.solve_variant = v0;
     h->d.sweep_variant = v1;
     h->d.factor_variant = v2;
+    h->d.factor_mid_variant = v3;
     drop_graph(h);                       // a captured graph holds the old variants
     store_tune_cache(h);
     h->stage = 1;                        // the tuning runs overwrote the MBF array

@@ -138,6 +138,7 @@ struct DeviceTables {
     int sms = 0;
     size_t solve_smem = 0;
     int factor_variant = 1;                    // blocks with b <= 64: 0 row per thread, 1 8x8 tiles, 2 4x4 tiles
+    int factor_mid_variant = 0;                // 64 < b <= 128: 0 register tiles, 1 tensor cores (TMEM)
     int solve_occ[kMaxSolveVariants] = {};
     int sweep_occ[kMaxSolveVariants] = {};
     int solve_variant = 0, sweep_variant = 0;  // chosen by the autotuner (or the tune cache)
@@ -265,7 +266,8 @@ int configure_local(const Tables& t, DeviceTables& d);
 int configure_interface(const Tables& t, DeviceTables& d);
 int configure_reconstruct(const Tables& t);
 int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, const double* f,
-                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, float* ms_out);
+                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, int* best_factor_mid,
+                   float* ms_out);
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P);

@@ -357,6 +357,304 @@ k_block_factor_reg(const SubInfo* __restrict__ subs, const int* __restrict__ lis
 // exactly (M[k][j] / p, -M[i][k] / p and 1 / p).  W_{s-1} stays in the
 // registers to form S_s = D_s - t o W_{s-1} o t for the next slab.
 // ---------------------------------------------------------------------------
+// ---- bulk-copy staging of the W blocks (TMA unit, completion on an mbarrier)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One thread: expect `bytes` on the barrier and start the copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // earlier generic reads of dst done
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after about two seconds
+// (then the status word records a timeout and the caller stops using the buffer).
+constexpr long long kWaitCycles = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core variant for 64 < b <= 128 (FP32 accuracy from 3xTF32): the
+// running block matrix lives in tensor memory (TMEM, 128 lanes = rows x 128
+// columns), one thread per row (128 threads).  Pivots are swept 16 at a time
+// with the blocked form of the same sign-symmetric Gauss-Jordan sweep
+// (P = the 16 pivots, all unswept):
+//   M_ij <- M_ij - M_iP M_PP^{-1} M_Pj,  M_Pj <- M_PP^{-1} M_Pj,
+//   M_iP <- -M_iP M_PP^{-1},             M_PP <- M_PP^{-1}.
+// With R_j = M_PP^{-1} M_Pj = sigma_j M_PP^{-1} M[j][P]^T (sign symmetry) and
+// A_i = -M[i][P] (+ e_p on the row of pivot p), one tcgen05.mma D += A R^T
+// (M = N = 128, K = 16) performs the trailing update and the new pivot rows
+// at once; the pivot columns are then written back from registers.  Each
+// operand is split into a TF32 high part and remainder and the product is
+// taken as hi*hi + hi*lo + lo*hi (three MMAs per K step).  M_PP^{-1} (16 x 16,
+// SPD) is swept by one warp.  Operands sit in shared memory in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices, 128 B apart
+// along K, 512 B apart along rows).  W_{s-1} stays in TMEM to form S_s.
+// Every wait on the MMA completion is bounded; a timeout sets the status word
+// and stops the subdomain.
+// ---------------------------------------------------------------------------
+constexpr int kTcN = 128;      // TMEM tile edge
+constexpr int kTcP = 16;       // pivots per block step (MMA K = 2 x 8)
+constexpr int kTcSmemPad = 21 * 1024;   // dynamic shared memory that limits residency to 4 CTAs per SM
+
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {    // byte offset of (row, k) in a 128 x 16 operand
+    return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {   // shared-memory matrix descriptor
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float v[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                    "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                    "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                    "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                    "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                    "r"(__float_as_uint(v[15]))
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_sync() {      // block barrier that also orders tcgen05 operations
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// D (TMEM) += A B^T, TF32 operands from shared-memory descriptors, issued by one thread
+__device__ __forceinline__ void tc_mma_acc(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(dtmem), "l"(da), "l"(db), "r"(idesc) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcN, 1)
+k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
+                  const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
+                  long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
+    __shared__ __align__(1024) unsigned char opb[4][8192];          // A hi, A lo, B hi, B lo (128 x 16 each)
+    __shared__ __align__(16) float mpp[kTcP][kTcP];                 // M_PP, swept in place to M_PP^{-1}
+    __shared__ float sd[kTcN], sup[kTcN], svp[kTcN], st[kTcN];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int stop_s;
+    const SubInfo s = subs[list[blockIdx.x]];
+    const int b = s.b, su = s.su;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i = tid;                                              // this thread's row = TMEM lane
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* sc = scale + s.cell_off;
+    float* W = Wall + s.w_off;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" :: "r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        stop_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);     // this warp's lane quarter, column 0
+    // instruction descriptor: D F32, A/B TF32, both K-major, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcN >> 4) << 24);
+    uint32_t phase = 0;
+    int bad = 0;
+    {
+        float z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) z[q] = 0.0f;
+        for (int c0 = 0; c0 < kTcN; c0 += 16) tm_st16(trow + c0, z);  // W_{-1} = 0
+    }
+    for (int sl = 0; sl < s.ns; ++sl) {
+        const int base = sl * b;
+        for (int r = tid; r < kTcN; r += blockDim.x) {
+            float d = 0.f, u = 0.f, v = 0.f, t = 0.f;
+            if (r < b) {
+                const int c = base + r;
+                d = (float)(cd[c] * sc[c] * sc[c]);
+                if ((r % su) + 1 < su) u = (float)(-cu[c] * sc[c] * sc[c + 1]);
+                if (r + su < b) v = (float)(-cv[c] * sc[c] * sc[c + su]);
+                if (sl > 0) t = (float)(cs[c - b] * sc[c - b] * sc[c]);
+                scf_all[s.cell_off + c] = (float)sc[c];
+                tsc_all[s.cell_off + c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+            }
+            sd[r] = d; sup[r] = u; svp[r] = v; st[r] = t;
+        }
+        __syncthreads();
+        // S_s = D_s - t o W_{s-1} o t, this thread's row
+        for (int c0 = 0; c0 < kTcN; c0 += 16) {
+            float v[16];
+            tm_ld16(trow + c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int j = c0 + q;
+                float x = -st[i] * st[j] * v[q];
+                if (j == i) x += sd[i];
+                if (j == i + 1) x += sup[i];
+                if (j + 1 == i) x += sup[j];
+                if (j == i + su) x += svp[i];
+                if (j + su == i) x += svp[j];
+                v[q] = (i < b && j < b) ? x : 0.0f;
+            }
+            tm_st16(trow + c0, v);
+        }
+        tc_sync();
+        // blocked sweep, 16 pivots per step
+        for (int k0 = 0; k0 < b; k0 += kTcP) {
+            const int nbk = min(kTcP, b - k0);
+            float m[16];
+            tm_ld16(trow + k0, m);                                  // M[i][P]
+            const int ip = i - k0;                                  // pivot index of this row, if in P
+            if (ip >= 0 && ip < kTcP) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) mpp[ip][q] = (ip < nbk && q < nbk) ? m[q] : (q == ip ? 1.0f : 0.0f);
+            }
+            __syncthreads();
+            if (warp == 0) {                                        // sweep M_PP (lane r < 16 owns row r)
+                for (int q = 0; q < kTcP; ++q) {
+                    float p = mpp[q][q];
+                    if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+                    const float inv = 1.0f / p;
+                    float rq[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) rq[c] = mpp[q][c];
+                    const float cr = lane < kTcP ? mpp[lane][q] : 0.0f;
+                    __syncwarp();
+                    if (lane < kTcP) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            float x;
+                            if (lane == q) x = c == q ? inv : rq[c] * inv;
+                            else if (c == q) x = -cr * inv;
+                            else x = fmaf(-cr, rq[c] * inv, mpp[lane][c]);
+                            mpp[lane][c] = x;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            // operands: A_i = -M[i][P] (+ e_p on pivot rows), R_i = sigma_i M_PP^{-1} M[i][P]^T
+            const float sg = i < k0 ? -1.0f : 1.0f;
+            float R[16], cnew[16];
+#pragma unroll
+            for (int p = 0; p < 16; ++p) { R[p] = 0.0f; cnew[p] = 0.0f; }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float4* row = reinterpret_cast<const float4*>(&mpp[q][0]);   // row q of M_PP^{-1}
+#pragma unroll
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    const float4 w4 = row[p4];
+                    const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        R[q] = fmaf(wq[t], m[4 * p4 + t], R[q]);        // (M_PP^{-1} m)[q]
+                        cnew[4 * p4 + t] = fmaf(-m[q], wq[t], cnew[4 * p4 + t]);   // (-m M_PP^{-1})[p]
+                    }
+                }
+            }
+            unsigned char* Ah = opb[0]; unsigned char* Al = opb[1];
+            unsigned char* Bh = opb[2]; unsigned char* Bl = opb[3];
+#pragma unroll
+            for (int p4 = 0; p4 < 4; ++p4) {
+                float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int p = 4 * p4 + t;
+                    const float a = -m[p] + (ip == p ? 1.0f : 0.0f);
+                    const float r = sg * R[p];
+                    ah[t] = tf32_hi(a); al[t] = a - ah[t];
+                    bh[t] = tf32_hi(r); bl[t] = r - bh[t];
+                }
+                const uint32_t o = tc_off(i, 4 * p4);
+                *reinterpret_cast<float4*>(Ah + o) = make_float4(ah[0], ah[1], ah[2], ah[3]);
+                *reinterpret_cast<float4*>(Al + o) = make_float4(al[0], al[1], al[2], al[3]);
+                *reinterpret_cast<float4*>(Bh + o) = make_float4(bh[0], bh[1], bh[2], bh[3]);
+                *reinterpret_cast<float4*>(Bl + o) = make_float4(bl[0], bl[1], bl[2], bl[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor core
+            tc_sync();
+            if (tid == 0) {
+                const uint32_t ah0 = smem_u32(Ah), al0 = smem_u32(Al), bh0 = smem_u32(Bh), bl0 = smem_u32(Bl);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t ko = ks * 256;                       // K step of 8 = two core matrices
+                    const uint64_t dah = tc_desc(ah0 + ko), dal = tc_desc(al0 + ko);
+                    const uint64_t dbh = tc_desc(bh0 + ko), dbl = tc_desc(bl0 + ko);
+                    tc_mma_acc(tmem, dal, dbh, idesc);                  // D += A_lo B_hi
+                    tc_mma_acc(tmem, dah, dbl, idesc);                  //    + A_hi B_lo
+                    tc_mma_acc(tmem, dah, dbh, idesc);                  //    + A_hi B_hi
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&bar)) : "memory");
+            }
+            if (!mbar_wait(&bar, phase)) {                          // bounded: about two seconds
+                if (tid == 0) { atomicAdd(&status[ST_TIMEOUT], 1); stop_s = 1; }
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // new pivot columns: M_PP^{-1} on the pivot rows, -M[i][P] M_PP^{-1} elsewhere
+            if (ip >= 0 && ip < kTcP) {
+#pragma unroll
+                for (int p = 0; p < 16; ++p) cnew[p] = mpp[ip][p];
+            }
+            tm_st16(trow + k0, cnew);
+            tc_sync();
+            if (stop_s) break;
+        }
+        if (stop_s) break;
+        // W_s: row i of the swept matrix (every lane loads: the TMEM loads are warp-collective)
+        {
+            float* row = W + (long long)sl * wstride<float>(b) + (long long)min(i, b - 1) * b;
+            for (int c0 = 0; c0 < kTcN; c0 += 16) {
+                float v[16];
+                tm_ld16(trow + c0, v);
+                if (i < b) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (c0 + q < b) row[c0 + q] = v[q];
+                }
+            }
+        }
+        tc_sync();
+    }
+    if (bad && tid == 0) atomicAdd(&status[ST_NOT_SPD], 1);
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem));
+}
+
 template <int TPT, int G>
 __global__ void __launch_bounds__(G * G, G == 16 ? 2 : 8)
 k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
@@ -702,40 +1000,6 @@ template <> struct Coupling<double, false> {
     __device__ double in(double r, float, int) const { return r; }
     __device__ double out(double x, int) const { return x; }
 };
-
-// ---- bulk-copy staging of the W blocks (TMA unit, completion on an mbarrier)
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// One thread: expect `bytes` on the barrier and start the copy global -> shared.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // earlier generic reads of dst done
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-// Wait for phase `parity` of the barrier, giving up after about two seconds
-// (then the status word records a timeout and the caller stops using the buffer).
-constexpr long long kWaitCycles = 4000000000LL;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-}
 
 // Per-CTA state of the W staging pipeline, kept across subdomains (the same
 // in every thread).
@@ -1112,9 +1376,14 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
                 MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<4, 16><<<n_small, 256, 0, st>>>(d.subs, d.class_list + o0, coef, scale,
                     (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
-        if (n_mid > 0)
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 16><<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
-                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        if (n_mid > 0) {
+            if (d.factor_mid_variant == 1)       // tensor cores; the padding keeps <= 4 CTAs (4 x 128 TMEM columns) per SM
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tc<<<n_mid, kTcN, kTcSmemPad, st>>>(d.subs, d.class_list + o1, coef, scale,
+                    (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+            else
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 16><<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
+                    (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        }
         if (n_large > 0) {
             size_t sm = factor_smem<float>(t.max_b);
             MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
@@ -1179,6 +1448,7 @@ int configure_local(const Tables& t, DeviceTables& d) {
                          (int)factor_smem<double>(std::min(t.max_b, kMaxBlock64)));
     cudaFuncSetAttribute(k_block_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem<float>(t.max_b));
+    cudaFuncSetAttribute(k_block_factor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemPad);
     return (int)cudaGetLastError();
 }
 
@@ -1251,7 +1521,8 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
 // the configured tolerance, so retired columns shrink the later sweeps) and
 // keep the fastest.  Tuned on the first wave.
 int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, const double* f,
-                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, float* ms_out) {
+                   void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, int* best_factor_mid,
+                   float* ms_out) {
     cudaStream_t st = (cudaStream_t)stream;
     LocalArgs g = local_args(t, d, L, ws, f);
     g.tol2 = t.cfg.ir_tol * t.cfg.ir_tol;
@@ -1284,6 +1555,27 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
             if (mf < bestf) { bestf = mf; *best_factor = fv; }
         }
         d.factor_variant = *best_factor;
+        launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
+    }
+    // (0b) factor kernel for 64 < b <= 128: register tiles or the tensor-core (TMEM) kernel
+    if (mixed && t.wave_class_off[2] > t.wave_class_off[1]) {
+        float bestf = 1e30f;
+        for (int fv = 0; fv < 2; ++fv) {
+            d.factor_mid_variant = fv;
+            std::vector<float> tf;
+            for (int r = 0; r < reps; ++r) {
+                cudaEventRecord(e0, st);
+                launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tf.push_back(ms);
+            }
+            const float mf = median(tf);
+            if (mf < bestf) { bestf = mf; *best_factor_mid = fv; }
+        }
+        d.factor_mid_variant = *best_factor_mid;
         launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
     }
     float best0 = 1e30f, best1 = 1e30f;

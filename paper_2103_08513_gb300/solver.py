@@ -160,6 +160,12 @@ class MRCM:
             self.reconstruct(X, p, u, mres, stream=stream)
         return p, u, X, mres
 
+    def tuning(self):
+        """{'solve', 'sweep', 'factor_small', 'factor_mid'}: the kernel variants in use."""
+        v = [C.c_int() for _ in range(4)]
+        L.check(self.lib.mrcm_query_tuning(self.handle, *[C.byref(x) for x in v]), self.handle)
+        return dict(zip(("solve", "sweep", "factor_small", "factor_mid"), (x.value for x in v)))
+
     def autotune(self, f, stream=None):
         """Pick the fastest local-solve kernel variants for this problem (after factor_local)."""
         v0, v1 = C.c_int(), C.c_int()

@@ -159,3 +159,16 @@ def test_device_calls_reject_bad_arguments_without_gpu(lib):
     assert lib.mrcm_solve_mbf(h, C.c_void_p(256), C.c_void_p(256), None) == 9   # out of order
     assert lib.mrcm_factor_local(h, C.c_void_p(256), C.c_void_p(257), 1 << 30, None) == 1
     lib.mrcm_destroy(h)
+
+
+def test_query_tuning_reports_the_defaults_without_a_gpu(lib):
+    w = small()
+    cfg, keep = _cfg(w)
+    h = C.c_void_p()
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 0
+    v = [C.c_int(-1) for _ in range(4)]
+    assert lib.mrcm_query_tuning(h, *[C.byref(x) for x in v]) == 0
+    assert [x.value for x in v] == [0, 0, 1, 0]
+    assert lib.mrcm_query_tuning(h, None, None, None, None) == 0
+    assert lib.mrcm_query_tuning(None, None, None, None, None) == 1
+    lib.mrcm_destroy(h)

@@ -218,7 +218,7 @@ def test_repeat_calls_are_deterministic():
     assert T.equal(p1, p2) and T.equal(X1, X2)
 
 
-@pytest.mark.parametrize("name", ["many_tiles", "uneven_mix"])
+@pytest.mark.parametrize("name", ["many_tiles", "uneven_mix", "blocks_128"])
 def test_every_solve_variant_matches_oracle(name, tmp_path):
     """Each local-solve variant (SIMT tiles and the 3xTF32 tensor-core block
     products), forced through the tune cache, reaches the mixed-mode bar."""
@@ -233,11 +233,11 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
     s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
     s.factor_local(K)
     s.autotune(f)
-    key, _, _, fv = open(cache).read().split()[:4]
-    # every solve variant with the tuned small-block factor, and both small-block factor kernels
-    for v, fvv in [(v, fv) for v in range(10)] + [(0, 0), (0, 1), (0, 2)]:
+    key, _, _, fv, fm = open(cache).read().split()[:5]
+    # every solve variant with the tuned factors, then every factor kernel (b <= 64: 3, 64 < b <= 128: 2)
+    for v, fvv, fmv in [(v, fv, fm) for v in range(10)] + [(0, 0, 0), (0, 1, 0), (0, 2, 0), (0, 1, 1)]:
         with open(cache, "w") as fp:
-            fp.write(f"{key} {v} {v} {fvv}\n")
+            fp.write(f"{key} {v} {v} {fvv} {fmv}\n")
         sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
         p, u, X, _ = sv.solve(K, f)
         assert rel_l2(X.cpu().numpy(), r.X) < 1e-8, v
