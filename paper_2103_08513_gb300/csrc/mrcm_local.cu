@@ -455,12 +455,12 @@ __device__ __forceinline__ void tc_mma_acc(uint32_t dtmem, uint64_t da, uint64_t
                  :: "r"(dtmem), "l"(da), "l"(db), "r"(idesc) : "memory");
 }
 
-__global__ void __launch_bounds__(kTcN, 1)
+__global__ void __launch_bounds__(kTcN, 4)
 k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                   const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
                   long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
     __shared__ __align__(1024) unsigned char opb[4][8192];          // A hi, A lo, B hi, B lo (128 x 16 each)
-    __shared__ __align__(16) float mpp[kTcP][kTcP];                 // M_PP, swept in place to M_PP^{-1}
+    __shared__ __align__(16) float mpp[2][kTcP][kTcP];              // M_PP^{-1}, double-buffered
     __shared__ float sd[kTcN], sup[kTcN], svp[kTcN], st[kTcN];
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) unsigned long long bar;
@@ -532,37 +532,40 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
         }
         tc_sync();
         // blocked sweep, 16 pivots per step
-        for (int k0 = 0; k0 < b; k0 += kTcP) {
+        for (int k0 = 0, blk = 0; k0 < b; k0 += kTcP, ++blk) {
             const int nbk = min(kTcP, b - k0);
             float m[16];
             tm_ld16(trow + k0, m);                                  // M[i][P]
             const int ip = i - k0;                                  // pivot index of this row, if in P
-            if (ip >= 0 && ip < kTcP) {
+            float (*minv)[kTcP] = mpp[blk & 1];                     // double-buffered M_PP^{-1}
+            if (warp == (k0 >> 5)) {
+                // the warp holding rows P sweeps M_PP in registers (lane L0 + r owns row r)
+                const int L0 = k0 & 31;
+                float a[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) mpp[ip][q] = (ip < nbk && q < nbk) ? m[q] : (q == ip ? 1.0f : 0.0f);
-            }
-            __syncthreads();
-            if (warp == 0) {                                        // sweep M_PP (lane r < 16 owns row r)
+                for (int c = 0; c < 16; ++c)
+                    a[c] = (ip >= 0 && ip < nbk && c < nbk) ? m[c] : (c == ip ? 1.0f : 0.0f);
+#pragma unroll
                 for (int q = 0; q < kTcP; ++q) {
-                    float p = mpp[q][q];
-                    if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
-                    const float inv = 1.0f / p;
                     float rq[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) rq[c] = mpp[q][c];
-                    const float cr = lane < kTcP ? mpp[lane][q] : 0.0f;
-                    __syncwarp();
-                    if (lane < kTcP) {
+                    for (int c = 0; c < 16; ++c) rq[c] = __shfl_sync(0xffffffffu, a[c], L0 + q);
+                    float p = rq[q];
+                    if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+                    const float inv = 1.0f / p;
+                    const float cr = a[q];
+                    if (ip == q) {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            float x;
-                            if (lane == q) x = c == q ? inv : rq[c] * inv;
-                            else if (c == q) x = -cr * inv;
-                            else x = fmaf(-cr, rq[c] * inv, mpp[lane][c]);
-                            mpp[lane][c] = x;
-                        }
+                        for (int c = 0; c < 16; ++c) a[c] = c == q ? inv : rq[c] * inv;
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) a[c] = c == q ? -cr * inv : fmaf(-cr, rq[c] * inv, a[c]);
                     }
-                    __syncwarp();
+                }
+                if (ip >= 0 && ip < kTcP) {
+#pragma unroll
+                    for (int c = 0; c < 16; c += 4)
+                        *reinterpret_cast<float4*>(&minv[ip][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
                 }
             }
             __syncthreads();
@@ -573,7 +576,7 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
             for (int p = 0; p < 16; ++p) { R[p] = 0.0f; cnew[p] = 0.0f; }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float4* row = reinterpret_cast<const float4*>(&mpp[q][0]);   // row q of M_PP^{-1}
+                const float4* row = reinterpret_cast<const float4*>(&minv[q][0]);   // row q of M_PP^{-1}
 #pragma unroll
                 for (int p4 = 0; p4 < 4; ++p4) {
                     const float4 w4 = row[p4];
@@ -604,6 +607,10 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
                 *reinterpret_cast<float4*>(Bh + o) = make_float4(bh[0], bh[1], bh[2], bh[3]);
                 *reinterpret_cast<float4*>(Bl + o) = make_float4(bl[0], bl[1], bl[2], bl[3]);
             }
+            if (ip >= 0 && ip < kTcP) {                             // pivot rows: row of M_PP^{-1}
+#pragma unroll
+                for (int p = 0; p < 16; ++p) cnew[p] = minv[ip][p];
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor core
             tc_sync();
             if (tid == 0) {
@@ -620,20 +627,18 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(smem_u32(&bar)) : "memory");
             }
-            if (!mbar_wait(&bar, phase)) {                          // bounded: about two seconds
-                if (tid == 0) { atomicAdd(&status[ST_TIMEOUT], 1); stop_s = 1; }
-            }
+            const bool tout = !mbar_wait(&bar, phase);             // bounded: about two seconds
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // new pivot columns: M_PP^{-1} on the pivot rows, -M[i][P] M_PP^{-1} elsewhere
-            if (ip >= 0 && ip < kTcP) {
-#pragma unroll
-                for (int p = 0; p < 16; ++p) cnew[p] = mpp[ip][p];
-            }
+            // new pivot columns (the operands are consumed: the MMA has completed)
             tm_st16(trow + k0, cnew);
-            tc_sync();
-            if (stop_s) break;
+            // one decision for the whole CTA (a timeout in any thread stops the subdomain)
+            if (__syncthreads_or(tout)) {
+                if (tid == 0) { atomicAdd(&status[ST_TIMEOUT], 1); stop_s = 1; }
+                break;
+            }
         }
+        tc_sync();
         if (stop_s) break;
         // W_s: row i of the swept matrix (every lane loads: the TMEM loads are warp-collective)
         {
@@ -650,8 +655,9 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
         }
         tc_sync();
     }
-    if (bad && tid == 0) atomicAdd(&status[ST_NOT_SPD], 1);
-    tc_sync();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (__syncthreads_or(bad) && tid == 0) atomicAdd(&status[ST_NOT_SPD], 1);   // any warp's pivot
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem));
 }
 
