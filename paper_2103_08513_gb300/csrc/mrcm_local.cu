@@ -403,8 +403,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 // A_i = -M[i][P] (+ e_p on the row of pivot p), one tcgen05.mma D += A R^T
 // (M = N = 128, K = 16) performs the trailing update and the new pivot rows
 // at once; the pivot columns are then written back from registers.  Each
-// operand is split into a TF32 high part and remainder and the product is
-// taken as hi*hi + hi*lo + lo*hi (three MMAs per K step).  M_PP^{-1} (16 x 16,
+// operand is split into three TF32 pieces x1 + x2 + x3 and the product is
+// taken as the six terms down to 2^-22 relative (six MMAs per K step): the
+// two-piece "3xTF32" product leaves about 2^-21 per product, enough error to
+// stall the FP64 refinement on ill-conditioned blocks.  M_PP^{-1} (16 x 16,
 // SPD) is swept by one warp.  Operands sit in shared memory in the canonical
 // K-major layout without swizzle (8-row x 16-byte core matrices, 128 B apart
 // along K, 512 B apart along rows).  W_{s-1} stays in TMEM to form S_s.
@@ -413,7 +415,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 // ---------------------------------------------------------------------------
 constexpr int kTcN = 128;      // TMEM tile edge
 constexpr int kTcP = 16;       // pivots per block step (MMA K = 2 x 8)
-constexpr int kTcSmemPad = 21 * 1024;   // dynamic shared memory that limits residency to 4 CTAs per SM
+constexpr int kTcSmem = 6 * 8192;       // operand pieces; with the static part, at most 4 CTAs (all of TMEM) per SM
 
 __device__ __forceinline__ uint32_t tc_off(int r, int k) {    // byte offset of (row, k) in a 128 x 16 operand
     return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(kTcN, 4)
 k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                   const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
                   long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
-    __shared__ __align__(1024) unsigned char opb[4][8192];          // A hi, A lo, B hi, B lo (128 x 16 each)
+    extern __shared__ __align__(1024) unsigned char opd[];         // A1..A3, B1..B3 (128 x 16 each, 8 KB)
     __shared__ __align__(16) float mpp[2][kTcP][kTcP];              // M_PP^{-1}, double-buffered
     __shared__ float sd[kTcN], sup[kTcN], svp[kTcN], st[kTcN];
     __shared__ uint32_t tmem_base;
@@ -588,24 +590,25 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
                     }
                 }
             }
-            unsigned char* Ah = opb[0]; unsigned char* Al = opb[1];
-            unsigned char* Bh = opb[2]; unsigned char* Bl = opb[3];
+            // three-piece TF32 split x = x1 + x2 + x3 (x1, x2 TF32; x3 below 2^-22 |x|)
 #pragma unroll
             for (int p4 = 0; p4 < 4; ++p4) {
-                float ah[4], al[4], bh[4], bl[4];
+                float a1[4], a2[4], a3[4], b1[4], b2[4], b3[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int p = 4 * p4 + t;
                     const float a = -m[p] + (ip == p ? 1.0f : 0.0f);
                     const float r = sg * R[p];
-                    ah[t] = tf32_hi(a); al[t] = a - ah[t];
-                    bh[t] = tf32_hi(r); bl[t] = r - bh[t];
+                    a1[t] = tf32_hi(a); a2[t] = tf32_hi(a - a1[t]); a3[t] = (a - a1[t]) - a2[t];
+                    b1[t] = tf32_hi(r); b2[t] = tf32_hi(r - b1[t]); b3[t] = (r - b1[t]) - b2[t];
                 }
                 const uint32_t o = tc_off(i, 4 * p4);
-                *reinterpret_cast<float4*>(Ah + o) = make_float4(ah[0], ah[1], ah[2], ah[3]);
-                *reinterpret_cast<float4*>(Al + o) = make_float4(al[0], al[1], al[2], al[3]);
-                *reinterpret_cast<float4*>(Bh + o) = make_float4(bh[0], bh[1], bh[2], bh[3]);
-                *reinterpret_cast<float4*>(Bl + o) = make_float4(bl[0], bl[1], bl[2], bl[3]);
+                *reinterpret_cast<float4*>(opd + 0 * 8192 + o) = make_float4(a1[0], a1[1], a1[2], a1[3]);
+                *reinterpret_cast<float4*>(opd + 1 * 8192 + o) = make_float4(a2[0], a2[1], a2[2], a2[3]);
+                *reinterpret_cast<float4*>(opd + 2 * 8192 + o) = make_float4(a3[0], a3[1], a3[2], a3[3]);
+                *reinterpret_cast<float4*>(opd + 3 * 8192 + o) = make_float4(b1[0], b1[1], b1[2], b1[3]);
+                *reinterpret_cast<float4*>(opd + 4 * 8192 + o) = make_float4(b2[0], b2[1], b2[2], b2[3]);
+                *reinterpret_cast<float4*>(opd + 5 * 8192 + o) = make_float4(b3[0], b3[1], b3[2], b3[3]);
             }
             if (ip >= 0 && ip < kTcP) {                             // pivot rows: row of M_PP^{-1}
 #pragma unroll
@@ -614,15 +617,18 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor core
             tc_sync();
             if (tid == 0) {
-                const uint32_t ah0 = smem_u32(Ah), al0 = smem_u32(Al), bh0 = smem_u32(Bh), bl0 = smem_u32(Bl);
+                const uint32_t o0 = smem_u32(opd);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t ko = ks * 256;                       // K step of 8 = two core matrices
-                    const uint64_t dah = tc_desc(ah0 + ko), dal = tc_desc(al0 + ko);
-                    const uint64_t dbh = tc_desc(bh0 + ko), dbl = tc_desc(bl0 + ko);
-                    tc_mma_acc(tmem, dal, dbh, idesc);                  // D += A_lo B_hi
-                    tc_mma_acc(tmem, dah, dbl, idesc);                  //    + A_hi B_lo
-                    tc_mma_acc(tmem, dah, dbh, idesc);                  //    + A_hi B_hi
+                    const uint32_t ko = o0 + ks * 256;                  // K step of 8 = two core matrices
+                    const uint64_t a1d = tc_desc(ko), a2d = tc_desc(ko + 8192), a3d = tc_desc(ko + 2 * 8192);
+                    const uint64_t b1d = tc_desc(ko + 3 * 8192), b2d = tc_desc(ko + 4 * 8192), b3d = tc_desc(ko + 5 * 8192);
+                    tc_mma_acc(tmem, a2d, b2d, idesc);                  // D += a2 b2 + a3 b1 + a1 b3
+                    tc_mma_acc(tmem, a3d, b1d, idesc);                  //    + a2 b1 + a1 b2 + a1 b1
+                    tc_mma_acc(tmem, a1d, b3d, idesc);                  // (smallest terms first)
+                    tc_mma_acc(tmem, a2d, b1d, idesc);
+                    tc_mma_acc(tmem, a1d, b2d, idesc);
+                    tc_mma_acc(tmem, a1d, b1d, idesc);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(smem_u32(&bar)) : "memory");
@@ -1383,8 +1389,8 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
                     (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
         if (n_mid > 0) {
-            if (d.factor_mid_variant == 1)       // tensor cores; the padding keeps <= 4 CTAs (4 x 128 TMEM columns) per SM
-                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tc<<<n_mid, kTcN, kTcSmemPad, st>>>(d.subs, d.class_list + o1, coef, scale,
+            if (d.factor_mid_variant == 1)       // tensor cores; its shared memory keeps <= 4 CTAs (4 x 128 TMEM columns) per SM
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tc<<<n_mid, kTcN, kTcSmem, st>>>(d.subs, d.class_list + o1, coef, scale,
                     (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
             else
                 MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 16><<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
@@ -1454,7 +1460,7 @@ int configure_local(const Tables& t, DeviceTables& d) {
                          (int)factor_smem<double>(std::min(t.max_b, kMaxBlock64)));
     cudaFuncSetAttribute(k_block_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem<float>(t.max_b));
-    cudaFuncSetAttribute(k_block_factor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemPad);
+    cudaFuncSetAttribute(k_block_factor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     return (int)cudaGetLastError();
 }
 
@@ -1563,9 +1569,13 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
         d.factor_variant = *best_factor;
         launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
     }
-    // (0b) factor kernel for 64 < b <= 128: register tiles or the tensor-core (TMEM) kernel
+    // (0b) factor kernel for 64 < b <= 128: register tiles or the tensor-core (TMEM) kernel.  The
+    // tensor-core factor must also keep the refinement converging: its wave-0 solve may leave at
+    // most 1.5x (+16) the unconverged columns of the register-tile factor after the configured sweeps.
     if (mixed && t.wave_class_off[2] > t.wave_class_off[1]) {
         float bestf = 1e30f;
+        int unconv[2] = {0, 0};
+        int* status = (int*)(ws + L.status);
         for (int fv = 0; fv < 2; ++fv) {
             d.factor_mid_variant = fv;
             std::vector<float> tf;
@@ -1578,8 +1588,19 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
                 cudaEventElapsedTime(&ms, e0, e1);
                 tf.push_back(ms);
             }
+            // convergence of the refinement with this factor (wave 0)
+            k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0);
+            launch_local_pass(t, d, g, W, false, d.solve_variant, st, dummy);
+            for (int it = 0; it < t.cfg.ir_max_sweeps; ++it) {
+                g.count_unconverged = it + 1 == t.cfg.ir_max_sweeps ? 1 : 0;
+                launch_local_pass(t, d, g, W, true, d.sweep_variant, st, dummy);
+            }
+            g.count_unconverged = 0;
+            cudaMemcpyAsync(&unconv[fv], status + ST_UNCONVERGED, sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
             const float mf = median(tf);
-            if (mf < bestf) { bestf = mf; *best_factor_mid = fv; }
+            const bool converges = fv == 0 || unconv[fv] <= unconv[0] + unconv[0] / 2 + 16;
+            if (converges && mf < bestf) { bestf = mf; *best_factor_mid = fv; }
         }
         d.factor_mid_variant = *best_factor_mid;
         launch_factor_wave(t, d, L, ws, t.cfg.precision, 0, st, dummy);
