@@ -50,7 +50,7 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(INCLUDE, "mrcm.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "mrcm.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "mrcm_devmath.cuh"
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -69,35 +70,6 @@ __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const 
 
 __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 1.0 : -1.0; }
 
-// Front assembly as a gather: every lower-triangle entry (r >= q) of the
-// front is written once, as the sum (child 0 first) of the children's
-// entries at the same dofs -- J-signed, scaled subdomain blocks for leaves,
-// the lower triangle of the Schur complement otherwise.  64x64 tiles of the
-// lower triangle are spread over the grid; blockIdx.y selects the front.
-// 1 / d by Newton-Raphson iteration y <- y + y (1 - d y) from an FP32 seed
-// (FP32 reciprocal of d truncated to FP32, both conversions done with bit
-// operations): each step squares the relative error, so two steps take the
-// seed's ~2^-22 to the FP64 rounding level.  On this GPU an FP64 division is
-// a ~470-cycle dependent chain on the FP64 unit, this one four FMAs.  Values
-// whose reciprocal leaves the FP32 range fall back to the division.
-__device__ __forceinline__ double rcp64(double d) {
-    const unsigned long long bd = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((bd >> 52) & 0x7FF) - 1023;
-    if (e < -125 || e > 125) return 1.0 / d;
-    const float df = __uint_as_float((unsigned int)(bd >> 32) & 0x80000000u |
-                                     (unsigned int)(e + 127) << 23 | (unsigned int)((bd >> 29) & 0x7FFFFFu));
-    float yf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(df));
-    const unsigned int fy = __float_as_uint(yf);
-    const int ey = (int)((fy >> 23) & 0xFF);
-    double y = __longlong_as_double((long long)((unsigned long long)(fy & 0x80000000u) << 32 |
-                                                (unsigned long long)(ey - 127 + 1023) << 52 |
-                                                (unsigned long long)(fy & 0x7FFFFFu) << 29));
-    double r = fma(-d, y, 1.0);
-    y = fma(y, r, y);
-    r = fma(-d, y, 1.0);
-    return fma(y, r, y);
-}
 
 // LDL^T of the nbk x nbk (nbk <= 32) diagonal block of a front, in place
 // (strict lower part becomes L11, the diagonal D), together with V = L11^{-1}.
@@ -176,6 +148,11 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
     if (tid == 0 && *zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
 }
 
+// Front assembly as a gather: every lower-triangle entry (r >= q) of the
+// front is written once, as the sum (child 0 first) of the children's
+// entries at the same dofs -- J-signed, scaled subdomain blocks for leaves,
+// the lower triangle of the Schur complement otherwise.  64x64 tiles of the
+// lower triangle are spread over the grid; blockIdx.y selects the front.
 __global__ void __launch_bounds__(kThreads)
 k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                  const int* __restrict__ inv, const int* __restrict__ dofs, const SubInfo* __restrict__ subs,

@@ -123,7 +123,7 @@ struct Tables {
 
 // Workspace layout (byte offsets into the caller's workspace).
 struct Layout {
-    size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, face_u, W, X, R, colnorm, conv;
+    size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, face_u, face_bst, W, X, R, colnorm, conv;
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t total;
 };

@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "mrcm_devmath.cuh"
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -65,8 +66,13 @@ __device__ __forceinline__ double beta_of(int mode, double alpha, double beta_co
 // ---------------------------------------------------------------------------
 // Per-cell coefficients (FP64): diagonal (incl. Robin and Dirichlet terms),
 // the three "+" transmissibilities along (u, v, s), the Jacobi scale and the
-// Dirichlet part of the particular right-hand side.  Also T_R and beta of
-// every Robin face.
+// Dirichlet part of the particular right-hand side.  Also T_R, beta, the
+// U-MBF right-hand side -beta s T_R and beta s T_R of every Robin face.
+// Each interior face's transmissibility (area / h) 2 K1 K2 / (K1 + K2) is
+// computed once, by the cell on its low side, with a Newton reciprocal (an
+// FP64 division is a long chain on this GPU's FP64 unit); the high-side cell
+// reads it back after a barrier.  The Jacobi scale 1 / sqrt(diag) only has to
+// be a consistent preconditioner, so it is formed in FP32 and widened exactly.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
 k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
@@ -75,47 +81,68 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
                double3 bc_lo, double3 bc_hi,
                double* __restrict__ coef, double* __restrict__ scale, double* __restrict__ rhs_dir,
                double* __restrict__ face_tr, double* __restrict__ face_beta, double* __restrict__ face_u,
-               long long ncell_total) {
+               double* __restrict__ face_bst, long long ncell_total) {
     const SubInfo s = subs[blockIdx.x];
     const long long ncells = (long long)geo.n[0] * geo.n[1] * geo.n[2];
     const double* Kc[3] = {K, K + ncells, K + 2 * ncells};
     const long long stride[3] = {1, geo.n[0], (long long)geo.n[0] * geo.n[1]};
     const double blo[3] = {bc_lo.x, bc_lo.y, bc_lo.z};
     const double bhi[3] = {bc_hi.x, bc_hi.y, bc_hi.z};
+    double ah[3];                                      // area / h per axis
+    for (int a = 0; a < 3; ++a) ah[a] = geo.area[a] * rcp64(geo.h[a]);
+    int lstride[3];                                    // in-subdomain cell stride along each global axis
+    lstride[s.ua] = 1; lstride[s.va] = s.su; lstride[s.sa] = s.b;
+    double* tp[3];                                     // "+" transmissibility arrays by global axis
+    tp[s.ua] = coef + ncell_total + s.cell_off;
+    tp[s.va] = coef + 2 * ncell_total + s.cell_off;
+    tp[s.sa] = coef + 3 * ncell_total + s.cell_off;
+    // pass 1: interior faces, from their low-side cell
     for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
         int lc[3];
         local_coords(s, c, lc);
-        long long g = global_cell(s, lc, geo.n);
-        double d = 0.0, tplus[3] = {0.0, 0.0, 0.0}, rd = 0.0;
+        const long long g = global_cell(s, lc, geo.n);
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double ka = Kc[a][g];
+            double T = 0.0;
+            if (lc[a] + 1 < s.sz[a]) {
+                const double k1 = Kc[a][g], k2 = Kc[a][g + stride[a]];
+                T = 2.0 * ah[a] * k1 * k2 * rcp64(k1 + k2);
+            }
+            tp[a][c] = T;
+        }
+    }
+    __syncthreads();                                   // the high-side cells read their "-" faces
+    for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
+        int lc[3];
+        local_coords(s, c, lc);
+        const long long g = global_cell(s, lc, geo.n);
+        double d = 0.0, rd = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
             // +a side
             if (lc[a] + 1 < s.sz[a]) {
-                double T = geo.area[a] * harm(ka, Kc[a][g + stride[a]]) / geo.h[a];
-                tplus[a] = T;
-                d += T;
+                d += tp[a][c];
             } else if (s.o[a] + lc[a] == geo.n[a] - 1) {
-                if ((bc_lo_hi.y >> a) & 1) { double TD = geo.area[a] * 2.0 * ka / geo.h[a]; d += TD; rd += TD * bhi[a]; }
+                if ((bc_lo_hi.y >> a) & 1) { double TD = 2.0 * ah[a] * Kc[a][g]; d += TD; rd += TD * bhi[a]; }
             } else {
-                double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-                d += geo.area[a] / (geo.h[a] / (2.0 * ka) + beta);
+                const double ka = Kc[a][g];
+                const double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
+                d += geo.area[a] * rcp64(geo.h[a] / (2.0 * ka) + beta);
             }
             // -a side
             if (lc[a] > 0) {
-                d += geo.area[a] * harm(ka, Kc[a][g - stride[a]]) / geo.h[a];
+                d += tp[a][c - lstride[a]];
             } else if (s.o[a] == 0) {
-                if ((bc_lo_hi.x >> a) & 1) { double TD = geo.area[a] * 2.0 * ka / geo.h[a]; d += TD; rd += TD * blo[a]; }
+                if ((bc_lo_hi.x >> a) & 1) { double TD = 2.0 * ah[a] * Kc[a][g]; d += TD; rd += TD * blo[a]; }
             } else {
-                double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-                d += geo.area[a] / (geo.h[a] / (2.0 * ka) + beta);
+                const double ka = Kc[a][g];
+                const double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
+                d += geo.area[a] * rcp64(geo.h[a] / (2.0 * ka) + beta);
             }
         }
-        long long i = s.cell_off + c;
+        const long long i = s.cell_off + c;
         coef[i] = d;
-        coef[ncell_total + i] = tplus[s.ua];
-        coef[2 * ncell_total + i] = tplus[s.va];
-        coef[3 * ncell_total + i] = tplus[s.sa];
-        scale[i] = rsqrt(d);
+        scale[i] = f32_to_f64(rsqrtf(f64_to_f32_rz(d)));
         rhs_dir[i] = rd;
     }
     for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
@@ -130,6 +157,7 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
         face_tr[s.face_off + q] = tr;
         face_beta[s.face_off + q] = beta;
         face_u[s.face_off + q] = -beta * fi.s * tr;     // U-MBF right-hand side on this face
+        face_bst[s.face_off + q] = beta * fi.s * tr;     // weight of the face's flux in the U row
     }
 }
 
@@ -966,34 +994,6 @@ struct LocalArgs {
     int bar_off;          // shared-memory offset of the two mbarriers (after the largest layout)
 };
 
-// FP64 <-> FP32 conversions on the integer pipe.  On this GPU a conversion
-// instruction occupies the FP64 unit as long as an FMA does, and the local
-// solve is bound by that unit, so the refinement loop converts with bit
-// operations instead: FP64 -> FP32 truncates the significand (round toward
-// zero; the FP32 value only feeds the low-precision correction solve),
-// flushes magnitudes below the FP32 normal range to zero and saturates to
-// infinity above it; FP32 -> FP64 is exact for normal numbers (FP32
-// subnormals, which the correction never needs, become zero).
-__device__ __forceinline__ float f64_to_f32_rz(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-    unsigned int f;
-    if (e <= 0) f = sign;
-    else if (e >= 255) f = sign | 0x7F800000u;
-    else f = sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
-    return __uint_as_float(f);
-}
-__device__ __forceinline__ double f32_to_f64(float x) {
-    const unsigned int f = __float_as_uint(x);
-    const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
-    const int e = (int)((f >> 23) & 0xFF);
-    unsigned long long b;
-    if (e == 0) b = sign;
-    else if (e == 255) b = sign | 0x7FF0000000000000ull | ((unsigned long long)(f & 0x7FFFFFu) << 29);
-    else b = sign | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(f & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-}
 
 // Coupling between slab cells c and c+b in the solve's arithmetic: the FP32
 // scaled value t^ in mixed mode, the FP64 transmissibility otherwise.
@@ -1243,7 +1243,8 @@ __device__ __forceinline__ void drain_pipe(WPipe& pipe, unsigned long long* bar)
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
 __global__ void __launch_bounds__(NT, 1280 / NT)       // <= 51 (64 at 512 threads) registers per thread
 k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_ls[];
+    unsigned char* smem_raw = smem_ls;
     __shared__ int item;
     // mbarriers at the end of the largest layout (every subdomain's layout places them below)
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + g.bar_off);
@@ -1304,7 +1305,8 @@ const void* solve_kernel(int v) {
 __global__ void __launch_bounds__(kThreads)
 k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
           const double* __restrict__ face_tr, const double* __restrict__ face_beta,
-          const double* __restrict__ X, Geo geo, double* __restrict__ elem, double* __restrict__ elem_b) {
+          const double* __restrict__ face_bst, const double* __restrict__ X, Geo geo,
+          double* __restrict__ elem, double* __restrict__ elem_b) {
     const SubInfo s = subs[blockIdx.x];
     const int nI = s.nI, m = s.m, N = s.N, dim = s.el_dim;
     __shared__ int start[kMaxI + 1];                  // per-column face ranges
@@ -1316,20 +1318,33 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
     }
     __syncthreads();
     const double* Xs = X + s.x_off;
+    // The faces of basis k all carry column k; the Robin data g of MBF column j
+    // on them is 1 (j = k, P-MBF), -beta s (j = nI + k, U-MBF) or 0, so the
+    // traces are sum T_R x and sum beta s T_R x plus a correction on those two
+    // columns: two FMAs per face and column.
     for (int e = threadIdx.x; e < nI * m; e += blockDim.x) {
         int k = e / m, j = e - (e / m) * m;
         int q0 = start[k], q1 = start[k + 1];
-        double sf = 0.0, su = 0.0, sdiag = 0.0;
+        const double* x = Xs + (long long)j * N;
+        double sf = 0.0, su = 0.0;
         for (int q = q0; q < q1; ++q) {
-            FaceInfo fi = faces[s.face_off + q];
-            double tr = face_tr[s.face_off + q], be = face_beta[s.face_off + q];
-            double g = 0.0;
-            if (j == fi.col) g = 1.0;
-            else if (j == nI + fi.col) g = -be * fi.s;
-            double qf = tr * (Xs[(long long)j * N + fi.cell] - g);
-            sf += qf;
-            su += be * fi.s * qf;
-            sdiag += be * geo.area[fi.axis];
+            const double xv = x[faces[s.face_off + q].cell];
+            sf = fma(face_tr[s.face_off + q], xv, sf);
+            su = fma(face_bst[s.face_off + q], xv, su);
+        }
+        double sdiag = 0.0;
+        if (j == k || j == nI + k) {
+            for (int q = q0; q < q1; ++q) {
+                const FaceInfo fi = faces[s.face_off + q];
+                const double tr = face_tr[s.face_off + q], bst = face_bst[s.face_off + q];
+                const double be = face_beta[s.face_off + q];
+                if (j == k) { sf -= tr; su -= bst; }                    // g = 1
+                else {                                                  // g = -beta s
+                    sf += bst;
+                    su += bst * be * fi.s;
+                    sdiag += be * geo.area[fi.axis];
+                }
+            }
         }
         if (j < dim) {
             elem[s.el_off + (long long)k * dim + j] = sf;
@@ -1423,7 +1438,8 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
     MRCM_LAUNCH(P, "k_coefficients", st, k_coefficients<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, K, make_geo(c), c.beta_mode, c.alpha,
                                              c.beta_const, bcm, blo, bhi, coef, scale,
                                              (double*)(ws + L.rhs_part), (double*)(ws + L.face_tr),
-                                             (double*)(ws + L.face_beta), (double*)(ws + L.face_u), t.n_cells));
+                                             (double*)(ws + L.face_beta), (double*)(ws + L.face_u),
+                                             (double*)(ws + L.face_bst), t.n_cells));
     if (t.n_waves == 1) launch_factor_wave(t, d, L, ws, precision, 0, st, P);
     return (int)cudaGetLastError();
 }
@@ -1522,6 +1538,7 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     }
     MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 0 : sweeps));
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
+                                        (const double*)(ws + L.face_bst),
                                         (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
     return (int)cudaGetLastError();
 }

@@ -19,6 +19,7 @@ constexpr int kMaxCells = 4096;
 struct Geo2 {
     double h[3];
     double area[3];
+    double inv_area[3];          // 1 / area: no FP64 divisions per face
     int n[3];
     int dir_lo, dir_hi;          // Dirichlet wall masks
     double glo[3], ghi[3];
@@ -89,9 +90,9 @@ k_reconstruct(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fac
             double* ulo = u + (long long)(2 * a) * ncells;
             double* uhi = u + (long long)(2 * a + 1) * ncells;
             const double ka = K[(long long)a * ncells + g];
-            if (has_hi) uhi[g] = tp[c] * (pl[c] - pl[c + off]) / geo.area[a];
+            if (has_hi) uhi[g] = tp[c] * (pl[c] - pl[c + off]) * geo.inv_area[a];
             else if (wall_hi) uhi[g] = ((geo.dir_hi >> a) & 1) ? -2.0 * ka * (geo.ghi[a] - pl[c]) / geo.h[a] : 0.0;
-            if (has_lo) ulo[g] = tp[c - off] * (pl[c - off] - pl[c]) / geo.area[a];
+            if (has_lo) ulo[g] = tp[c - off] * (pl[c - off] - pl[c]) * geo.inv_area[a];
             else if (wall_lo) ulo[g] = ((geo.dir_lo >> a) & 1) ? -2.0 * ka * (pl[c] - geo.glo[a]) / geo.h[a] : 0.0;
             (void)strideg;
         }
@@ -107,8 +108,8 @@ k_reconstruct(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fac
         lcoords(s, fi.cell, lc);
         long long g = (s.o[0] + lc[0]) + geo.n[0] * ((long long)(s.o[1] + lc[1]) + (long long)geo.n[1] * (s.o[2] + lc[2]));
         int a = fi.axis;
-        if (fi.s > 0) u[(long long)(2 * a + 1) * ncells + g] = qo / geo.area[a];
-        else u[(long long)(2 * a) * ncells + g] = -qo / geo.area[a];
+        if (fi.s > 0) u[(long long)(2 * a + 1) * ncells + g] = qo * geo.inv_area[a];
+        else u[(long long)(2 * a) * ncells + g] = -qo * geo.inv_area[a];
     }
     __syncthreads();
     // mass balance of every cell of this subdomain
@@ -180,6 +181,7 @@ int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, 
     Geo2 geo;
     geo.h[0] = c.hx; geo.h[1] = c.hy; geo.h[2] = c.hz;
     geo.area[0] = c.hy * c.hz; geo.area[1] = c.hx * c.hz; geo.area[2] = c.hx * c.hy;
+    for (int a = 0; a < 3; ++a) geo.inv_area[a] = 1.0 / geo.area[a];
     geo.n[0] = c.nx; geo.n[1] = c.ny; geo.n[2] = c.nz;
     geo.dir_lo = geo.dir_hi = 0;
     for (int a = 0; a < 3; ++a) {

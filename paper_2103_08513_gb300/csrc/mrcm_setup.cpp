@@ -415,6 +415,7 @@ void compute_layout(const Tables& t, Layout& L) {
     L.face_tr = take(t.faces.size() * sizeof(double));
     L.face_beta = take(t.faces.size() * sizeof(double));
     L.face_u = take(t.faces.size() * sizeof(double));
+    L.face_bst = take(t.faces.size() * sizeof(double));
     L.W = take((size_t)t.total_w * (t.cfg.precision == MRCM_FP64 ? sizeof(double) : sizeof(float)));
     L.X = take((size_t)t.total_x * sizeof(double));
     L.R = take(t.cfg.precision == MRCM_FP64 ? (size_t)t.total_x * sizeof(double) : (size_t)t.total_x * sizeof(float));
