@@ -183,7 +183,7 @@ constexpr size_t kSolveSmemBudget = 220 * 1024;   // dynamic shared memory per C
 constexpr size_t kSolveTwoCta = 113 * 1024;       // two CTAs per SM fit below this
 
 struct SolveSmem {
-    size_t w, z, yp, nrm, cols, cf, total;
+    size_t w, z, yp, nrm, cols, cf, co, total;
     int nbuf;
 };
 
@@ -200,6 +200,7 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     rest += sizeof(double) * mpad + sizeof(int) * mpad;    // nrm, cols
     rest += sizeof(short) * 6 * (size_t)N;                 // cf
     rest = (rest + 15) & ~size_t(15);
+    rest += 5 * sizeof(double) * (size_t)b;                // one slab's stencil coefficients
     rest += 16;                                            // mbarriers (after the largest layout)
     L.nbuf = (2 * wb + rest + 128 <= kSolveTwoCta) ? 2 : (wb + rest + 128 <= kSolveSmemBudget ? 1 : 0);
     size_t x = 0;
@@ -216,6 +217,9 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     x += sizeof(int) * mpad;
     L.cf = x;
     x += sizeof(short) * 6 * (size_t)N;
+    x = (x + 15) & ~size_t(15);
+    L.co = x;
+    x += 5 * sizeof(double) * (size_t)b;
     L.total = (x + 127) & ~size_t(127);
     return L;
 }

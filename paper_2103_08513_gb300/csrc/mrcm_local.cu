@@ -1120,9 +1120,27 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         }
     };
 
+    // one slab's stencil coefficients, staged per slab for the refinement residual:
+    // diagonal, +u, +v, +slab and -slab transmissibilities
+    double* co_d = reinterpret_cast<double*>(smem_raw + lay.co);
+    double* co_u = co_d + b;
+    double* co_v = co_u + b;
+    double* co_sp = co_v + b;
+    double* co_sm = co_sp + b;
     // ---- forward sweep
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
+        if constexpr (kSweep) {
+            for (int i = threadIdx.x; i < b; i += blockDim.x) {
+                const int c = base + i;
+                co_d[i] = cd[c];
+                co_u[i] = cu[c];
+                co_v[i] = cv[c];
+                co_sp[i] = c + b < N ? cs[c] : 0.0;
+                co_sm[i] = c >= b ? cs[c - b] : 0.0;
+            }
+            __syncthreads();
+        }
         // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
         for (int jj = ty; jj < na; jj += NY) {
             const int j = cols[jj];
@@ -1151,13 +1169,13 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                 }
                 if (kSweep) {                     // r - A x as one FMA chain
                     const int u = i % su;
-                    r = fma(-cd[c], x[c], r);
-                    if (u + 1 < su) r = fma(cu[c], x[c + 1], r);
-                    if (u > 0) r = fma(cu[c - 1], x[c - 1], r);
-                    if (i + su < b) r = fma(cv[c], x[c + su], r);
-                    if (i >= su) r = fma(cv[c - su], x[c - su], r);
-                    if (c + b < N) r = fma(cs[c], x[c + b], r);
-                    if (c >= b) r = fma(cs[c - b], x[c - b], r);
+                    r = fma(-co_d[i], x[c], r);
+                    if (u + 1 < su) r = fma(co_u[i], x[c + 1], r);
+                    if (u > 0) r = fma(co_u[i - 1], x[c - 1], r);
+                    if (i + su < b) r = fma(co_v[i], x[c + su], r);
+                    if (i >= su) r = fma(co_v[i - su], x[c - su], r);
+                    if (c + b < N) r = fma(co_sp[i], x[c + b], r);
+                    if (c >= b) r = fma(co_sm[i], x[c - b], r);
                 }
                 const float rf = f64_to_f32_rz(r);
                 const float rn = rf * rscale;
