@@ -695,6 +695,159 @@ k_block_factor_tc(const SubInfo* __restrict__ subs, const int* __restrict__ list
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem));
 }
 
+// ---------------------------------------------------------------------------
+// Register-tiled variant for 128 < b <= 256 (FP32, scaled): the block is held
+// as 8 x 8 tiles of its lower triangle, one tile per thread (at most 32 x 33 /
+// 2 = 528 tiles; diagonal tiles keep their full 8 x 8 block).  Pivot k needs
+// the row M[k][:] of the sign-symmetric matrix: the threads of tile row k/8
+// publish M[k][x] for x in or left of the diagonal tile, the threads of tile
+// column k/8 publish M[x][k] = M[k][x] (both unswept) for x below it.  Column
+// k is read back as M[i][k] = sigma_i M[k][i].  Each thread then applies the
+// same sweep-operator step to its tile; W_s is written as a full matrix.
+// ---------------------------------------------------------------------------
+constexpr int kTriB = 256;                 // largest block
+
+// CTA size of the triangle factor for a b x b block: whole warps covering the
+// nt (nt + 1) / 2 tiles; 0 = beyond kTriB (packed kernel)
+static int tri_threads(int b) {
+    const int nt = (b + 7) / 8, T = nt * (nt + 1) / 2;
+    return b > kTriB ? 0 : T <= 192 ? 192 : T <= 320 ? 320 : T <= 512 ? 512 : 544;
+}
+
+// NTH threads: 192 cover b <= 144, 320 b <= 192, 512 b <= 248 (496 tiles),
+// all within 128 registers; 544 cover b <= 256 (528 tiles) but then have to
+// live with 96 registers (5 warps on one SM sub-partition).
+template <int NTH>
+__global__ void __launch_bounds__(NTH, NTH <= 192 ? 2 : 1)
+k_block_factor_tri(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
+                   const double* __restrict__ scale, float* __restrict__ Wall, int* __restrict__ status,
+                   long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
+    const SubInfo s = subs[list[blockIdx.x]];
+    const int b = s.b, su = s.su;
+    const int nt = (b + 7) >> 3;
+    const int T = nt * (nt + 1) / 2;
+    const int t = threadIdx.x;
+    const bool own = t < T;
+    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    int tj = t - ti * (ti + 1) / 2;
+    if (!own) ti = tj = 0;                                 // idle threads shadow tile (0, 0), never publish or store
+    const int i0 = ti * 8, j0 = tj * 8;
+    const bool diag = ti == tj;
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* sc = scale + s.cell_off;
+    float* W = Wall + s.w_off;
+    __shared__ __align__(16) float prow[2][kTriB];
+    __shared__ __align__(16) float sd[kTriB], sup[kTriB], svp[kTriB], st[kTriB];
+    float a[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[r][c] = 0.0f;
+    int bad = 0;
+    for (int sl = 0; sl < s.ns; ++sl) {
+        const int base = sl * b;
+        for (int i = t; i < kTriB; i += NTH) {
+            float d = 0.f, u = 0.f, v = 0.f, tt = 0.f;
+            if (i < b) {
+                const int c = base + i;
+                d = (float)(cd[c] * sc[c] * sc[c]);
+                if ((i % su) + 1 < su) u = (float)(-cu[c] * sc[c] * sc[c + 1]);
+                if (i + su < b) v = (float)(-cv[c] * sc[c] * sc[c + su]);
+                if (sl > 0) tt = (float)(cs[c - b] * sc[c - b] * sc[c]);
+                scf_all[s.cell_off + c] = (float)sc[c];
+                tsc_all[s.cell_off + c] = sl + 1 < s.ns ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+            }
+            sd[i] = d; sup[i] = u; svp[i] = v; st[i] = tt;
+        }
+        __syncthreads();
+        // S_s = D_s - t o W_{s-1} o t on the tile
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = i0 + r;
+            const float tiv = st[min(i, kTriB - 1)];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + c;
+                float v = -tiv * st[min(j, kTriB - 1)] * a[r][c];
+                if (j == i) v += sd[i];
+                if (j == i + 1) v += sup[i];
+                if (j + 1 == i) v += sup[j];
+                if (j == i + su) v += svp[i];
+                if (j + su == i) v += svp[j];
+                a[r][c] = (own && i < b && j < b) ? v : (own && i == j) ? 1.0f : 0.0f;
+            }
+        }
+        // The block is padded to 8 nt with identity pivots, which leave the
+        // rest untouched.  Pivots k = 8 kt + kr with kr unrolled, so that row kr and column kr
+        // of a tile are fixed registers.  Column k rides on the rank-1 update
+        // (zeroed, row factor 1 / p: -M[i][k] / p, and 1 / p at (k, k)); row k
+        // takes M[k][j] / p directly.
+#pragma unroll 1
+        for (int kt = 0; kt < nt; ++kt) {
+            const bool rowt = own && ti == kt, colt = own && tj == kt;
+#pragma unroll
+            for (int kr = 0; kr < 8; ++kr) {
+                const int k = kt * 8 + kr;
+                float* pr = prow[kr & 1];
+                if (rowt) {                                     // M[k][x], x in tiles (kt, tj <= kt)
+                    reinterpret_cast<float4*>(pr + j0)[0] = make_float4(a[kr][0], a[kr][1], a[kr][2], a[kr][3]);
+                    reinterpret_cast<float4*>(pr + j0)[1] = make_float4(a[kr][4], a[kr][5], a[kr][6], a[kr][7]);
+                }
+                if (colt && ti > kt) {                          // M[x][k] = M[k][x] for x below the diagonal tile
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) pr[i0 + r] = a[r][kr];
+                }
+                __syncthreads();
+                float p = pr[k];
+                if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+                const float ip = 1.0f / p;
+                const float4 q0 = reinterpret_cast<const float4*>(pr + j0)[0], q1 = reinterpret_cast<const float4*>(pr + j0)[1];
+                float rkv[8] = {q0.x * ip, q0.y * ip, q0.z * ip, q0.w * ip, q1.x * ip, q1.y * ip, q1.z * ip, q1.w * ip};
+                if (colt) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) a[r][kr] = 0.0f;
+                    rkv[kr] = ip;
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    float ckr = pr[i0 + r];
+                    if (i0 + r < k) ckr = -ckr;                   // M[i][k] = sigma_i M[k][i]
+                    if (r == kr && rowt) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) a[r][c] = rkv[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-ckr, rkv[c], a[r][c]);
+                    }
+                }
+            }
+        }
+        // W_s as a full matrix: the tile and, below the diagonal, its transpose
+        float* Ws = W + (long long)sl * wstride<float>(b);
+        if (own) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int i = i0 + r;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int j = j0 + c;
+                    if (i < b && j < b) {
+                        Ws[(long long)i * b + j] = a[r][c];
+                        if (!diag) Ws[(long long)j * b + i] = a[r][c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicAdd(&status[ST_NOT_SPD], 1);
+}
+
 template <int TPT, int G>
 __global__ void __launch_bounds__(G * G, G == 16 ? 2 : 8)
 k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
@@ -1429,10 +1582,28 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
                 MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tile<8, 16><<<n_mid, 256, 0, st>>>(d.subs, d.class_list + o1, coef, scale,
                     (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
         }
-        if (n_large > 0) {
-            size_t sm = factor_smem<float>(t.max_b);
-            MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
-                (float*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+        // the large class is ordered by b, largest first: one launch per run of
+        // subdomains that share a thread count (packed kernel above kTriB)
+        for (int q = o2; q < o3;) {
+            const int nth = tri_threads(t.subs[t.class_list[q]].b);
+            int e = q + 1;
+            while (e < o3 && tri_threads(t.subs[t.class_list[e]].b) == nth) ++e;
+            const int n = e - q;
+            const int* lst = d.class_list + q;
+            float* W = (float*)(ws + L.W);
+            float* scf = (float*)(ws + L.scf);
+            float* tsc = (float*)(ws + L.tsc);
+            switch (nth) {
+            case 192: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<192><<<n, 192, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
+            case 320: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<320><<<n, 320, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
+            case 512: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<512><<<n, 512, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
+            case 544: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<544><<<n, 544, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
+            default: {
+                size_t sm = factor_smem<float>(t.max_b);
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n, kThreads, sm, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc));
+            }
+            }
+            q = e;
         }
     }
 }

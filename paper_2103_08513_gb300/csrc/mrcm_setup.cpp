@@ -271,18 +271,20 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         t.total_w = wmax;
         t.class_list.clear();
         for (int w = 0; w < t.n_waves; ++w) {
-            std::vector<std::pair<double, int>> cls[3];
+            std::vector<std::tuple<int, double, int>> cls[3];
             for (int q = t.wave_off[w]; q < t.wave_off[w + 1]; ++q) {
                 const int l = t.solve_list[q];
                 const SubInfo& s = t.subs[l];
                 const double cost = (double)s.ns * s.b * s.b * s.b;
                 const int k = cfg->precision == MRCM_FP64 ? 2 : s.b <= kRegBlock ? 0 : s.b <= kTileBlock ? 1 : 2;
-                cls[k].push_back({-cost, l});
+                // mixed large class: ordered by b first (its factor launches
+                // one CTA size per run of b), then by cost
+                cls[k].push_back({k == 2 && cfg->precision != MRCM_FP64 ? -s.b : 0, -cost, l});
             }
             for (int k = 0; k < 3; ++k) {
                 std::sort(cls[k].begin(), cls[k].end());
                 t.wave_class_off.push_back((int)t.class_list.size());
-                for (auto& pr : cls[k]) t.class_list.push_back(pr.second);
+                for (auto& e : cls[k]) t.class_list.push_back(std::get<2>(e));
             }
             t.wave_class_off.push_back((int)t.class_list.size());
         }

@@ -97,6 +97,9 @@ UNEVEN = {
     # 16 x 16 x 8 subdomains with whole-face patches (b = 128, register-tiled factor), high contrast
     "blocks_128": dict(n=(32, 16, 16), edges=([16, 16], [16], [8, 8]), patch=((0, 0), (0, 0), (0, 0)),
                        sigma=3.0, lam=8.0),
+    # b = 11 x 13 = 143 and 13 x 13 = 169: large blocks that are not whole 8 x 8 tiles
+    "odd_large": dict(n=(24, 13, 13), edges=([11, 13], [13], [13]), patch=((0, 0), (0, 0), (0, 0)),
+                      sigma=1.5, lam=4.0),
 }
 
 
