@@ -583,29 +583,42 @@ k_front_forward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ 
 }
 
 // Backward substitution, boundary columns: w_E = D^{-1} y_E - L_BE^T x_B, with
-// x_B (scaled) from the ancestors.  32 columns x 8 row groups per CTA.
+// x_B (scaled) from the ancestors, gathered once into shared memory.  32
+// columns x 8 row groups per CTA, four partial sums per thread.
 __global__ void __launch_bounds__(kThreads)
 k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const int* __restrict__ dofs,
                    const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* xb = reinterpret_cast<double*>(smem_raw);
     const FrontInfo fr = fronts[ids[blockIdx.y]];
-    const int n = fr.n, ne = fr.ne;
+    const int n = fr.n, ne = fr.ne, nb = n - ne;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     if (blockIdx.x * 32 >= ne) return;
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) xb[q] = xs[fd[ne + q]];
     __shared__ double part[kThreads / 32][32];
-    double v = 0.0;
+    __syncthreads();
+    constexpr int G = kThreads / 32;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     if (i < ne) {
-#pragma unroll 4
-        for (int j = ne + g; j < n; j += kThreads / 32) v = fma(A[(long long)j * n + i], xs[fd[j]], v);
+        const double* col = A + (long long)ne * n + i;
+        int q = g;
+        for (; q + 3 * G < nb; q += 4 * G) {
+            v0 = fma(col[(long long)q * n], xb[q], v0);
+            v1 = fma(col[(long long)(q + G) * n], xb[q + G], v1);
+            v2 = fma(col[(long long)(q + 2 * G) * n], xb[q + 2 * G], v2);
+            v3 = fma(col[(long long)(q + 3 * G) * n], xb[q + 3 * G], v3);
+        }
+        for (; q < nb; q += G) v0 = fma(col[(long long)q * n], xb[q], v0);
     }
-    part[g][lane] = v;
+    part[g][lane] = (v0 + v1) + (v2 + v3);
     __syncthreads();
     if (g == 0 && i < ne) {
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) s += part[q][lane];
+        for (int q = 0; q < G; ++q) s += part[q][lane];
         double* z = frhs + fr.r_off;
         z[i] = z[i] / A[(long long)i * n + i] - s;
     }
@@ -762,7 +775,7 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
-        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, 0, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
+        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
         MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, Pv,
                                                    frhs, xs));
     }
@@ -773,6 +786,7 @@ int configure_interface(const Tables& t, DeviceTables& d) {
     if (d.front_smem > 48 * 1024) {
         cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
         cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+        cudaFuncSetAttribute(k_front_backward_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
     }
     return (int)cudaGetLastError();
 }

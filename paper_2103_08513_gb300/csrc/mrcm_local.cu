@@ -905,60 +905,54 @@ k_block_factor_tile(const SubInfo* __restrict__ subs, const int* __restrict__ li
                 if (j + 1 == i) v += sup[j];
                 if (j == i + su) v += svp[i];
                 if (j + su == i) v += svp[j];
-                a[r][c] = (i < b && j < b) ? v : 0.0f;
+                a[r][c] = (i < b && j < b) ? v : i == j ? 1.0f : 0.0f;
             }
         }
-        // Gauss-Jordan sweep over the b pivots
+        // Gauss-Jordan sweep over the b pivots, padded to whole tiles with
+        // identity pivots; k = TPT kt + kr with kr unrolled, so that row and
+        // column kr of the tile are fixed registers.  Column k rides on the
+        // rank-1 update (zeroed, row factor 1 / p); row k takes M[k][j] / p.
+        const int ntl = (b + TPT - 1) / TPT;
 #pragma unroll 1
-        for (int k = 0; k < b; ++k) {
-            float* pr = prow[k & 1];
-            if (ty == k / TPT) {
-                const int rk = k % TPT;
+        for (int kt = 0; kt < ntl; ++kt) {
+            const bool rowt = ty == kt, colt = tx == kt;
 #pragma unroll
-                for (int r = 0; r < TPT; ++r)
-                    if (r == rk) {
+            for (int kr = 0; kr < TPT; ++kr) {
+                const int k = kt * TPT + kr;
+                float* pr = prow[kr & 1];
+                if (rowt) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q)
-                            reinterpret_cast<float4*>(pr + j0)[q] =
-                                make_float4(a[r][4 * q], a[r][4 * q + 1], a[r][4 * q + 2], a[r][4 * q + 3]);
-                    }
-            }
-            __syncthreads();
-            float p = pr[k];
-            if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
-            const float ip = 1.0f / p;
-            float rkv[TPT], ck[TPT];
+                    for (int q = 0; q < NV; ++q)
+                        reinterpret_cast<float4*>(pr + j0)[q] =
+                            make_float4(a[kr][4 * q], a[kr][4 * q + 1], a[kr][4 * q + 2], a[kr][4 * q + 3]);
+                }
+                __syncthreads();
+                float p = pr[k];
+                if (!(p > 0.0f)) { bad = 1; p = 1.0f; }
+                const float ip = 1.0f / p;
+                float rkv[TPT];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const float4 qv = reinterpret_cast<const float4*>(pr + j0)[q];
-                const float4 cv4 = reinterpret_cast<const float4*>(pr + i0)[q];
-                rkv[4 * q] = qv.x * ip; rkv[4 * q + 1] = qv.y * ip; rkv[4 * q + 2] = qv.z * ip; rkv[4 * q + 3] = qv.w * ip;
-                ck[4 * q] = cv4.x; ck[4 * q + 1] = cv4.y; ck[4 * q + 2] = cv4.z; ck[4 * q + 3] = cv4.w;
-            }
+                for (int q = 0; q < NV; ++q) {
+                    const float4 qv = reinterpret_cast<const float4*>(pr + j0)[q];
+                    rkv[4 * q] = qv.x * ip; rkv[4 * q + 1] = qv.y * ip; rkv[4 * q + 2] = qv.z * ip; rkv[4 * q + 3] = qv.w * ip;
+                }
+                if (colt) {
 #pragma unroll
-            for (int r = 0; r < TPT; ++r)
-                if (i0 + r < k) ck[r] = -ck[r];                   // M[i][k] = sigma_i M[k][i]
+                    for (int r = 0; r < TPT; ++r) a[r][kr] = 0.0f;
+                    rkv[kr] = ip;
+                }
 #pragma unroll
-            for (int r = 0; r < TPT; ++r)
-#pragma unroll
-                for (int c = 0; c < TPT; ++c) a[r][c] = fmaf(-ck[r], rkv[c], a[r][c]);
-            if (ty == k / TPT) {                                  // row k: M[k][j] / p
-                const int rk = k % TPT;
-#pragma unroll
-                for (int r = 0; r < TPT; ++r)
-                    if (r == rk) {
+                for (int r = 0; r < TPT; ++r) {
+                    float ckr = pr[i0 + r];
+                    if (i0 + r < k) ckr = -ckr;                   // M[i][k] = sigma_i M[k][i]
+                    if (r == kr && rowt) {
 #pragma unroll
                         for (int c = 0; c < TPT; ++c) a[r][c] = rkv[c];
-                    }
-            }
-            if (tx == k / TPT) {                                  // column k: -M[i][k] / p, (k, k): 1 / p
-                const int ckc = k % TPT;
+                    } else {
 #pragma unroll
-                for (int c = 0; c < TPT; ++c)
-                    if (c == ckc) {
-#pragma unroll
-                        for (int r = 0; r < TPT; ++r) a[r][c] = (i0 + r == k) ? ip : -ck[r] * ip;
+                        for (int c = 0; c < TPT; ++c) a[r][c] = fmaf(-ckr, rkv[c], a[r][c]);
                     }
+                }
             }
         }
         // store W_s (full symmetric matrix, row major)
