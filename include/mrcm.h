@@ -138,6 +138,8 @@ typedef struct {
     double ldl_flops;           /* flops of the interface LDL^T (lower triangle) */
     double ldl_update_flops;    /* part of ldl_flops in the trailing (Schur) updates */
     int n_waves;                /* memory-bounded waves of the local phase */
+    int max_front_ne;           /* largest eliminated block of a front (its substitutions
+                                   run on a cluster of CTAs from 128 on) */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;

@@ -78,19 +78,18 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // w_c = V[k][c] / d_k on the V part (c <= k), every row i > k takes
 //   T[i][c] -= T[i][k] w_c   (k < c <= i, and all c <= k of V),
 // the rank-1 Schur update of the block and V <- (I - l e_k^T) V at once (row k
-// of V is final at step k), and l_i = T[i][k] / d_k goes to a separate column
-// store, so column k stays readable during the step: one barrier per pivot.
-// One lane per column: a row costs one FP64 FMA per step.  Warp 0 updates
-// row k + 1 alone and then computes 1 / d_{k+1} (Newton iteration), while
+// of V is final at step k).  Block column k is not written after step k - 1,
+// so L = T[i][k] / d_k is formed once at the end: one barrier per pivot.  One
+// lane per column: a row costs one FP64 FMA per step.  Warp 0 updates row
+// k + 1 alone and then computes 1 / d_{k+1} (one cubic Newton step), while
 // warps 1.. update the other rows.  A zero or NaN pivot is replaced by 1 and
 // counted.  Block-wide, >= 2 warps.
 constexpr int kDiagW = 2 * kPanel + 1;
-constexpr int kDiagWork = kPanel * kDiagW + kPanel * (kPanel + 1) + kPanel + 4;   // doubles of shared work space
+constexpr int kDiagWork = kPanel * kDiagW + kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
                                   int* status, double* work) {
     double (*T)[kDiagW] = reinterpret_cast<double (*)[kDiagW]>(work);
-    double (*Lc)[kPanel + 1] = reinterpret_cast<double (*)[kPanel + 1]>(work + kPanel * kDiagW);
-    double* sinv = work + kPanel * kDiagW + kPanel * (kPanel + 1);      // 1 / d_k for every k
+    double* sinv = work + kPanel * kDiagW;                    // 1 / d_k for every k
     int* zero = reinterpret_cast<int*>(sinv + kPanel);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
     __syncthreads();                                          // the block's last writes are complete
@@ -106,7 +105,7 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
         *zero = 0;
         double d = T[0][0];
         if (d == 0.0 || d != d) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
-        sinv[0] = rcp64(d);
+        sinv[0] = rcp64c(d);
     }
     for (int k = 0; k < nbk; ++k) {
         __syncthreads();                                      // rows of step k - 1 done, 1 / d_k ready
@@ -126,10 +125,9 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
                 if (lane == 0) {
                     double d = T[i][i];
                     if (d == 0.0 || d != d) { d = 1.0; T[i][i] = 1.0; *zero = 1; }
-                    sinv[i] = rcp64(d);
+                    sinv[i] = rcp64c(d);
                 }
             }
-            if (lane > k && lane < nbk) Lc[lane][k] = T[lane][k] * inv;   // column k of L
         } else {
             for (int i = k + 1 + w; i < nbk; i += nw - 1) {
                 if (c <= i) {
@@ -142,7 +140,7 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
     __syncthreads();
     for (int e = tid; e < kPanel * kPanel; e += nthr) {
         const int i = e >> 5, c = e & 31;
-        if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = c == i ? T[i][i] : Lc[i][c];
+        if (i < nbk && c <= i) A[(long long)(k0 + i) * n + k0 + c] = c == i ? T[i][i] : T[i][c] * sinv[c];
         Pinv[e] = T[i][kPanel + c];
     }
     if (tid == 0 && *zero) atomicAdd(&status[ST_ZERO_PIVOT], 1);
@@ -216,7 +214,7 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
     }
 }
 
-constexpr int kPanelRows = 8;           // warp passes per panel-kernel CTA
+constexpr int kPanelRows = 4;           // warp passes per panel-kernel CTA (one per warp)
 
 // Tensor-core emulation of the FP64 trailing update (Ozaki-type splitting
 // with exact integer arithmetic).  For each panel row x (of L21 D for the left
@@ -315,12 +313,16 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
         const bool live = r < r_end && j < nbk;
         double* row = A + (long long)r * n + k0;
         const double a = live ? row[j] : 0.0;
-        double acc = 0.0;
-        for (int k = 0; k < nbk; ++k) {
-            const double ak = __shfl_sync(0xffffffffu, a, rs * W + k);
-            acc = fma(ak, Vs[j][k], acc);                        // V[j][k] = 0 for k > j
+        double acc0 = 0.0, acc1 = 0.0;                            // two chains of FP64 FMAs
+        int k = 0;
+        for (; k + 1 < nbk; k += 2) {
+            const double ak0 = __shfl_sync(0xffffffffu, a, rs * W + k);
+            const double ak1 = __shfl_sync(0xffffffffu, a, rs * W + k + 1);
+            acc0 = fma(ak0, Vs[j][k], acc0);                     // V[j][k] = 0 for k > j
+            acc1 = fma(ak1, Vs[j][k + 1], acc1);
         }
-        const double l = live ? acc * Dinv[j] : 0.0;
+        if (k < nbk) acc0 = fma(__shfl_sync(0xffffffffu, a, rs * W + k), Vs[j][k], acc0);
+        const double l = live ? (acc0 + acc1) * Dinv[j] : 0.0;
         if (live) row[j] = l;
         if (oz_on) {                                              // all lanes: segment reductions inside
             const long long sr = (long long)fr.s_off + min(r, r_end - 1);
@@ -669,6 +671,178 @@ k_front_backward(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
     for (int i = threadIdx.x; i < ne; i += blockDim.x) xs[fd[i]] = w[i];
 }
 
+// ---------------------------------------------------------------------------
+// Cluster variants of the two eliminated-part substitutions for large fronts:
+// kSolveCl CTAs (one thread-block cluster) share a front.  Panel p belongs to
+// CTA p mod kSolveCl, which keeps the rows (forward) or entries (backward) of
+// its panels.  Per panel the owner solves the 32 x 32 diagonal system in one
+// warp, writes the result into every CTA's shared memory (distributed shared
+// memory), and a cluster barrier releases it; every CTA then applies it to its
+// own later (forward) or earlier (backward) panels.  The FP64 updates, which
+// bind a single SM, are spread over the cluster; the only waits are the
+// hardware cluster barrier.
+// ---------------------------------------------------------------------------
+constexpr int kSolveCl = 8;
+constexpr int kSolveClMinNe = 4 * kPanel;    // fronts with fewer E dofs keep one CTA
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// store v at the same shared-memory offset as `local` in CTA `rank` of the cluster
+__device__ __forceinline__ void st_cluster(double* local, unsigned rank, double v) {
+    unsigned la = (unsigned)__cvta_generic_to_shared(local), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(ra), "d"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_front_forward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
+                   const int* __restrict__ maps, const int* __restrict__ dofs,
+                   const double* __restrict__ F, const double* __restrict__ P, const double* __restrict__ bglob,
+                   const double* __restrict__ dscale, int NV, double* __restrict__ frhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* r = reinterpret_cast<double*>(smem_raw);
+    __shared__ double Vs[kPanel][kPanel + 1];
+    __shared__ double ybuf[2][kPanel];
+    const unsigned q = cluster_rank();
+    const FrontInfo fr = fronts[ids[blockIdx.x / kSolveCl]];
+    const int n = fr.n, ne = fr.ne;
+    const double* A = F + fr.f_off;
+    const int* fd = dofs + fr.e_dof_off;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = 0.0;
+        if (i < ne) { int d = fd[i]; v = dof_sign(d, NV) * dscale[d] * bglob[d]; }
+        r[i] = v;
+    }
+    __syncthreads();
+    for (int ci = 0; ci < 2; ++ci) {
+        const int c = fr.child[ci];
+        if (c < 0) continue;
+        const FrontInfo cf = fronts[c];
+        const int* mp = maps + fr.map_off[ci];
+        for (int i = threadIdx.x; i < cf.nb; i += blockDim.x) r[mp[i]] += frhs[cf.r_off + cf.ne + i];
+        __syncthreads();
+    }
+    cluster_sync_all();                                     // every CTA of the cluster is running
+    const int np = (ne + kPanel - 1) / kPanel;
+    for (int p = 0; p < np; ++p) {
+        const int k0 = p * kPanel, nbk = min(kPanel, ne - k0);
+        double* yb = ybuf[p & 1];
+        if ((unsigned)(p % kSolveCl) == q) {                // owner: y_p = V_p r_p, sent to the cluster
+            const double* V = P + (long long)(fr.p_off + p) * kPanel * kPanel;
+            for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
+            __syncthreads();
+            if (w == 0) {
+                const double rk = lane < nbk ? r[k0 + lane] : 0.0;
+                double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < kPanel; k += 2) {
+                    y0 = fma(Vs[lane][k], __shfl_sync(0xffffffffu, rk, k), y0);
+                    y1 = fma(Vs[lane][k + 1], __shfl_sync(0xffffffffu, rk, k + 1), y1);
+                }
+                const double y = y0 + y1;
+                if (lane < nbk) r[k0 + lane] = y;
+#pragma unroll 1
+                for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&yb[lane], t, y);
+            }
+        }
+        cluster_sync_all();                                 // y_p in every CTA
+        // own rows of the later panels: r_i -= L[i][k0 .. k0 + nbk) y_p
+        // (the first own panel after p, then every kSolveCl-th; thread group
+        // threadIdx.x / 32 takes every (kThreads / 32)-th of them, a lane per row)
+        const int p1 = p + 1 + (int)((q + kSolveCl - (unsigned)((p + 1) % kSolveCl)) % kSolveCl);
+        for (int pp = p1 + kSolveCl * (threadIdx.x / kPanel); pp < np; pp += kSolveCl * (kThreads / kPanel)) {
+            const int i = pp * kPanel + threadIdx.x % kPanel;
+            if (i >= ne) continue;
+            const double* row = A + (long long)i * n + k0;
+            double v0 = 0.0, v1 = 0.0;
+            if (nbk == kPanel) {
+#pragma unroll
+                for (int k = 0; k < kPanel; k += 2) { v0 = fma(row[k], yb[k], v0); v1 = fma(row[k + 1], yb[k + 1], v1); }
+            } else {
+                for (int k = 0; k < nbk; ++k) v0 = fma(row[k], yb[k], v0);
+            }
+            r[i] -= v0 + v1;
+        }
+        __syncthreads();
+    }
+    double* out = frhs + fr.r_off;
+    for (int p = q; p < np; p += kSolveCl)
+        for (int i = p * kPanel + threadIdx.x; i < min(ne, p * kPanel + kPanel); i += blockDim.x) out[i] = r[i];
+    if (q == 0)
+        for (int i = ne + threadIdx.x; i < n; i += blockDim.x) out[i] = r[i];
+    cluster_sync_all();                                     // no CTA leaves while others may write to it
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_front_backward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
+                    const int* __restrict__ dofs, const double* __restrict__ F, const double* __restrict__ P,
+                    const double* __restrict__ frhs, double* __restrict__ xs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* wv = reinterpret_cast<double*>(smem_raw);
+    __shared__ double Vs[kPanel][kPanel + 1];
+    __shared__ double xbuf[2][kPanel];
+    const unsigned q = cluster_rank();
+    const FrontInfo fr = fronts[ids[blockIdx.x / kSolveCl]];
+    const int n = fr.n, ne = fr.ne;
+    const double* A = F + fr.f_off;
+    const int* fd = dofs + fr.e_dof_off;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) wv[i] = frhs[fr.r_off + i];
+    __syncthreads();
+    cluster_sync_all();
+    const int np = (ne + kPanel - 1) / kPanel;
+    for (int p = np - 1; p >= 0; --p) {
+        const int k0 = p * kPanel, nbk = min(kPanel, ne - k0);
+        double* xb = xbuf[p & 1];
+        if ((unsigned)(p % kSolveCl) == q) {                // owner: x_p = V_p^T w_p, sent to the cluster
+            const double* V = P + (long long)(fr.p_off + p) * kPanel * kPanel;
+            for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
+            __syncthreads();
+            if (w == 0) {
+                const double wk = lane < nbk ? wv[k0 + lane] : 0.0;
+                double x0 = 0.0, x1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < kPanel; k += 2) {
+                    x0 = fma(Vs[k][lane], __shfl_sync(0xffffffffu, wk, k), x0);
+                    x1 = fma(Vs[k + 1][lane], __shfl_sync(0xffffffffu, wk, k + 1), x1);
+                }
+                const double x = x0 + x1;
+                if (lane < nbk) wv[k0 + lane] = x;
+#pragma unroll 1
+                for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&xb[lane], t, lane < nbk ? x : 0.0);
+            }
+        }
+        cluster_sync_all();                                 // x_p in every CTA
+        // own entries of the earlier panels: w_i -= sum_k L[k0 + k][i] x_p[k]
+        for (int pp = (int)q; pp < p; pp += kSolveCl) {
+            const int i = pp * kPanel + lane;
+            double acc = 0.0;
+            for (int k = w; k < nbk; k += kThreads / 32) acc = fma(A[(long long)(k0 + k) * n + i], xb[k], acc);
+            // reduce the 8 warps' partial sums of entry i through shared memory
+            __shared__ double red[kThreads / 32][32];
+            red[w][lane] = acc;
+            __syncthreads();
+            if (w == 0) {
+                double sacc = 0.0;
+#pragma unroll
+                for (int g = 0; g < kThreads / 32; ++g) sacc += red[g][lane];
+                wv[i] -= sacc;
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = q; p < np; p += kSolveCl)
+        for (int i = p * kPanel + threadIdx.x; i < min(ne, p * kPanel + kPanel); i += blockDim.x) xs[fd[i]] = wv[i];
+    cluster_sync_all();
+}
+
 // r = b - (A^int - delta e0 e0^T) x   (CSR, FP64; delta = 1/d_0^2 when pinned)
 __global__ void k_csr_residual(int nrows, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                const double* __restrict__ val, const double* __restrict__ b,
@@ -690,7 +864,7 @@ __global__ void k_unscale(int n, const double* __restrict__ xs, const double* __
     x[i] = accumulate ? x[i] + v : v;
 }
 
-struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols; };
+struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols, max_ne; };
 
 LevelPlan plan_level(const Tables& t, int h) {
     LevelPlan p;
@@ -699,6 +873,7 @@ LevelPlan plan_level(const Tables& t, int h) {
     p.steps = (max_ne + kPanel - 1) / kPanel;
     p.fwd_rows = std::max(1, (max_nb + kSolveRows - 1) / kSolveRows);
     p.bwd_cols = std::max(1, (max_ne + 31) / 32);
+    p.max_ne = max_ne;
     for (int s = 0; s < p.steps; ++s) {
         int k0 = s * kPanel, rt = 1, ut = 1;
         for (int id : t.levels[h]) {
@@ -754,6 +929,24 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
     return (int)cudaGetLastError();
 }
 
+// Launch `kern` as clusters of kSolveCl CTAs, one cluster per front of the level.
+template <typename... Args>
+static void launch_cluster(void (*kern)(Args...), int fronts, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(fronts * kSolveCl);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kSolveCl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                                const double* rhs, double* xs, cudaStream_t st, Prof& P) {
     double* F = (double*)(ws + L.fronts);
@@ -766,8 +959,13 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
-        MRCM_LAUNCH(P, "k_front_forward", st, k_front_forward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_maps,
-                                                  d.front_dofs, F, Pv, rhs, dscale, t.NV, frhs));
+        if (p.max_ne >= kSolveClMinNe)
+            MRCM_LAUNCH(P, "k_front_forward", st, launch_cluster(k_front_forward_cl, cnt, sm, st, (const FrontInfo*)d.fronts, ids,
+                                                                 (const int*)d.front_maps, (const int*)d.front_dofs, (const double*)F,
+                                                                 Pv, rhs, dscale, (int)t.NV, frhs));
+        else
+            MRCM_LAUNCH(P, "k_front_forward", st, k_front_forward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_maps,
+                                                      d.front_dofs, F, Pv, rhs, dscale, t.NV, frhs));
         MRCM_LAUNCH(P, "k_front_forward_b", st, k_front_forward_b<<<dim3(p.fwd_rows, cnt), kThreads, 0, st>>>(d.fronts, ids, F, frhs));
     }
     for (size_t h = t.levels.size() - 1; h >= 1; --h) {
@@ -776,8 +974,13 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
         MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
-        MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, Pv,
-                                                   frhs, xs));
+        if (p.max_ne >= kSolveClMinNe)
+            MRCM_LAUNCH(P, "k_front_backward", st, launch_cluster(k_front_backward_cl, cnt, sm, st, (const FrontInfo*)d.fronts, ids,
+                                                                  (const int*)d.front_dofs, (const double*)F, Pv,
+                                                                  (const double*)frhs, xs));
+        else
+            MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, Pv,
+                                                       frhs, xs));
     }
 }
 
@@ -787,6 +990,8 @@ int configure_interface(const Tables& t, DeviceTables& d) {
         cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
         cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
         cudaFuncSetAttribute(k_front_backward_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+        cudaFuncSetAttribute(k_front_forward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+        cudaFuncSetAttribute(k_front_backward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
     }
     return (int)cudaGetLastError();
 }

@@ -115,6 +115,20 @@ def test_c2_sizes(lib):
     lib.mrcm_destroy(h)
 
 
+def test_front_sizes_cover_cluster_substitution(lib):
+    """The parity case big_fronts has fronts with >= 128 eliminated dofs (the
+    cluster substitution kernels), C2 with 528."""
+    from paper_2103_08513_gb300._lib import mrcm_sizes
+    from test_gpu_parity import CASES
+    for w, lo in ((small(**CASES["big_fronts"]), 128), (workload("c2"), 528)):
+        rc, h = _setup(lib, w)
+        assert rc == 0
+        sz = mrcm_sizes()
+        lib.mrcm_query_sizes(h, C.byref(sz))
+        assert sz.max_front_ne >= lo and sz.max_front_ne <= sz.max_front
+        lib.mrcm_destroy(h)
+
+
 def test_c3_uneven_setup(lib):
     from paper_2103_08513_gb300._lib import mrcm_sizes
     w = workload("c3")

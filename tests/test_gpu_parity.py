@@ -28,6 +28,10 @@ CASES = {
     "thin": dict(n=(9, 6, 4), edges=([3, 1, 5], [2, 4], [1, 3]), patch=((1, 2), (2, 1), (2, 2))),
     "many_tiles": dict(n=(24, 20, 12), edges=([6, 6, 7, 5], [5, 5, 5, 5], [4, 4, 4]),
                        patch=((3, 2), (2, 2), (3, 5)), sigma=2.0, lam=4.0),
+    # 6 x 6 x 3 subdomains: the top fronts eliminate 144 dofs (4.5 panels), so
+    # their substitutions take the cluster kernels
+    "big_fronts": dict(n=(36, 36, 12), edges=([6] * 6, [6] * 6, [4, 4, 4]),
+                       patch=((3, 2), (3, 2), (3, 3)), sigma=1.5, lam=4.0),
 }
 
 
