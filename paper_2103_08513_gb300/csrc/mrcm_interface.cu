@@ -187,26 +187,54 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
             off[ci] = cf.ne;
         }
     }
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-        const int r = ti * kTile + e / kTile;
-        const int q = tj * kTile + e % kTile;
-        if (r >= n || q > r) continue;
-        double v = 0.0;
-        const int dr = fd[r], dq = fd[q];
+    // per tile row / column: its dof, the two children's positions, the scale
+    __shared__ int s_fd[2][kTile], s_iv[2][2][kTile];
+    __shared__ double s_ds[2][kTile];
+    for (int x = threadIdx.x; x < 2 * kTile; x += blockDim.x) {
+        const int side = x / kTile, o = x % kTile;
+        const int g = (side == 0 ? ti : tj) * kTile + o;
+        int dd = 0, a0 = -1, a1 = -1;
+        double sc = 0.0;
+        if (g < n) { dd = fd[g]; a0 = inv0[g]; a1 = inv1[g]; sc = dscale[dd]; }
+        s_fd[side][o] = dd; s_iv[side][0][o] = a0; s_iv[side][1][o] = a1; s_ds[side][o] = sc;
+    }
+    __syncthreads();
+    // kBatch entries per thread at a time: all their child loads are issued
+    // before any is used
+    constexpr int kBatch = 8;
+    for (int e0 = threadIdx.x; e0 < kTile * kTile; e0 += kBatch * blockDim.x) {
+        double x[2][kBatch];
 #pragma unroll
-        for (int ci = 0; ci < 2; ++ci) {
-            const int* iv = ci == 0 ? inv0 : inv1;
-            const int ir = iv[r], iq = iv[q];
-            if (ir < 0 || iq < 0) continue;
-            if (leaf[ci]) {
-                v += dof_sign(dr, NV) * src[ci][(long long)ir * ld[ci] + iq] * dscale[dr] * dscale[dq];
-            } else {
-                const int a = off[ci] + max(ir, iq), b2 = off[ci] + min(ir, iq);
-                v += src[ci][(long long)a * ld[ci] + b2];
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int rl = e / kTile, ql = e % kTile;
+            const int r = ti * kTile + rl, q = tj * kTile + ql;
+            const bool in = e < kTile * kTile && r < n && q <= r;
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci) {
+                const int ir = in ? s_iv[0][ci][rl] : -1, iq = in ? s_iv[1][ci][ql] : -1;
+                double v = 0.0;
+                if (ir >= 0 && iq >= 0) {
+                    const long long a = leaf[ci] ? (long long)ir * ld[ci] + iq
+                                                 : (long long)(off[ci] + max(ir, iq)) * ld[ci] + off[ci] + min(ir, iq);
+                    v = src[ci][a];
+                }
+                x[ci][u] = v;
             }
         }
-        if (r == fr.pin_row && q == fr.pin_row) v -= 1.0;
-        Fm[(long long)r * n + q] = v;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int rl = e / kTile, ql = e % kTile;
+            const int r = ti * kTile + rl, q = tj * kTile + ql;
+            if (e >= kTile * kTile || r >= n || q > r) continue;
+            double v = 0.0;
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci)
+                v += leaf[ci] ? dof_sign(s_fd[0][rl], NV) * x[ci][u] * s_ds[0][rl] * s_ds[1][ql] : x[ci][u];
+            if (r == fr.pin_row && q == fr.pin_row) v -= 1.0;
+            Fm[(long long)r * n + q] = v;
+        }
     }
     if (t == 0 && fr.ne > 0) {              // first panel's diagonal block (inside tile (0, 0))
         __shared__ double work[kDiagWork];
@@ -586,7 +614,7 @@ k_front_forward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ 
 
 // Backward substitution, boundary columns: w_E = D^{-1} y_E - L_BE^T x_B, with
 // x_B (scaled) from the ancestors, gathered once into shared memory.  32
-// columns x 8 row groups per CTA, four partial sums per thread.
+// columns x 8 row groups per CTA, eight partial sums per thread.
 __global__ void __launch_bounds__(kThreads)
 k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const int* __restrict__ dofs,
                    const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs) {
@@ -603,19 +631,20 @@ k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__
     __shared__ double part[kThreads / 32][32];
     __syncthreads();
     constexpr int G = kThreads / 32;
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};      // eight loads in flight per thread
     if (i < ne) {
         const double* col = A + (long long)ne * n + i;
         int q = g;
-        for (; q + 3 * G < nb; q += 4 * G) {
-            v0 = fma(col[(long long)q * n], xb[q], v0);
-            v1 = fma(col[(long long)(q + G) * n], xb[q + G], v1);
-            v2 = fma(col[(long long)(q + 2 * G) * n], xb[q + 2 * G], v2);
-            v3 = fma(col[(long long)(q + 3 * G) * n], xb[q + 3 * G], v3);
+        for (; q + 7 * G < nb; q += 8 * G) {
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = col[(long long)(q + u * G) * n];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = fma(a[u], xb[q + u * G], v[u]);
         }
-        for (; q < nb; q += G) v0 = fma(col[(long long)q * n], xb[q], v0);
+        for (; q < nb; q += G) v[0] = fma(col[(long long)q * n], xb[q], v[0]);
     }
-    part[g][lane] = (v0 + v1) + (v2 + v3);
+    part[g][lane] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     __syncthreads();
     if (g == 0 && i < ne) {
         double s = 0.0;
@@ -684,6 +713,7 @@ k_front_backward(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
 // ---------------------------------------------------------------------------
 constexpr int kSolveCl = 8;
 constexpr int kSolveClMinNe = 4 * kPanel;    // fronts with fewer E dofs keep one CTA
+constexpr size_t kClSmemMax = 180 * 1024;    // dynamic shared memory cap of the cluster kernels
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -700,21 +730,48 @@ __device__ __forceinline__ void st_cluster(double* local, unsigned rank, double 
     asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(ra), "d"(v) : "memory");
 }
 
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared memory of the cluster substitutions: the front's vector (n doubles,
+// padded to 16 bytes), then the inverse diagonal blocks of this CTA's panels.
+__host__ __device__ inline size_t cl_own_panels(int ne) { return ((ne + kPanel - 1) / kPanel + kSolveCl - 1) / kSolveCl; }
+__host__ __device__ inline size_t cl_vec_bytes(int n) { return ((size_t)n * sizeof(double) + 15) & ~size_t(15); }
+__host__ __device__ inline size_t cl_smem_bytes(int n, int ne) {
+    return cl_vec_bytes(n) + cl_own_panels(ne) * kPanel * (kPanel + 1) * sizeof(double);
+}
+
+// Copy this CTA's inverse diagonal blocks (panels q, q + kSolveCl, ...) into Vown.
+__device__ __forceinline__ void cl_load_own_v(const double* __restrict__ P, const FrontInfo& fr, unsigned q, int np,
+                                              double* Vown) {
+    for (int j = 0; q + (unsigned)j * kSolveCl < (unsigned)np; ++j) {
+        const double* V = P + (long long)(fr.p_off + q + j * kSolveCl) * kPanel * kPanel;
+        double* D = Vown + (size_t)j * kPanel * (kPanel + 1);
+        for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) D[(e >> 5) * (kPanel + 1) + (e & 31)] = V[e];
+    }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_front_forward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                    const int* __restrict__ maps, const int* __restrict__ dofs,
                    const double* __restrict__ F, const double* __restrict__ P, const double* __restrict__ bglob,
                    const double* __restrict__ dscale, int NV, double* __restrict__ frhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* r = reinterpret_cast<double*>(smem_raw);
-    __shared__ double Vs[kPanel][kPanel + 1];
     __shared__ double ybuf[2][kPanel];
     const unsigned q = cluster_rank();
     const FrontInfo fr = fronts[ids[blockIdx.x / kSolveCl]];
     const int n = fr.n, ne = fr.ne;
+    const int np = (ne + kPanel - 1) / kPanel;
+    double* r = reinterpret_cast<double*>(smem_raw);
+    double* Vown = reinterpret_cast<double*>(smem_raw + cl_vec_bytes(n));
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cl_load_own_v(P, fr, q, np, Vown);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double v = 0.0;
         if (i < ne) { int d = fd[i]; v = dof_sign(d, NV) * dscale[d] * bglob[d]; }
@@ -730,35 +787,47 @@ k_front_forward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__
         __syncthreads();
     }
     cluster_sync_all();                                     // every CTA of the cluster is running
-    const int np = (ne + kPanel - 1) / kPanel;
     for (int p = 0; p < np; ++p) {
         const int k0 = p * kPanel, nbk = min(kPanel, ne - k0);
         double* yb = ybuf[p & 1];
-        if ((unsigned)(p % kSolveCl) == q) {                // owner: y_p = V_p r_p, sent to the cluster
-            const double* V = P + (long long)(fr.p_off + p) * kPanel * kPanel;
-            for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
-            __syncthreads();
-            if (w == 0) {
-                const double rk = lane < nbk ? r[k0 + lane] : 0.0;
-                double y0 = 0.0, y1 = 0.0;
+        if ((unsigned)(p % kSolveCl) == q && w == 0) {      // owner: y_p = V_p r_p, sent to the cluster
+            const double* Vs = Vown + (size_t)(p / kSolveCl) * kPanel * (kPanel + 1);
+            const double rk = lane < nbk ? r[k0 + lane] : 0.0;
+            double y0 = 0.0, y1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < kPanel; k += 2) {
-                    y0 = fma(Vs[lane][k], __shfl_sync(0xffffffffu, rk, k), y0);
-                    y1 = fma(Vs[lane][k + 1], __shfl_sync(0xffffffffu, rk, k + 1), y1);
-                }
-                const double y = y0 + y1;
-                if (lane < nbk) r[k0 + lane] = y;
-#pragma unroll 1
-                for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&yb[lane], t, y);
+            for (int k = 0; k < kPanel; k += 2) {
+                y0 = fma(Vs[lane * (kPanel + 1) + k], __shfl_sync(0xffffffffu, rk, k), y0);
+                y1 = fma(Vs[lane * (kPanel + 1) + k + 1], __shfl_sync(0xffffffffu, rk, k + 1), y1);
             }
+            const double y = y0 + y1;
+            if (lane < nbk) r[k0 + lane] = y;
+#pragma unroll 1
+            for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&yb[lane], t, y);
         }
-        cluster_sync_all();                                 // y_p in every CTA
-        // own rows of the later panels: r_i -= L[i][k0 .. k0 + nbk) y_p
-        // (the first own panel after p, then every kSolveCl-th; thread group
-        // threadIdx.x / 32 takes every (kThreads / 32)-th of them, a lane per row)
+        cluster_arrive();
+        // own rows of the later panels: r_i -= L[i][k0 .. k0 + nbk) y_p.  The
+        // first own panel after p, then every kSolveCl-th; thread group
+        // threadIdx.x / 32 takes every (kThreads / 32)-th of them, a lane per
+        // row.  The first row's segment is read before the barrier completes.
         const int p1 = p + 1 + (int)((q + kSolveCl - (unsigned)((p + 1) % kSolveCl)) % kSolveCl);
-        for (int pp = p1 + kSolveCl * (threadIdx.x / kPanel); pp < np; pp += kSolveCl * (kThreads / kPanel)) {
-            const int i = pp * kPanel + threadIdx.x % kPanel;
+        int pp = p1 + kSolveCl * (threadIdx.x / kPanel);
+        int i = pp * kPanel + threadIdx.x % kPanel;
+        double a[kPanel];
+        const bool pre = pp < np && i < ne && nbk == kPanel;
+        {
+            const double* row = A + (pre ? (long long)i * n + k0 : 0);      // the front's first entries when idle
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) a[k] = pre ? row[k] : 0.0;
+        }
+        cluster_wait();                                     // y_p in every CTA
+        if (pre) {
+            double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < kPanel; k += 2) { v0 = fma(a[k], yb[k], v0); v1 = fma(a[k + 1], yb[k + 1], v1); }
+            r[i] -= v0 + v1;
+        }
+        for (pp += pre ? kSolveCl * (kThreads / kPanel) : 0; pp < np; pp += kSolveCl * (kThreads / kPanel)) {
+            i = pp * kPanel + threadIdx.x % kPanel;
             if (i >= ne) continue;
             const double* row = A + (long long)i * n + k0;
             double v0 = 0.0, v1 = 0.0;
@@ -785,55 +854,78 @@ k_front_backward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict_
                     const int* __restrict__ dofs, const double* __restrict__ F, const double* __restrict__ P,
                     const double* __restrict__ frhs, double* __restrict__ xs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* wv = reinterpret_cast<double*>(smem_raw);
-    __shared__ double Vs[kPanel][kPanel + 1];
+    constexpr int kChunk = 8;                               // own earlier panels per reduction round
     __shared__ double xbuf[2][kPanel];
+    __shared__ double red[kChunk][kThreads / 32][kPanel];
     const unsigned q = cluster_rank();
     const FrontInfo fr = fronts[ids[blockIdx.x / kSolveCl]];
     const int n = fr.n, ne = fr.ne;
+    const int np = (ne + kPanel - 1) / kPanel;
+    double* wv = reinterpret_cast<double*>(smem_raw);
+    double* Vown = reinterpret_cast<double*>(smem_raw + cl_vec_bytes(n));
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cl_load_own_v(P, fr, q, np, Vown);
     for (int i = threadIdx.x; i < ne; i += blockDim.x) wv[i] = frhs[fr.r_off + i];
     __syncthreads();
     cluster_sync_all();
-    const int np = (ne + kPanel - 1) / kPanel;
     for (int p = np - 1; p >= 0; --p) {
         const int k0 = p * kPanel, nbk = min(kPanel, ne - k0);
         double* xb = xbuf[p & 1];
-        if ((unsigned)(p % kSolveCl) == q) {                // owner: x_p = V_p^T w_p, sent to the cluster
-            const double* V = P + (long long)(fr.p_off + p) * kPanel * kPanel;
-            for (int e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x) Vs[e >> 5][e & 31] = V[e];
-            __syncthreads();
-            if (w == 0) {
-                const double wk = lane < nbk ? wv[k0 + lane] : 0.0;
-                double x0 = 0.0, x1 = 0.0;
+        if ((unsigned)(p % kSolveCl) == q && w == 0) {      // owner: x_p = V_p^T w_p, sent to the cluster
+            const double* Vs = Vown + (size_t)(p / kSolveCl) * kPanel * (kPanel + 1);
+            const double wk = lane < nbk ? wv[k0 + lane] : 0.0;
+            double x0 = 0.0, x1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < kPanel; k += 2) {
-                    x0 = fma(Vs[k][lane], __shfl_sync(0xffffffffu, wk, k), x0);
-                    x1 = fma(Vs[k + 1][lane], __shfl_sync(0xffffffffu, wk, k + 1), x1);
-                }
-                const double x = x0 + x1;
-                if (lane < nbk) wv[k0 + lane] = x;
-#pragma unroll 1
-                for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&xb[lane], t, lane < nbk ? x : 0.0);
+            for (int k = 0; k < kPanel; k += 2) {
+                x0 = fma(Vs[k * (kPanel + 1) + lane], __shfl_sync(0xffffffffu, wk, k), x0);
+                x1 = fma(Vs[(k + 1) * (kPanel + 1) + lane], __shfl_sync(0xffffffffu, wk, k + 1), x1);
             }
+            const double x = x0 + x1;
+            if (lane < nbk) wv[k0 + lane] = x;
+#pragma unroll 1
+            for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&xb[lane], t, lane < nbk ? x : 0.0);
         }
-        cluster_sync_all();                                 // x_p in every CTA
-        // own entries of the earlier panels: w_i -= sum_k L[k0 + k][i] x_p[k]
-        for (int pp = (int)q; pp < p; pp += kSolveCl) {
-            const int i = pp * kPanel + lane;
-            double acc = 0.0;
-            for (int k = w; k < nbk; k += kThreads / 32) acc = fma(A[(long long)(k0 + k) * n + i], xb[k], acc);
-            // reduce the 8 warps' partial sums of entry i through shared memory
-            __shared__ double red[kThreads / 32][32];
-            red[w][lane] = acc;
+        cluster_arrive();
+        // own entries of the earlier panels pp = q, q + kSolveCl, ... < p:
+        // w_i -= sum_k L[k0 + k][i] x_p[k], warp w taking k = w, w + 8, ...;
+        // the first chunk's matrix entries are read before the barrier completes
+        const int nown = p > (int)q ? (p - (int)q + kSolveCl - 1) / kSolveCl : 0;
+        double a[kChunk][kPanel / (kThreads / 32)];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+#pragma unroll
+            for (int u = 0; u < kPanel / (kThreads / 32); ++u) {
+                const int k = w + u * (kThreads / 32);
+                a[j][u] = (j < nown && k < nbk) ? A[(long long)(k0 + k) * n + (q + j * kSolveCl) * kPanel + lane] : 0.0;
+            }
+        cluster_wait();                                     // x_p in every CTA
+        for (int j0 = 0; j0 < nown; j0 += kChunk) {
+            if (j0 > 0) {
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+#pragma unroll
+                    for (int u = 0; u < kPanel / (kThreads / 32); ++u) {
+                        const int k = w + u * (kThreads / 32);
+                        a[j][u] = (j0 + j < nown && k < nbk)
+                                      ? A[(long long)(k0 + k) * n + (q + (j0 + j) * kSolveCl) * kPanel + lane] : 0.0;
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                if (j0 + j >= nown) break;                  // FP64 instructions only for real panels
+                double acc = 0.0;
+#pragma unroll
+                for (int u = 0; u < kPanel / (kThreads / 32); ++u) acc = fma(a[j][u], xb[w + u * (kThreads / 32)], acc);
+                red[j][w][lane] = acc;
+            }
             __syncthreads();
-            if (w == 0) {
+            if (w < kChunk && j0 + w < nown) {              // warp j sums entry lane of own panel j0 + j
                 double sacc = 0.0;
 #pragma unroll
-                for (int g = 0; g < kThreads / 32; ++g) sacc += red[g][lane];
-                wv[i] -= sacc;
+                for (int g = 0; g < kThreads / 32; ++g) sacc += red[w][g][lane];
+                wv[(q + (j0 + w) * kSolveCl) * kPanel + lane] -= sacc;
             }
             __syncthreads();
         }
@@ -864,7 +956,7 @@ __global__ void k_unscale(int n, const double* __restrict__ xs, const double* __
     x[i] = accumulate ? x[i] + v : v;
 }
 
-struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols, max_ne; };
+struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols, max_ne; size_t cl_smem; };
 
 LevelPlan plan_level(const Tables& t, int h) {
     LevelPlan p;
@@ -874,6 +966,8 @@ LevelPlan plan_level(const Tables& t, int h) {
     p.fwd_rows = std::max(1, (max_nb + kSolveRows - 1) / kSolveRows);
     p.bwd_cols = std::max(1, (max_ne + 31) / 32);
     p.max_ne = max_ne;
+    p.cl_smem = 0;
+    for (int id : t.levels[h]) p.cl_smem = std::max(p.cl_smem, cl_smem_bytes(t.fronts[id].n, t.fronts[id].ne));
     for (int s = 0; s < p.steps; ++s) {
         int k0 = s * kPanel, rt = 1, ut = 1;
         for (int id : t.levels[h]) {
@@ -959,8 +1053,8 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
-        if (p.max_ne >= kSolveClMinNe)
-            MRCM_LAUNCH(P, "k_front_forward", st, launch_cluster(k_front_forward_cl, cnt, sm, st, (const FrontInfo*)d.fronts, ids,
+        if (p.max_ne >= kSolveClMinNe && p.cl_smem <= kClSmemMax)
+            MRCM_LAUNCH(P, "k_front_forward", st, launch_cluster(k_front_forward_cl, cnt, p.cl_smem, st, (const FrontInfo*)d.fronts, ids,
                                                                  (const int*)d.front_maps, (const int*)d.front_dofs, (const double*)F,
                                                                  Pv, rhs, dscale, (int)t.NV, frhs));
         else
@@ -974,8 +1068,8 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
         MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
-        if (p.max_ne >= kSolveClMinNe)
-            MRCM_LAUNCH(P, "k_front_backward", st, launch_cluster(k_front_backward_cl, cnt, sm, st, (const FrontInfo*)d.fronts, ids,
+        if (p.max_ne >= kSolveClMinNe && p.cl_smem <= kClSmemMax)
+            MRCM_LAUNCH(P, "k_front_backward", st, launch_cluster(k_front_backward_cl, cnt, p.cl_smem, st, (const FrontInfo*)d.fronts, ids,
                                                                   (const int*)d.front_dofs, (const double*)F, Pv,
                                                                   (const double*)frhs, xs));
         else
@@ -985,14 +1079,18 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
 }
 
 int configure_interface(const Tables& t, DeviceTables& d) {
+    // opt in to the dynamic shared memory each substitution kernel may take
+    // (static + dynamic above 48 KB needs it)
     d.front_smem = sizeof(double) * (size_t)std::max(t.max_front, 1);
-    if (d.front_smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
-        cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
-        cudaFuncSetAttribute(k_front_backward_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
-        cudaFuncSetAttribute(k_front_forward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
-        cudaFuncSetAttribute(k_front_backward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
-    }
+    cudaFuncSetAttribute(k_front_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+    cudaFuncSetAttribute(k_front_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+    cudaFuncSetAttribute(k_front_backward_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.front_smem);
+    size_t cl = 0;
+    for (const FrontInfo& f : t.fronts)
+        if (f.ne >= kSolveClMinNe) cl = std::max(cl, cl_smem_bytes(f.n, f.ne));
+    const int lim = (int)std::max<size_t>(std::min(cl, kClSmemMax), 1);
+    cudaFuncSetAttribute(k_front_forward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_front_backward_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     return (int)cudaGetLastError();
 }
 
