@@ -58,9 +58,16 @@ __device__ __forceinline__ long long global_cell(const SubInfo& s, const int lc[
     return (long long)(s.o[0] + lc[0]) + (long long)n[0] * ((s.o[1] + lc[1]) + (long long)n[1] * (s.o[2] + lc[2]));
 }
 
-__device__ __forceinline__ double beta_of(int mode, double alpha, double beta_const, const SubInfo& s,
-                                          int a, double h_a, double Kn) {
-    return mode == MRCM_BETA_CONST ? beta_const : alpha * (double)s.sz[a] * h_a / Kn;
+// Robin coefficient of a face with normal permeability Kn: beta (the constant,
+// or alpha H / Kn with H the subdomain's extent along the normal) and
+// T_R = A_f / (h_n / (2 Kn) + beta), with one Newton reciprocal of Kn shared by
+// both and one of the denominator instead of FP64 divisions.
+__device__ __forceinline__ void robin_of(int mode, double alpha, double beta_const, const SubInfo& s, int a,
+                                         double h_a, double area_a, double Kn, double* beta, double* tr) {
+    const double ik = rcp64(Kn);
+    const double be = mode == MRCM_BETA_CONST ? beta_const : alpha * (double)s.sz[a] * h_a * ik;
+    *beta = be;
+    *tr = area_a * rcp64(fma(0.5 * h_a, ik, be));
 }
 
 // ---------------------------------------------------------------------------
@@ -125,9 +132,9 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
             } else if (s.o[a] + lc[a] == geo.n[a] - 1) {
                 if ((bc_lo_hi.y >> a) & 1) { double TD = 2.0 * ah[a] * Kc[a][g]; d += TD; rd += TD * bhi[a]; }
             } else {
-                const double ka = Kc[a][g];
-                const double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-                d += geo.area[a] * rcp64(geo.h[a] / (2.0 * ka) + beta);
+                double beta, tr;
+                robin_of(beta_mode, alpha, beta_const, s, a, geo.h[a], geo.area[a], Kc[a][g], &beta, &tr);
+                d += tr;
             }
             // -a side
             if (lc[a] > 0) {
@@ -135,9 +142,9 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
             } else if (s.o[a] == 0) {
                 if ((bc_lo_hi.x >> a) & 1) { double TD = 2.0 * ah[a] * Kc[a][g]; d += TD; rd += TD * blo[a]; }
             } else {
-                const double ka = Kc[a][g];
-                const double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-                d += geo.area[a] * rcp64(geo.h[a] / (2.0 * ka) + beta);
+                double beta, tr;
+                robin_of(beta_mode, alpha, beta_const, s, a, geo.h[a], geo.area[a], Kc[a][g], &beta, &tr);
+                d += tr;
             }
         }
         const long long i = s.cell_off + c;
@@ -151,9 +158,8 @@ k_coefficients(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fa
         local_coords(s, fi.cell, lc);
         long long g = global_cell(s, lc, geo.n);
         int a = fi.axis;
-        double ka = Kc[a][g];
-        double beta = beta_of(beta_mode, alpha, beta_const, s, a, geo.h[a], ka);
-        const double tr = geo.area[a] / (geo.h[a] / (2.0 * ka) + beta);
+        double beta, tr;
+        robin_of(beta_mode, alpha, beta_const, s, a, geo.h[a], geo.area[a], Kc[a][g], &beta, &tr);
         face_tr[s.face_off + q] = tr;
         face_beta[s.face_off + q] = beta;
         face_u[s.face_off + q] = -beta * fi.s * tr;     // U-MBF right-hand side on this face
@@ -1472,30 +1478,51 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
           const double* __restrict__ face_tr, const double* __restrict__ face_beta,
           const double* __restrict__ face_bst, const double* __restrict__ X, Geo geo,
           double* __restrict__ elem, double* __restrict__ elem_b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubInfo s = subs[blockIdx.x];
-    const int nI = s.nI, m = s.m, N = s.N, dim = s.el_dim;
+    const int nI = s.nI, m = s.m, N = s.N, dim = s.el_dim, nf = s.nface;
+    // the subdomain's face cells and weights, staged once
+    double* s_tr = reinterpret_cast<double*>(smem_raw);
+    double* s_bst = s_tr + nf;
+    int* s_cell = reinterpret_cast<int*>(s_bst + nf);
     __shared__ int start[kMaxI + 1];                  // per-column face ranges
-    for (int q = threadIdx.x; q <= nI; q += blockDim.x) start[q] = s.nface;
+    for (int q = threadIdx.x; q <= nI; q += blockDim.x) start[q] = nf;
     __syncthreads();
-    for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
-        int c = faces[s.face_off + q].col;
+    for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+        const FaceInfo fi = faces[s.face_off + q];
+        const int c = fi.col;
         if (q == 0 || faces[s.face_off + q - 1].col != c) start[c] = q;
+        s_cell[q] = fi.cell;
+        s_tr[q] = face_tr[s.face_off + q];
+        s_bst[q] = face_bst[s.face_off + q];
     }
     __syncthreads();
     const double* Xs = X + s.x_off;
     // The faces of basis k all carry column k; the Robin data g of MBF column j
     // on them is 1 (j = k, P-MBF), -beta s (j = nI + k, U-MBF) or 0, so the
     // traces are sum T_R x and sum beta s T_R x plus a correction on those two
-    // columns: two FMAs per face and column.
+    // columns: two FMAs per face and column.  Four faces' x values are read at
+    // once.
     for (int e = threadIdx.x; e < nI * m; e += blockDim.x) {
         int k = e / m, j = e - (e / m) * m;
         int q0 = start[k], q1 = start[k + 1];
         const double* x = Xs + (long long)j * N;
         double sf = 0.0, su = 0.0;
-        for (int q = q0; q < q1; ++q) {
-            const double xv = x[faces[s.face_off + q].cell];
-            sf = fma(face_tr[s.face_off + q], xv, sf);
-            su = fma(face_bst[s.face_off + q], xv, su);
+        int q = q0;
+        for (; q + 3 < q1; q += 4) {
+            double xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = x[s_cell[q + u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sf = fma(s_tr[q + u], xv[u], sf);
+                su = fma(s_bst[q + u], xv[u], su);
+            }
+        }
+        for (; q < q1; ++q) {
+            const double xv = x[s_cell[q]];
+            sf = fma(s_tr[q], xv, sf);
+            su = fma(s_bst[q], xv, su);
         }
         double sdiag = 0.0;
         if (j == k || j == nI + k) {
@@ -1528,6 +1555,13 @@ __global__ void k_zero_int(int* p, int n) {
 }
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
+
+// dynamic shared memory of k_element: cells and two weights of the largest face set
+static size_t element_smem(const Tables& t) {
+    int mx = 1;
+    for (const SubInfo& s : t.subs) mx = std::max(mx, s.nface);
+    return (size_t)mx * (2 * sizeof(double) + sizeof(int));
+}
 
 Geo make_geo(const mrcm_config& c) {
     Geo g;
@@ -1643,6 +1677,7 @@ int configure_local(const Tables& t, DeviceTables& d) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f64 = t.cfg.precision == MRCM_FP64;
+    cudaFuncSetAttribute(k_element, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)element_smem(t));
     d.solve_smem = solve_smem_bytes(t, t.cfg.precision);
     for (int v = 0; v < kNumSolveVariants; ++v) {
         const void* k0 = f64 ? solve_kernel<double, false, false>(v) : solve_kernel<float, true, false>(v);
@@ -1720,7 +1755,7 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
         }
     }
     MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 0 : sweeps));
-    MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, 0, st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
+    MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
                                         (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
     return (int)cudaGetLastError();
