@@ -285,8 +285,9 @@ def parse():
     ap.add_argument("--ir-sweeps", type=int, default=None,
                     help="FP64 refinement sweeps of the mixed local solve (default 6 for the C5 layouts, else 3: "
                          "the fewest that keep p and u within 1e-8 of the FP64 form with margin)")
-    ap.add_argument("--ir-tol", type=float, default=1e-11,
-                    help="per-column refinement stop ||r|| <= tol ||b|| (columns retire early)")
+    ap.add_argument("--ir-tol", type=float, default=1e-9,
+                    help="per-column refinement stop ||r|| <= tol ||b|| (columns retire early; 1e-9, a tenth "
+                         "of the 1e-8 target, leaves the error against the FP64 form unchanged at C2)")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
