@@ -81,9 +81,9 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // of V is final at step k).  Block column k is not written after step k - 1,
 // so L = T[i][k] / d_k is formed once at the end: one barrier per pivot.  One
 // lane per column: a row costs one FP64 FMA per step.  Warp 0 updates row
-// k + 1 alone and then computes 1 / d_{k+1} (one cubic Newton step), while
-// warps 1.. update the other rows.  A zero or NaN pivot is replaced by 1 and
-// counted.  Block-wide, >= 2 warps.
+// k + 1 alone and its lane k + 1 computes 1 / d_{k+1} (one cubic Newton step)
+// from the fresh diagonal, while warps 1.. update the other rows.  A zero or
+// NaN pivot is replaced by 1 and counted.  Block-wide, >= 2 warps.
 constexpr int kDiagW = 2 * kPanel + 1;
 constexpr int kDiagWork = kPanel * kDiagW + kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
@@ -119,13 +119,12 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
                 const int i = k + 1;
                 if (c <= i) {
                     double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
-                    *dst = fma(-T[i][k], wc, *dst);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    double d = T[i][i];
-                    if (d == 0.0 || d != d) { d = 1.0; T[i][i] = 1.0; *zero = 1; }
-                    sinv[i] = rcp64c(d);
+                    double v = fma(-T[i][k], wc, *dst);
+                    if (c == i) {                             // the next pivot, straight from the register
+                        if (v == 0.0 || v != v) { v = 1.0; *zero = 1; }
+                        sinv[i] = rcp64c(v);
+                    }
+                    *dst = v;
                 }
             }
         } else {
