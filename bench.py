@@ -187,7 +187,7 @@ def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks, wo
 def learned_form(dev, stream, train_fields=200, epochs=2, eval_fields=4):
     """The learned warm start on its own workload (40x40x10 cells, 10x10x5 subdomains,
     5x2 patches, config-1-style fields): train on the P-MBFs of seeded fields, then
-    warm-start FP32 CG on held-out fields; the direct FP64 MBFs judge the error."""
+    warm-start FP32 CG on held-out fields; the direct FP64 MBFs are the reference for its error."""
     import torch
     from paper_2103_08513_gb300 import MRCM
     from paper_2103_08513_gb300.learned import WarmStartNet
@@ -230,7 +230,7 @@ def learned_form(dev, stream, train_fields=200, epochs=2, eval_fields=4):
     for sd in range(201, 201 + eval_fields):
         s.factor_local(field(sd))
         e0.record(stream)
-        s.solve_mbf(f)                              # direct FP64 MBFs: the judge and the fallback
+        s.solve_mbf(f)                              # direct FP64 MBFs: the reference and the fallback
         e1.record(stream)
         torch.cuda.synchronize()
         t_dir += e0.elapsed_time(e1)
@@ -270,7 +270,7 @@ def learned_form(dev, stream, train_fields=200, epochs=2, eval_fields=4):
                  "direct_fp64_ms_per_subdomain_set": round(t_dir / (eval_fields * 32), 5),
                  "rel_err_vs_direct_fp64": max(errs), "cg_tol": 1e-6, "fallbacks_to_direct": fallbacks},
         "note": "FP32 CG reaches its 1e-6 tolerance, not the 1e-8 of the mixed form; the direct FP64-refined "
-                "MBFs stay the fallback and the judge",
+                "MBFs stay the fallback and the reference",
     }
 
 

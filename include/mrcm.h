@@ -349,7 +349,7 @@ mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, floa
  * first n_samples samples (order of mrcm_net_samples), from x0[s] (unscaled
  * guess in the sample layout; NULL = zero), to ||r|| <= tol ||b|| or maxit
  * iterations.  The result replaces the P-MBF column in the MBF array (so the
- * FP64 direct solve can judge it first); iters[s] (device int) receives the
+ * FP64 direct solve can check it first); iters[s] (device int) receives the
  * iterations, maxit + 1 when the tolerance was not reached. */
 mrcm_status mrcm_pcg_mbf(mrcm_handle* h, const mrcm_net* net, void* ws, const float* x0, int n_samples,
                          int maxit, double tol, int* iters, void* stream);

@@ -1,5 +1,5 @@
 """Learned warm start on the GPU: gradients against the oracle, training on
-the method's own MBFs, and the warm-start gain judged by the FP64 direct MBFs.
+the method's own MBFs, and the warm-start gain checked against the FP64 direct MBFs.
 """
 import numpy as np
 import pytest
@@ -53,7 +53,7 @@ def _mrcm_fields(seeds, n=(40, 40, 10)):
 def test_training_and_warm_start_gain():
     """Train on the method's own P-MBFs (config-1-style fields), then warm-start CG
     on a held-out field: fewer iterations than from zero, and the CG result agrees
-    with the FP64 direct MBFs (the judge) to the CG tolerance."""
+    with the FP64 direct MBFs (the reference) to the CG tolerance."""
     from paper_2103_08513_gb300 import MRCM
     n = (40, 40, 10)
     edges = ([10] * 4, [10] * 4, [5, 5])
@@ -83,7 +83,7 @@ def test_training_and_warm_start_gain():
     nsm = min(256, x.shape[0])
     y = net.forward(x[:nsm].contiguous())
     it_net = net.pcg(s, y, nsm, maxit=500, tol=1e-6).cpu().numpy()
-    _, t_net = net.samples(s)                  # CG results, judged by the direct FP64 MBFs
+    _, t_net = net.samples(s)                  # CG results, checked against the direct FP64 MBFs
     s.solve_mbf(fd)
     it_zero = net.pcg(s, None, nsm, maxit=500, tol=1e-6).cpu().numpy()
     assert (it_net <= 500).all() and (it_zero <= 500).all()
