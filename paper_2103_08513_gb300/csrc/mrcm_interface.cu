@@ -800,7 +800,7 @@ k_front_forward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__
             }
             const double y = y0 + y1;
             if (lane < nbk) r[k0 + lane] = y;
-#pragma unroll 1
+#pragma unroll
             for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&yb[lane], t, y);
         }
         cluster_arrive();
@@ -883,7 +883,7 @@ k_front_backward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict_
             }
             const double x = x0 + x1;
             if (lane < nbk) wv[k0 + lane] = x;
-#pragma unroll 1
+#pragma unroll
             for (unsigned t = 0; t < kSolveCl; ++t) st_cluster(&xb[lane], t, lane < nbk ? x : 0.0);
         }
         cluster_arrive();
