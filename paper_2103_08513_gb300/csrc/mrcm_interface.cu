@@ -612,11 +612,16 @@ k_front_forward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ 
 }
 
 // Backward substitution, boundary columns: w_E = D^{-1} y_E - L_BE^T x_B, with
-// x_B (scaled) from the ancestors, gathered once into shared memory.  32
-// columns x 8 row groups per CTA, eight partial sums per thread.
+// x_B (scaled) from the ancestors.  32 columns x 8 row groups per CTA, eight
+// partial sums per thread; the boundary rows are cut into gridDim.z chunks
+// (one CTA each, its x_B chunk gathered into shared memory).  With several
+// chunks each CTA stores its column sums, and the CTA that completes a column
+// block (counter wrapping back to 0, so the counters are ready for the next
+// level) adds them in chunk order: the result does not depend on timing.
 __global__ void __launch_bounds__(kThreads)
 k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const int* __restrict__ dofs,
-                   const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs) {
+                   const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs,
+                   double* __restrict__ bpart, unsigned* __restrict__ bcnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* xb = reinterpret_cast<double*>(smem_raw);
     const FrontInfo fr = fronts[ids[blockIdx.y]];
@@ -624,33 +629,52 @@ k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     if (blockIdx.x * 32 >= ne) return;
+    const int Z = gridDim.z, z = blockIdx.z;
+    const int chunk = (nb + Z - 1) / Z;
+    const int q0 = min(nb, z * chunk), q1 = min(nb, q0 + chunk);
     const double* A = F + fr.f_off;
     const int* fd = dofs + fr.e_dof_off;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) xb[q] = xs[fd[ne + q]];
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) xb[q - q0] = xs[fd[ne + q]];
     __shared__ double part[kThreads / 32][32];
+    __shared__ unsigned last;
     __syncthreads();
     constexpr int G = kThreads / 32;
     double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};      // eight loads in flight per thread
     if (i < ne) {
         const double* col = A + (long long)ne * n + i;
-        int q = g;
-        for (; q + 7 * G < nb; q += 8 * G) {
+        int q = q0 + g;
+        for (; q + 7 * G < q1; q += 8 * G) {
             double a[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = col[(long long)(q + u * G) * n];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = fma(a[u], xb[q + u * G], v[u]);
+            for (int u = 0; u < 8; ++u) v[u] = fma(a[u], xb[q - q0 + u * G], v[u]);
         }
-        for (; q < nb; q += G) v[0] = fma(col[(long long)q * n], xb[q], v[0]);
+        for (; q < q1; q += G) v[0] = fma(col[(long long)q * n], xb[q - q0], v[0]);
     }
     part[g][lane] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     __syncthreads();
-    if (g == 0 && i < ne) {
-        double s = 0.0;
+    double s = 0.0;
+    if (g == 0) {
 #pragma unroll
         for (int q = 0; q < G; ++q) s += part[q][lane];
-        double* z = frhs + fr.r_off;
-        z[i] = z[i] / A[(long long)i * n + i] - s;
+    }
+    double* zr = frhs + fr.r_off;
+    if (Z == 1) {
+        if (g == 0 && i < ne) zr[i] = zr[i] / A[(long long)i * n + i] - s;
+        return;
+    }
+    const long long slot = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    if (g == 0) bpart[(slot * Z + z) * 32 + lane] = s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicInc(&bcnt[slot], (unsigned)(Z - 1)) == (unsigned)(Z - 1);
+    __syncthreads();
+    if (last && g == 0 && i < ne) {
+        __threadfence();
+        double t = 0.0;
+        for (int zz = 0; zz < Z; ++zz) t += __ldcg(&bpart[(slot * Z + zz) * 32 + lane]);
+        zr[i] = zr[i] / A[(long long)i * n + i] - t;
     }
 }
 
@@ -955,7 +979,7 @@ __global__ void k_unscale(int n, const double* __restrict__ xs, const double* __
     x[i] = accumulate ? x[i] + v : v;
 }
 
-struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols, max_ne; size_t cl_smem; };
+struct LevelPlan { int steps; std::vector<int> row_tiles, upd_tiles; int fwd_rows, bwd_cols, max_ne, max_nb; size_t cl_smem; };
 
 LevelPlan plan_level(const Tables& t, int h) {
     LevelPlan p;
@@ -965,6 +989,7 @@ LevelPlan plan_level(const Tables& t, int h) {
     p.fwd_rows = std::max(1, (max_nb + kSolveRows - 1) / kSolveRows);
     p.bwd_cols = std::max(1, (max_ne + 31) / 32);
     p.max_ne = max_ne;
+    p.max_nb = max_nb;
     p.cl_smem = 0;
     for (int id : t.levels[h]) p.cl_smem = std::max(p.cl_smem, cl_smem_bytes(t.fronts[id].n, t.fronts[id].ne));
     for (int s = 0; s < p.steps; ++s) {
@@ -1046,6 +1071,8 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
     const double* Pv = (const double*)(ws + L.panel);
     double* frhs = (double*)(ws + L.frhs);
     const double* dscale = (const double*)(ws + L.dscale);
+    double* bpart = (double*)(ws + L.bpart);
+    unsigned* bcnt = (unsigned*)(ws + L.bcnt);
     size_t sm = sizeof(double) * (size_t)std::max(t.max_front, 1);
     for (size_t h = 1; h < t.levels.size(); ++h) {
         int cnt = (int)t.levels[h].size();
@@ -1066,7 +1093,8 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
-        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt), kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, xs, frhs));
+        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt, bwd_split(p.max_nb)), kThreads, sm, st>>>(
+                                                        d.fronts, ids, d.front_dofs, F, xs, frhs, bpart, bcnt));
         if (p.max_ne >= kSolveClMinNe && p.cl_smem <= kClSmemMax)
             MRCM_LAUNCH(P, "k_front_backward", st, launch_cluster(k_front_backward_cl, cnt, p.cl_smem, st, (const FrontInfo*)d.fronts, ids,
                                                                   (const int*)d.front_dofs, (const double*)F, Pv,
@@ -1103,6 +1131,11 @@ int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout&
     double* r = (double*)(ws + L.xres);
     double* xs = (double*)(ws + L.xtmp);
     const int pin = t.has_dirichlet ? 0 : 1;
+    {
+        size_t parts, cnts;                     // counters of the split back substitution start at 0
+        bwd_split_sizes(t.levels, t.fronts, &parts, &cnts);
+        cudaMemsetAsync(ws + L.bcnt, 0, cnts * sizeof(unsigned), st);
+    }
     multifrontal_solve(t, d, L, ws, b, xs, st, P);
     MRCM_LAUNCH(P, "k_unscale", st, k_unscale<<<(nd + 255) / 256, 256, 0, st>>>(nd, xs, dscale, X, 0));
     const int refine = t.cfg.interface_refine == 0 ? 1 : std::max(0, t.cfg.interface_refine);

@@ -1,5 +1,6 @@
 // Internal tables shared by the host setup and the CUDA kernels of libmrcm.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -125,6 +126,7 @@ struct Tables {
 struct Layout {
     size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, face_u, face_bst, W, X, R, colnorm, conv;
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
+    size_t bpart, bcnt;    // row-chunk partial sums and counters of the split boundary back substitution
     size_t total;
 };
 
@@ -222,6 +224,25 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     x += 5 * sizeof(double) * (size_t)b;
     L.total = (x + 127) & ~size_t(127);
     return L;
+}
+
+// Row chunks of the boundary back substitution for a level whose fronts have
+// at most max_nb boundary rows (about 128 rows per chunk, at most 8 chunks).
+inline int bwd_split(int max_nb) { return std::max(1, std::min(8, (max_nb + 127) / 128)); }
+
+// Sizes (doubles, counters) of the split back substitution's work arrays: the
+// largest level's (fronts x column blocks x chunks x 32) and (fronts x column blocks).
+inline void bwd_split_sizes(const std::vector<std::vector<int>>& levels, const std::vector<FrontInfo>& fronts,
+                            size_t* parts, size_t* counters) {
+    *parts = 32;
+    *counters = 1;
+    for (const auto& lv : levels) {
+        int mne = 0, mnb = 0;
+        for (int id : lv) { mne = std::max(mne, fronts[id].ne); mnb = std::max(mnb, fronts[id].nb); }
+        const size_t slots = lv.size() * (size_t)std::max(1, (mne + 31) / 32);
+        *parts = std::max(*parts, slots * bwd_split(mnb) * 32);
+        *counters = std::max(*counters, slots);
+    }
 }
 
 // Device status words at Layout::status.

@@ -437,6 +437,12 @@ void compute_layout(const Tables& t, Layout& L) {
     L.xtmp = take((size_t)2 * t.NV * sizeof(double));
     L.psum = take(((size_t)t.subs.size() + 64) * sizeof(double));
     L.status = take(ST_COUNT * sizeof(int));
+    {
+        size_t parts, cnts;
+        bwd_split_sizes(t.levels, t.fronts, &parts, &cnts);
+        L.bpart = take(parts * sizeof(double));
+        L.bcnt = take(cnts * sizeof(unsigned));
+    }
     L.total = off;
 }
 
