@@ -140,6 +140,8 @@ typedef struct {
     int n_waves;                /* memory-bounded waves of the local phase */
     int max_front_ne;           /* largest eliminated block of a front (its substitutions
                                    run on a cluster of CTAs from 128 on) */
+    int max_front_nb;           /* largest boundary block of a front (its back substitution
+                                   is split into row chunks above 128) */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;

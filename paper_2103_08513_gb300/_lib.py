@@ -50,6 +50,7 @@ class mrcm_sizes(C.Structure):
         ("mbf_entries", C.c_longlong), ("ldl_flops", C.c_double), ("ldl_update_flops", C.c_double),
         ("n_waves", C.c_int),
         ("max_front_ne", C.c_int),
+        ("max_front_nb", C.c_int),
     ]
 
 

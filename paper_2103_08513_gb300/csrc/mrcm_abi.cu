@@ -224,7 +224,11 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
     o->ldl_update_flops = t.ldl_update_flops;
     o->n_waves = t.n_waves;
     o->max_front_ne = 0;
-    for (const auto& f : t.fronts) o->max_front_ne = std::max(o->max_front_ne, f.ne);
+    o->max_front_nb = 0;
+    for (const auto& f : t.fronts) {
+        o->max_front_ne = std::max(o->max_front_ne, f.ne);
+        o->max_front_nb = std::max(o->max_front_nb, f.nb);
+    }
     return MRCM_OK;
 }
 

@@ -117,15 +117,17 @@ def test_c2_sizes(lib):
 
 def test_front_sizes_cover_cluster_substitution(lib):
     """The parity case big_fronts has fronts with >= 128 eliminated dofs (the
-    cluster substitution kernels), C2 with 528."""
+    cluster substitution kernels) and > 128 boundary dofs (the back
+    substitution split into row chunks); C2 has 528 and 768."""
     from paper_2103_08513_gb300._lib import mrcm_sizes
     from test_gpu_parity import CASES
-    for w, lo in ((small(**CASES["big_fronts"]), 128), (workload("c2"), 528)):
+    for w, lo_ne, lo_nb in ((small(**CASES["big_fronts"]), 128, 129), (workload("c2"), 528, 768)):
         rc, h = _setup(lib, w)
         assert rc == 0
         sz = mrcm_sizes()
         lib.mrcm_query_sizes(h, C.byref(sz))
-        assert sz.max_front_ne >= lo and sz.max_front_ne <= sz.max_front
+        assert sz.max_front_ne >= lo_ne and sz.max_front_ne <= sz.max_front
+        assert sz.max_front_nb >= lo_nb and sz.max_front_nb <= sz.max_front
         lib.mrcm_destroy(h)
 
 
