@@ -39,9 +39,10 @@ METRIC = "MRCM pressure solve s and MBF-sets/s, mixed/learned vs FP64 GPU at rel
 UNIT = "MBF-sets/s"
 
 # Peaks (roofline denominators).  HBM and BF16 tensor from MEASURED_PEAKS.json
-# when present; SIMT ALU peaks from unit counts and the maximum SM clock:
-# FP32 = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 = the GB300 FP64
-# rate (1.25 TFLOP/s).
+# when present; the FP32 SIMT peak from unit counts and the maximum SM clock
+# (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz); the FP64 peak measured on
+# the device by the library (mrcm_measure_fp64_peak: independent FMA chains
+# on every SM, CUDA events, best of three).
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -57,8 +58,20 @@ def load_peaks():
     sm_max = float(d.get("sm_max_mhz", 2070.0))
     d["fp32_tflops"] = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     d["fp64_tflops"] = 1.25
+    d["fp64_source"] = "nominal"
     d["source"] = src
     return d
+
+
+def measure_fp64_peak(peaks, stream):
+    """Replace the nominal FP64 peak by the rate measured on this device."""
+    import ctypes as C
+    from paper_2103_08513_gb300 import _lib
+    v = C.c_double()
+    if _lib.load().mrcm_measure_fp64_peak(C.c_void_p(stream.cuda_stream), C.byref(v)) == 0 and v.value > 0:
+        peaks["fp64_tflops"] = float(v.value)
+        peaks["fp64_source"] = "measured (mrcm_measure_fp64_peak)"
+    return peaks
 
 
 # ------------------------------------------------------------------ clocks
@@ -110,33 +123,52 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-# ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(w, K, f, n_sub_sample, seed=0):
-    """Time the oracle's local MBF stage on a seeded sample of subdomains (1 core)."""
-    import numpy as np
-
-    import oracle
-    from oracle.mrcm import local_problem, solve_local, traces
-    from oracle.problem import build_bases
-    prob = oracle.from_workload(w, K=K, f=f)
-    bases, sub_bases, face_basis = build_bases(prob)
-    rng = np.random.default_rng(seed)
-    subs = rng.choice(prob.nsub, size=min(n_sub_sample, prob.nsub), replace=False)
-    t0 = time.perf_counter()
-    for l in subs:
-        lp = local_problem(prob, int(l), sub_bases, face_basis)
-        X = solve_local(lp)
-        traces(lp, X)
-    dt = time.perf_counter() - t0
-    return len(subs), dt
+# ------------------------------------------------------------------ CPU oracle
+FULL_ORACLE = ("c1", "c2", "c2_betaHK")      # workloads the oracle solves in full within a bench run
 
 
 def cpu_cores_used():
-    return 1
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_full(w, K, f, pool=None):
+    """The whole staged oracle (local stage, interface assembly + solve,
+    reconstruction) on all host cores; returns (result, seconds)."""
+    import oracle
+    prob = oracle.from_workload(w, K=K, f=f)
+    t0 = time.perf_counter()
+    r = oracle.solve_mrcm(prob, keep=False, processes=None if pool else cpu_cores_used(), pool=pool)
+    return r, time.perf_counter() - t0
+
+
+def oracle_sample(w, K, f, n_sub_sample, seed=0, pool=None):
+    """The oracle's local MBF stage (assembly, sparse LU, all m_l right-hand sides,
+    traces and the subdomain's interface block) on a seeded sample of subdomains,
+    over the pool's workers; for workloads too large to solve in full."""
+    import numpy as np
+
+    import oracle
+    from oracle import mrcm as om
+    prob = oracle.from_workload(w, K=K, f=f)
+    rng = np.random.default_rng(seed)
+    subs = [int(x) for x in rng.choice(prob.nsub, size=min(n_sub_sample, prob.nsub), replace=False)]
+    own = pool is None
+    if own:
+        pool = om.make_pool(prob, cpu_cores_used())
+    try:
+        t0 = time.perf_counter()
+        chunk = max(1, len(subs) // (4 * pool.n_procs))
+        pool.map(om._pool_local, [subs[i:i + chunk] for i in range(0, len(subs), chunk)])
+        dt = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    return len(subs), dt
 
 
 # ------------------------------------------------------------------ roofline
-def kernel_work(name, sizes, swept, precision, peaks):
+def kernel_work(name, sizes, swept, precision, peaks, sweeps=0):
     """Algorithmic work of one solve step for a kernel: (work, bound, unit, peak)."""
     f32 = precision != "fp64"
     alu32 = peaks["fp32_tflops"] if f32 else peaks["fp64_tflops"]
@@ -145,8 +177,9 @@ def kernel_work(name, sizes, swept, precision, peaks):
     if name == "k_ldl_panel":
         return sizes["ldl_flops"] - sizes["ldl_update_flops"], "alu", "TFLOP/s", peaks["fp64_tflops"]
     if name == "k_ir_sweep":
-        # FP64 7-point residual: 13 flops per swept MBF entry
-        return 13.0 * swept, "alu", "TFLOP/s", peaks["fp64_tflops"]
+        # refinement sweep (FP64 7-point residual + correction): HBM-bound, 16 B per swept
+        # MBF entry (read X, write X) + 32 B of coefficients per cell and sweep
+        return 16.0 * swept + 32.0 * sizes["n_cells"] * sweeps, "hbm", "GB/s", peaks["hbm_gbs"]
     if name == "k_block_factor":
         return sizes["local_factor_flops"], "alu", "TFLOP/s", alu32
     if name == "k_local_solve":
@@ -170,9 +203,9 @@ def traffic_per_launch(workload_key, kernel):
     return None
 
 
-def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks, workload_key=None):
+def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks, workload_key=None, sweeps=0):
     """Achieved rate of a kernel: its algorithmic work per step over its time per step."""
-    work, bound, unit, peak = kernel_work(name, sizes, swept, precision, peaks)
+    work, bound, unit, peak = kernel_work(name, sizes, swept, precision, peaks, sweeps)
     per_step_s = total_ms / 1e3 / steps
     scale = 1e12 if unit == "TFLOP/s" else 1e9
     achieved = work / per_step_s / scale
@@ -180,7 +213,18 @@ def roofline(name, total_ms, launches, steps, sizes, swept, precision, peaks, wo
             "frac": round(achieved / peak, 4),
             "traffic": traffic_per_launch(workload_key, name) if workload_key else None, "launches": launches,
             "avg_launch_ms": round(total_ms / max(launches, 1), 4),
-            "work_per_step": work, "peak_source": peaks["source"] if bound == "hbm" else "derived"}
+            "work_per_step": work,
+            "peak_source": (peaks["source"] if bound == "hbm" else
+                            peaks["fp64_source"] if peak == peaks["fp64_tflops"] else "derived")}
+
+
+def fp64_view(total_ms, steps, swept, peaks):
+    """The refinement sweep against the FP64 pipe: 7 FMAs + 1 add per swept entry."""
+    flops = 15.0 * swept
+    achieved = flops / (total_ms / 1e3 / steps) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peaks["fp64_tflops"], 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peaks["fp64_tflops"], 4),
+            "flops_per_swept_entry": 15, "peak_source": peaks["fp64_source"]}
 
 
 # ------------------------------------------------------------------ main
@@ -283,12 +327,13 @@ def parse():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir"])
     ap.add_argument("--ir-sweeps", type=int, default=None,
-                    help="FP64 refinement sweeps of the mixed local solve (default 6 for the C5 layouts, else 3: "
-                         "the fewest that keep p and u within 1e-8 of the FP64 form with margin)")
-    ap.add_argument("--ir-tol", type=float, default=1e-9,
-                    help="per-column refinement stop ||r|| <= tol ||b|| (columns retire early; 1e-9, a tenth "
-                         "of the 1e-8 target, leaves the error against the FP64 form unchanged at C2)")
-    ap.add_argument("--cpu-sample", type=int, default=1024, help="subdomains in the CPU-oracle sample")
+                    help="FP64 refinement sweeps of the mixed local solve (default from synth BENCH_SETTINGS: "
+                         "6 for the C5 layouts, else 3, the fewest that keep p and u within 1e-8 with margin)")
+    ap.add_argument("--ir-tol", type=float, default=None,
+                    help="per-column refinement stop ||r|| <= tol ||b|| (default 1e-9, a tenth of the 1e-8 "
+                         "target; columns retire early)")
+    ap.add_argument("--cpu-sample", type=int, default=1024,
+                    help="subdomains in the CPU-oracle sample (workloads the oracle cannot solve in full)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start section")
@@ -320,20 +365,37 @@ def job_rate(units_per_rank, steps, ws, ms):
 
 
 def run_reference(args, w, K, f, ws, rank):
+    """The oracle as the reference arm: per step, the whole staged oracle solve of the
+    workload on all host cores (workloads too large for that: a seeded sample of the
+    local stage per step).  Rank 0 only."""
     if rank != 0:
         return 0
+    import oracle
+    from oracle import mrcm as om
+    prob = oracle.from_workload(w, K=K, f=f)
+    pool = om.make_pool(prob, cpu_cores_used())
+    full = args.workload in FULL_ORACLE
     per_step = max(8, args.cpu_sample // 8)
-    for i in range(args.warmup):
-        oracle_sample(w, K, f, per_step, seed=1000 + i)
-    tot_n, tot_t = 0, 0.0
-    for i in range(args.steps):
-        n, dt = oracle_sample(w, K, f, per_step, seed=i)
-        tot_n += n
-        tot_t += dt
+    try:
+        def step(i):
+            if full:
+                return w.n_sub, oracle_full(w, K, f, pool=pool)[1]
+            return oracle_sample(w, K, f, per_step, seed=i, pool=pool)
+        for i in range(args.warmup):
+            step(1000 + i)
+        tot_n, tot_t = 0, 0.0
+        for i in range(args.steps):
+            n, dt = step(i)
+            tot_n += n
+            tot_t += dt
+    finally:
+        pool.close()
+        pool.join()
     value = tot_n / tot_t
-    sample = (f"local MBF stage (assembly + sparse LU + all m_l right-hand sides + traces) of "
-              f"{per_step} seeded random subdomains per step out of {w.n_sub}; interface and "
-              f"reconstruction stages not included")
+    sample = (f"whole staged oracle solve of the workload per step (local stage, interface assembly + sparse "
+              f"LU solve, reconstruction), {w.n_sub} subdomains" if full else
+              f"local MBF stage of {per_step} seeded random subdomains per step out of {w.n_sub}")
+    sample += f", FP64 numpy/scipy, a process pool over {cpu_cores_used()} host cores (one BLAS thread each)"
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -371,9 +433,13 @@ def main():
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(local)
 
+    from synth.configs import BENCH_SETTINGS
+    bs = BENCH_SETTINGS.get(args.workload, BENCH_SETTINGS["c2"])
     if args.ir_sweeps is None:
-        args.ir_sweeps = 6 if args.workload in ("c5", "c5_slab") else 3
-    wave_gb = args.wave_gb if args.wave_gb is not None else (16.0 if args.workload == "c5" else 0.0)
+        args.ir_sweeps = bs["ir_sweeps"]
+    if args.ir_tol is None:
+        args.ir_tol = bs["ir_tol"]
+    wave_gb = args.wave_gb if args.wave_gb is not None else bs["wave_gb"]
     wave_bytes = int(wave_gb * (1 << 30))
 
     def make(precision):
@@ -405,6 +471,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)        # non-default stream: the solve is graph-captured
     torch.cuda.set_stream(stream)
+    peaks = measure_fp64_peak(peaks, stream)
 
     # reference FP64 GPU solution (untimed), autotuning, warm-up (first graph call captures)
     p64, u64, X64, _ = s64.solve(Kd, fd)
@@ -464,6 +531,8 @@ def main():
         Kh = torch.from_numpy(K).pin_memory()
         fh = torch.from_numpy(f).pin_memory()
         ph = torch.empty((nz, ny, nx), dtype=torch.float64).pin_memory()
+        uh = torch.empty((6, nz, ny, nx), dtype=torch.float64).pin_memory()
+        Xh = torch.empty(outs[0].shape, dtype=torch.float64).pin_memory()
         e2e_steps = max(3, args.steps // 2)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
         if ws > 1:
@@ -476,10 +545,12 @@ def main():
             fd.copy_(fh, non_blocking=True)
             s.solve(Kd, fd, out=outs, graph=True)
             ph.copy_(outs[1], non_blocking=True)
+            uh.copy_(outs[2], non_blocking=True)
+            Xh.copy_(outs[0], non_blocking=True)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         e2e_ms = sum(a.elapsed_time(b) for a, b in evs)
-        e2e = (e2e_ms, e2e_steps, K.nbytes + f.nbytes, ph.numel() * 8)
+        e2e = (e2e_ms, e2e_steps, K.nbytes + f.nbytes, (ph.numel() + uh.numel() + Xh.numel()) * 8)
     clk = clocks.stop()
 
     # max over ranks
@@ -496,18 +567,35 @@ def main():
     swept = s.read_work()
     ranked = sorted(kprof.items(), key=lambda kv: -kv[1][1])
     wkey = args.workload if args.precision == "fp32_ir" else None
-    roof = roofline(ranked[0][0], ranked[0][1][1], ranked[0][1][0], args.steps, sizes, swept, args.precision, peaks, wkey)
-    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks, wkey) for k, v in ranked[1:4]]
+    roof = roofline(ranked[0][0], ranked[0][1][1], ranked[0][1][0], args.steps, sizes, swept, args.precision, peaks,
+                    wkey, sweeps=ranked[0][1][0] / args.steps)
+    if ranked[0][0] == "k_ir_sweep":
+        roof["fp64_view"] = fp64_view(ranked[0][1][1], args.steps, swept, peaks)
+    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks, wkey, sweeps=v[0] / args.steps)
+              for k, v in ranked[1:4]]
     kern_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(sum(x[1] for x in kprof.values()), 1e-9), 4)}
                   for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])}
 
-    cpu = None
+    cpu, vs_oracle = None, None
     if not args.no_cpu_baseline:
-        n_s, dt = oracle_sample(w, K, f, args.cpu_sample)
-        cpu = {"value": round(n_s / dt, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"local MBF stage (assembly + sparse LU + all m_l right-hand sides + traces) of {n_s} "
-                         f"seeded random subdomains of {n_sub} ({dt:.1f} s, one core); interface and "
-                         f"reconstruction stages not included"}
+        if args.workload in FULL_ORACLE:
+            r, dt = oracle_full(w, K, f)
+            cpu = {"value": round(n_sub / dt, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                   "sample": f"whole staged oracle solve of the workload (local stage, interface assembly + "
+                             f"sparse LU solve, reconstruction; {n_sub} subdomains, {dt:.1f} s), FP64 "
+                             f"numpy/scipy, a process pool over {cpu_cores_used()} host cores (one BLAS "
+                             f"thread each)"}
+            pg, ug, Xg = outs[1].cpu().numpy().ravel(), outs[2].cpu().numpy().ravel(), outs[0].cpu().numpy()
+            rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))  # noqa: E731
+            vs_oracle = {"p": rel(pg, r.p), "u": rel(ug, r.u.ravel()), "X": rel(Xg, r.X), "tol": 1e-8}
+            vs_oracle["ok"] = bool(max(vs_oracle["p"], vs_oracle["u"], vs_oracle["X"]) <= 1e-8)
+            del r
+        else:
+            n_s, dt = oracle_sample(w, K, f, max(64, n_sub // 100))
+            cpu = {"value": round(n_s / dt, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                   "sample": f"local MBF stage (assembly, sparse LU, all m_l right-hand sides, traces, interface "
+                             f"block) of {n_s} seeded random subdomains of {n_sub} ({dt:.1f} s) over "
+                             f"{cpu_cores_used()} host cores; interface solve and reconstruction not included"}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
@@ -526,6 +614,7 @@ def main():
                       "ms_per_step": round(ms64 / steps64, 4)} if ref_kind == "fp64_gpu" else None),
         "rel_err_vs_fp64": {"p": rel_p, "u": rel_u, "tol": 1e-8, "ok": bool(rel_p <= 1e-8 and rel_u <= 1e-8),
                             "reference": ref_kind},
+        "rel_err_vs_oracle": vs_oracle,
         "status": status, "mass_residual_max": mres,
         "roofline": dict(roof, measured="CUDA events around each kernel on its launching stream, "
                                           "over a profiled non-graph pass of the same steps"),

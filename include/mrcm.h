@@ -265,6 +265,13 @@ mrcm_status mrcm_profile(mrcm_handle* h, int enable);
  * the count.  INVALID_ARG if buf is too small (the text is truncated). */
 mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long* launches);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA), the denominator of the library's FP64 roofline fractions (no
+ * counterpart in the paper).  Runs a short kernel of independent FMA chains
+ * on every SM on `stream` and synchronises it; *tflops (host) receives the
+ * best of three timed launches. */
+mrcm_status mrcm_measure_fp64_peak(void* stream, double* tflops);
+
 /* Allocation-free local solve of one box subdomain (the paper has no
  * counterpart: this is a deployment variant of the local factor and solve).
  * It is for callers that cannot allocate device memory -- code whose host
@@ -293,7 +300,9 @@ mrcm_status mrcm_profile_report(mrcm_handle* h, char* buf, size_t len, long long
  * return MRCM_ERR_OOM.  At least one side must be Robin or Dirichlet
  * (MRCM_ERR_INVALID_ARG otherwise).  The first call on a device looks up the
  * scratch address and sets the kernel's shared-memory limit; make that first
- * call before any stream capture.  Every call on a device shares the one
+ * call before any stream capture.  The looked-up address is kept for the
+ * life of the process; calling this entry point again after cudaDeviceReset
+ * is not supported.  Every call on a device shares the one
  * scratch array (nothing in it is read before the same call writes it), so
  * calls that overlap on the GPU (different streams, or host threads) race:
  * serialise them. */

@@ -211,26 +211,49 @@ class MRCMResult:
     mass_residual_max: float
 
 
-def assemble_interface(prob: Problem, bases, locs, Qs):
-    """A^int and b^int of Eq. interface_problem (before any pinning)."""
+def interface_entries(NV, lp: LocalProblem, Q):
+    """One subdomain's block of A^int and b^int (Eq. sec2-int-APP, sec2-int-AUU, sec2-int-bU).
+
+    The faces' traces are summed over each basis function's faces into the
+    subdomain's local interface block E (2|I^l| x 2|I^l|, rows and columns
+    ordered [P of I^l, U of I^l]) and right-hand side e; returned as COO
+    triplets (rows, cols, vals) and (b_rows, b_vals) in global numbering.  The
+    interface system is the sum of these blocks over all subdomains.
+    """
+    m = len(lp.I)
+    E = np.zeros((2 * m, 2 * m))
+    e = np.zeros(2 * m)
+    for r, fc in enumerate(lp.faces):
+        k = fc.col
+        E[k, :] += Q[r, :2 * m]                          # F row: sum of fluxes
+        E[m + k, :] += fc.beta * fc.s * Q[r, :2 * m]     # U row: sum of beta s fluxes
+        E[m + k, m + k] -= fc.beta * fc.area             # U row: - beta A_f pi^u
+        e[k] -= Q[r, -1]
+        e[m + k] -= fc.beta * fc.s * Q[r, -1]
+    I = np.asarray(lp.I, dtype=np.int64)
+    g = np.concatenate([I, NV + I])
+    return np.repeat(g, 2 * m), np.tile(g, 2 * m), E.ravel(), g, e
+
+
+def assemble_interface(prob: Problem, bases, locs, Qs, entries=None):
+    """A^int and b^int of Eq. interface_problem (before any pinning).
+
+    ``entries`` may hold the subdomains' ``interface_entries`` already computed
+    (by a worker pool); they are summed in subdomain order either way.
+    """
     NV = len(bases)
-    rows, cols, vals = [], [], []
+    if entries is None:
+        entries = [interface_entries(NV, lp, Q) for lp, Q in zip(locs, Qs)]
     b = np.zeros(2 * NV)
-    for lp, Q in zip(locs, Qs):
-        m = len(lp.I)
-        for r, fc in enumerate(lp.faces):
-            i = fc.basis
-            for c in range(m):
-                j = lp.I[c]
-                rows += [i, i, NV + i, NV + i]
-                cols += [j, NV + j, j, NV + j]
-                vals += [Q[r, c], Q[r, m + c],
-                         fc.beta * fc.s * Q[r, c], fc.beta * fc.s * Q[r, m + c]]
-            rows.append(NV + i)
-            cols.append(NV + i)
-            vals.append(-fc.beta * fc.area)
-            b[i] -= Q[r, -1]
-            b[NV + i] -= fc.beta * fc.s * Q[r, -1]
+    for (_, _, _, br, bv) in entries:
+        np.add.at(b, br, bv)
+    if entries:
+        rows = np.concatenate([x[0] for x in entries])
+        cols = np.concatenate([x[1] for x in entries])
+        vals = np.concatenate([x[2] for x in entries])
+    else:
+        rows = cols = np.zeros(0, dtype=np.int64)
+        vals = np.zeros(0)
     A = sp.csr_matrix((vals, (rows, cols)), shape=(2 * NV, 2 * NV))
     A.sum_duplicates()
     return A, b
@@ -279,25 +302,30 @@ def reconstruct_local_resolve(lp: LocalProblem, X, NV):
     return spla.splu(lp.A.tocsc()).solve(rhs)
 
 
-def local_velocities(prob: Problem, lp: LocalProblem, p_loc, X, NV, u):
-    """Fill the per-cell face velocities of subdomain l into u (6, nz, ny, nx).
+def local_velocity_entries(prob: Problem, lp: LocalProblem, p_loc, X, NV):
+    """The per-cell face velocities of subdomain l as (row, flat cell, value) triplets.
 
     Interior faces by Eq. two_point; Gamma faces by the Robin flux with the final
     Robin data, each side keeping its own value; walls 0 or the Dirichlet flux.
+    Rows index the six faces (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) of a cell.
     """
-    uf = u.reshape(6, -1)
+    rows, cells, vals = [], [], []
     for (c, d, a, T) in lp.interior:
         vel = T * (p_loc[c] - p_loc[d]) / prob.face_area(a)
-        uf[2 * a + 1, lp.cells[c]] = vel
-        uf[2 * a, lp.cells[d]] = vel
+        rows += [2 * a + 1, 2 * a]
+        cells += [lp.cells[c], lp.cells[d]]
+        vals += [vel, vel]
     g = robin_data_final(lp, X, NV) if lp.faces else []
     for r, fc in enumerate(lp.faces):
         q_out = fc.T_R * (p_loc[fc.local_cell] - g[r])
         vel = q_out / fc.area
         if fc.s == +1:   # outward of l is +axis: the cell's high face
-            uf[2 * fc.axis + 1, lp.cells[fc.local_cell]] = vel
+            rows.append(2 * fc.axis + 1)
+            vals.append(vel)
         else:            # outward of l is -axis: the cell's low face
-            uf[2 * fc.axis, lp.cells[fc.local_cell]] = -vel
+            rows.append(2 * fc.axis)
+            vals.append(-vel)
+        cells.append(lp.cells[fc.local_cell])
     # Dirichlet walls
     nx, ny, nz = prob.n
     Kflat = prob.K.reshape(3, -1)
@@ -309,9 +337,20 @@ def local_velocities(prob: Problem, lp: LocalProblem, p_loc, X, NV, u):
             for c, gc in enumerate(lp.cells):
                 co = [gc % nx, (gc // nx) % ny, gc // (nx * ny)]
                 if (side == 0 and co[a] == 0):
-                    uf[2 * a, gc] = -2.0 * Kflat[a, gc] * (p_loc[c] - gval) / prob.h[a]
+                    rows.append(2 * a)
+                    cells.append(gc)
+                    vals.append(-2.0 * Kflat[a, gc] * (p_loc[c] - gval) / prob.h[a])
                 if (side == 1 and co[a] == prob.n[a] - 1):
-                    uf[2 * a + 1, gc] = -2.0 * Kflat[a, gc] * (gval - p_loc[c]) / prob.h[a]
+                    rows.append(2 * a + 1)
+                    cells.append(gc)
+                    vals.append(-2.0 * Kflat[a, gc] * (gval - p_loc[c]) / prob.h[a])
+    return np.asarray(rows, dtype=np.int64), np.asarray(cells, dtype=np.int64), np.asarray(vals, dtype=float)
+
+
+def local_velocities(prob: Problem, lp: LocalProblem, p_loc, X, NV, u):
+    """Fill the per-cell face velocities of subdomain l into u (6, nz, ny, nx)."""
+    rows, cells, vals = local_velocity_entries(prob, lp, p_loc, X, NV)
+    u.reshape(6, -1)[rows, cells] = vals
 
 
 def mass_residual(prob: Problem, u):
@@ -322,26 +361,122 @@ def mass_residual(prob: Problem, u):
     return div - prob.f * prob.cell_volume
 
 
-def solve_mrcm(prob: Problem, option=1, keep=True) -> MRCMResult:
-    """Run Alg. MRCM end to end on the CPU in FP64."""
+# ---- worker pool (Sec. 8(d) oracle timing: subdomains are independent, one process per core)
+_POOL_STATE = {}
+
+
+def _pool_init(prob, sub_bases, face_basis, NV):
+    _POOL_STATE.update(prob=prob, sub_bases=sub_bases, face_basis=face_basis, NV=NV)
+
+
+def _pool_local(ls):
+    """Local stage of a chunk of subdomains: A^H_l, all MBF columns, traces, interface block."""
+    st = _POOL_STATE
+    out = []
+    for l in ls:
+        lp = local_problem(st["prob"], l, st["sub_bases"], st["face_basis"])
+        Xl = solve_local(lp)
+        Q = traces(lp, Xl)
+        out.append((lp if st.get("keep_locals") else None, Xl, Q, interface_entries(st["NV"], lp, Q)))
+    return out
+
+
+def _pool_reconstruct(task):
+    """Reconstruction of a chunk of subdomains (the local problem is re-assembled
+    where it was not kept): p^l and the face-velocity triplets."""
+    items, X, option = task
+    st = _POOL_STATE
+    out = []
+    for l, lp, Xl in items:
+        if lp is None:
+            lp = local_problem(st["prob"], l, st["sub_bases"], st["face_basis"])
+        pl = reconstruct_local(lp, Xl, X, st["NV"]) if option == 1 else reconstruct_local_resolve(lp, X, st["NV"])
+        out.append((lp.cells, pl, local_velocity_entries(st["prob"], lp, pl, X, st["NV"])))
+    return out
+
+
+def _chunks(seq, n):
+    return [seq[i:i + n] for i in range(0, len(seq), n)]
+
+
+def make_pool(prob: Problem, processes):
+    """A pool of ``processes`` spawned workers holding ``prob`` (one BLAS thread each).
+
+    Pass it to ``solve_mrcm(pool=...)`` to reuse it over several solves of the
+    same problem; close it with ``pool.close(); pool.join()``.
+    """
+    import multiprocessing as mp
+    import os
+    bases, sub_bases, face_basis = build_bases(prob)
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        pool = mp.get_context("spawn").Pool(processes, initializer=_pool_init,
+                                            initargs=(prob, sub_bases, face_basis, len(bases)))
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    pool.n_procs = processes
+    return pool
+
+
+def solve_mrcm(prob: Problem, option=1, keep=True, processes=None, pool=None) -> MRCMResult:
+    """Run Alg. MRCM end to end on the CPU in FP64.
+
+    ``processes`` > 1 runs the per-subdomain work (local problems, MBFs,
+    traces, interface blocks, reconstruction) in a pool of that many spawned
+    processes, one BLAS thread each (or ``pool``, from ``make_pool`` for this
+    problem); the arithmetic and the order of every sum are the same as with
+    one process.  The pool does not ship the local problems back (the
+    reconstruction re-assembles them), so the result's ``locals`` is empty
+    then.
+    """
     bases, sub_bases, face_basis = build_bases(prob)
     NV = len(bases)
-    locs, mbfs, Qs = [], [], []
-    for l in range(prob.nsub):
-        lp = local_problem(prob, l, sub_bases, face_basis)
-        Xl = solve_local(lp)
-        locs.append(lp)
-        mbfs.append(Xl)
-        Qs.append(traces(lp, Xl))
-    A_raw, b_raw = assemble_interface(prob, bases, locs, Qs)
-    A, b = pin_interface(prob, A_raw, b_raw)
-    X = solve_interface(A, b)
-    p = np.zeros(prob.ncells)
-    u = np.zeros((6,) + prob.f.shape)
-    for lp, Xl in zip(locs, mbfs):
-        pl = reconstruct_local(lp, Xl, X, NV) if option == 1 else reconstruct_local_resolve(lp, X, NV)
-        p[lp.cells] = pl
-        local_velocities(prob, lp, pl, X, NV, u)
+    locs, mbfs, Qs, entries = [], [], [], []
+    own_pool = False
+    if pool is None and processes and processes > 1 and prob.nsub > 1:
+        pool = make_pool(prob, processes)
+        own_pool = True
+    nproc = getattr(pool, "n_procs", 1) if pool else 1
+    try:
+        chunk = max(1, prob.nsub // (4 * nproc)) if pool else prob.nsub
+        if pool:
+            parts = pool.map(_pool_local, _chunks(list(range(prob.nsub)), chunk))
+        else:
+            _pool_init(prob, sub_bases, face_basis, NV)
+            _POOL_STATE["keep_locals"] = True
+            parts = [_pool_local(list(range(prob.nsub)))]
+        for part in parts:
+            for lp, Xl, Q, ent in part:
+                if lp is not None:
+                    locs.append(lp)
+                mbfs.append(Xl)
+                Qs.append(Q)
+                entries.append(ent)
+        A_raw, b_raw = assemble_interface(prob, bases, locs, Qs, entries)
+        A, b = pin_interface(prob, A_raw, b_raw)
+        X = solve_interface(A, b)
+        p = np.zeros(prob.ncells)
+        u = np.zeros((6,) + prob.f.shape)
+        items = [(l, locs[l] if locs else None, mbfs[l]) for l in range(prob.nsub)]
+        tasks = [(c, X, option) for c in _chunks(items, chunk)]
+        rparts = pool.map(_pool_reconstruct, tasks) if pool else [_pool_reconstruct(t) for t in tasks]
+        uf = u.reshape(6, -1)
+        for part in rparts:
+            for cells_l, pl, (rows, cells, vals) in part:
+                p[cells_l] = pl
+                uf[rows, cells] = vals
+    finally:
+        if own_pool:
+            pool.close()
+            pool.join()
+        if not pool:
+            _POOL_STATE.clear()
     shift = 0.0 if prob.has_dirichlet() else p.mean()
     p = p - shift
     res = mass_residual(prob, u)

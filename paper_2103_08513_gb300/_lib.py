@@ -85,6 +85,7 @@ SIGNATURES = {
     "mrcm_net_destroy": (None, [C.c_void_p]),
     "mrcm_net_samples": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "mrcm_pcg_mbf": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "mrcm_measure_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrcm_destroy": (None, [C.c_void_p]),
     "mrcm_last_error": (C.c_char_p, [C.c_void_p]),
 }

@@ -204,7 +204,11 @@ constexpr size_t kNaSmem = sizeof(double) * kNaMaxBlock * (kNaMaxBlock + 1) / 2;
 // Device addresses of the scratch array and the pivot flag, looked up once
 // per device (with that device current) on the first call there.  In host
 // code the names of __device__ variables are host-side stand-ins, not device
-// addresses, so the kernel gets the looked-up pointers.
+// addresses, so the kernel gets the looked-up pointers.  The cached addresses
+// (and the kernel's shared-memory attribute) belong to the device's primary
+// context as it was at that first call: after cudaDeviceReset the module is
+// loaded afresh and they are stale, so the entry point does not support use
+// after a device reset in the same process.
 std::mutex g_mu;
 double* g_scratch_ptr[64] = {};
 int* g_flag_ptr[64] = {};
@@ -247,6 +251,9 @@ extern "C" mrcm_status mrcm_box_solve_noalloc(const int box[3], const double h[3
         a.sz[ax] = box[ax];
         a.h[ax] = h[ax];
     }
+    // the fixed scratch bounds the problem: larger boxes are refused, never truncated
+    // (the cell count is formed in 64 bits, before any product is narrowed to int)
+    if ((long long)box[0] * box[1] * box[2] > kNaMaxCells) return MRCM_ERR_OOM;
     for (int sd = 0; sd < 6; ++sd) {
         if (side_type[sd] < 0 || side_type[sd] > 2) return MRCM_ERR_INVALID_ARG;
         a.side_type[sd] = side_type[sd];
@@ -267,7 +274,6 @@ extern "C" mrcm_status mrcm_box_solve_noalloc(const int box[3], const double h[3
     a.b = box[a.ua] * box[a.va];
     a.ns = box[sa];
     a.N = a.b * a.ns;
-    // the fixed scratch bounds the problem: larger boxes are refused, never truncated
     if (a.N > kNaMaxCells || a.b > kNaMaxBlock || (long long)a.ns * a.b * a.b > kNaMaxW) return MRCM_ERR_OOM;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -29,7 +29,7 @@ def lib():
 def declared_symbols():
     hdr = open(os.path.join(ROOT, "include", "mrcm.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(mrcm_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(mrcm_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -188,3 +188,16 @@ def test_query_tuning_reports_the_defaults_without_a_gpu(lib):
     assert lib.mrcm_query_tuning(h, None, None, None, None) == 0
     assert lib.mrcm_query_tuning(None, None, None, None, None) == 1
     lib.mrcm_destroy(h)
+
+
+@pytest.mark.parametrize("box", [(65536, 65536, 65536), (4097, 1, 1), (1, 1, 1 << 20), (8, 16, 17), (12, 12, 12)])
+def test_noalloc_rejects_oversized_boxes_before_any_device_work(lib, box):
+    """Boxes beyond the fixed scratch (4096 cells, slab block <= 128, edge x block^2 <= 262144)
+    return MRCM_ERR_OOM from the host-side checks, before a CUDA call is made; products of
+    the edges that overflow 32 bits are not allowed to wrap past the checks."""
+    dummy = (C.c_double * 4)()
+    ptr = C.cast(dummy, C.c_void_p)
+    flag = (C.c_int * 1)()
+    rc = lib.mrcm_box_solve_noalloc((C.c_int * 3)(*box), (C.c_double * 3)(1.0, 1.0, 1.0), (C.c_int * 6)(*[1] * 6),
+                                    ptr, ptr, ptr, ptr, ptr, ptr, C.cast(flag, C.c_void_p), None)
+    assert rc == 7                           # MRCM_ERR_OOM

@@ -15,6 +15,38 @@ def _net(D, H, W, hidden, layers, seed=0, batch=8):
     return WarmStartNet(D, H, W, hidden=hidden, layers=layers, batch=batch, seed=seed)
 
 
+def _oracle_params(net, hidden, layers):
+    """The network's parameters as the oracle's layers: BF16 weights (as the
+    convolutions use them), FP32 master biases."""
+    cin = [4] + [hidden] * (layers - 1)
+    cout = [hidden] * (layers - 1) + [1]
+    wb = net.bf16_weights().cpu().numpy().astype(np.float64)
+    master = net.master.cpu().numpy().astype(np.float64)
+    flat = wb.copy()
+    off = 0
+    for ci, co in zip(cin, cout):
+        off += co * ci * 27
+        flat[off: off + co] = master[off: off + co]
+        off += co
+    return conv3d.unflatten(flat, cin, cout)
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5, 8, 3, 3), (5, 10, 10, 32, 4, 37)])
+def test_gpu_forward_matches_oracle_elementwise(shape):
+    """Inference output, element by element, against the oracle's FP64 forward pass
+    with the same (BF16-rounded) weights; the GPU accumulates in FP32."""
+    D, H, W, hidden, layers, batch = shape
+    net = _net(D, H, W, hidden, layers, seed=2, batch=batch)
+    rng = np.random.default_rng(7)
+    x = torch.from_numpy(rng.normal(size=(batch, 4, D, H, W)).astype(np.float32)).cuda()
+    y = net.forward(x)
+    torch.cuda.synchronize()
+    params = _oracle_params(net, hidden, layers)
+    yref = conv3d.forward(params, x.cpu().numpy().astype(np.float64))[-1]
+    got = y.cpu().numpy().astype(np.float64).reshape(yref.shape)
+    assert np.abs(got - yref).max() <= 2e-6
+
+
 def test_gpu_gradient_matches_oracle():
     D, H, W, hidden, layers = 3, 4, 5, 8, 3
     net = _net(D, H, W, hidden, layers)

@@ -121,6 +121,9 @@ CASES = [
          beta_mode=BETA_ALPHA_H_OVER_K, alpha=0.7),
     dict(n=(8, 4, 4), edges=([2, 3, 3], [4], [2, 2]), patch=((1, 2), (1, 1), (3, 1)), beta_const=0.3,
          h=(0.5, 1.0, 2.0)),
+    # beta = alpha H / K with non-unit anisotropic h: H in length units, each side's own K
+    dict(n=(6, 5, 4), edges=([2, 4], [3, 2], [1, 3]), patch=((2, 2), (3, 0), (1, 2)),
+         beta_mode=BETA_ALPHA_H_OVER_K, alpha=1.3, h=(0.4, 1.7, 0.9), sigma=1.5),
 ]
 
 
@@ -235,3 +238,106 @@ def test_reconstruction_options_agree(kw):
     r2 = oracle.solve_mrcm(prob, option=2)
     assert np.abs(r1.p - r2.p).max() <= 1e-12 * np.abs(r1.p).max()
     assert np.abs(r1.u - r2.u).max() <= 1e-12 * np.abs(r1.u).max()
+
+
+# ---------------------------------------------------------------- beta = alpha H / K (Eq. Robin_par)
+def _two_by_two_closed_form(h, kL, kR, kyL, kyR, alpha, q):
+    """Hand-derived MRCM solution of a 2 x 2 x 1 grid cut into two 1 x 2 x 1 subdomains.
+
+    One x-interface with two fine faces forms a single patch (coarse patch).
+    Cells: a = (0,0), b = (0,1) on the left, c = (1,0), d = (1,1) on the right;
+    sources q = (q_a, q_b, q_c, q_d) with zero sum; every wall no-flow.
+
+    Each local problem (Eq. localomegaint) with Robin data g has the solution
+    g + w, where w solves the 2 x 2 system [[T_y + T_R, -T_y], [-T_y, T_y + T_R]] w = q
+    (constants pass through the y-coupling).  Its sum and difference give
+    w_a + w_b = (q_a + q_b) / T_R and w_a - w_b = (q_a - q_b) / (2 T_y + T_R).
+    The F row (Eq. weakcont_f) is the zero total source (pinned by pi^p = 0);
+    the U row (Eq. weakcont_p) with Q_L = q_a + q_b = -Q_R reads
+    beta_L (Q_L - 2 A_x pi^u) + beta_R (Q_L - 2 A_x pi^u) = 0, so
+    pi^u = Q_L / (2 A_x).  Robin data: g_L = pi^p - beta_L pi^u (s = +1),
+    g_R = pi^p + beta_R pi^u (s = -1).  beta_side = alpha H / K_x of the side's
+    own cell, H = one cell's length along x (reading R3).
+    """
+    hx, hy, hz = h
+    Ax = hy * hz
+    bL, bR = alpha * hx / kL, alpha * hx / kR
+    TRL, TRR = Ax / (hx / (2 * kL) + bL), Ax / (hx / (2 * kR) + bR)
+    TyL, TyR = hx * hz * kyL / hy, hx * hz * kyR / hy
+    qa, qb, qc, qd = q
+
+    def local(Ty, TR, q1, q2):
+        S = (q1 + q2) / TR
+        D = (q1 - q2) / (2 * Ty + TR)
+        return (S + D) / 2, (S - D) / 2
+
+    wa, wb = local(TyL, TRL, qa, qb)
+    wc, wd = local(TyR, TRR, qc, qd)
+    piu = (qa + qb) / (2 * Ax)
+    gL, gR = -bL * piu, bR * piu
+    p = np.array([gL + wa, gR + wc, gL + wb, gR + wd])    # global order: x fastest
+    return p - p.mean(), np.array([0.0, piu]), (TRL * wa / Ax, TRL * wb / Ax)
+
+
+def test_beta_alpha_H_over_K_closed_form():
+    """beta = alpha H / K changes the answer, and the oracle matches the hand solution.
+
+    Non-unit anisotropic h (H in length units differs from H in cells), K_x
+    differing across Gamma (the side's own K differs from the neighbour's), and
+    a two-face patch (the Robin data is not the fine-face trace).
+    """
+    h = (0.5, 2.0, 0.7)
+    kL, kR, kyL, kyR, alpha = 2.0, 0.25, 0.6, 3.0, 0.8
+    q = (1.0, 0.0, 0.0, -1.0)
+    V = h[0] * h[1] * h[2]
+    K = np.empty((3, 1, 2, 2))
+    K[0, 0, :, 0], K[0, 0, :, 1] = kL, kR
+    K[1, 0, :, 0], K[1, 0, :, 1] = kyL, kyR
+    K[2] = 1.0
+    f = np.array([[[q[0], q[2]], [q[1], q[3]]]]) / V     # [z][y][x]: a, c on y = 0; b, d on y = 1
+    prob = Problem(n=(2, 2, 1), h=h, edges=([1, 1], [2], [1]), patch=((0, 0),) * 3, K=K, f=f,
+                   beta_mode=1, alpha=alpha)
+    p_ref, X_ref, (va, vb) = _two_by_two_closed_form(h, kL, kR, kyL, kyR, alpha, q)
+    r = oracle.solve_mrcm(prob)
+    assert np.abs(r.p - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
+    assert np.abs(r.X - X_ref).max() <= 1e-12 * np.abs(X_ref).max()
+    # Gamma velocities seen from the left cells (x-high faces of a and b)
+    assert abs(r.u[1, 0, 0, 0] - va) <= 1e-12 * abs(va)
+    assert abs(r.u[1, 0, 1, 0] - vb) <= 1e-12 * abs(vb)
+    # the monolithic assembly (written separately) agrees
+    pm, Xm = oracle.solve_monolithic(prob)
+    assert np.abs(pm - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
+    # beta matters here: the answer with a constant beta is different
+    p_c, _, _ = _two_by_two_closed_form(h, kL, kR, kyL, kyR, 0.0, q)
+    assert np.abs(p_c - p_ref).max() > 1e-2 * np.abs(p_ref).max()
+
+
+def test_relative_errors_weighting():
+    """Eq. of Sec. "Numerical setup": volume-weighted L2 pressure error and the
+    K^-1-weighted velocity error with the trapezoidal rule per cell."""
+    rng = np.random.default_rng(11)
+    n = (3, 2, 2)
+    h = (0.5, 1.5, 2.0)
+    V = h[0] * h[1] * h[2]
+    K = np.exp(rng.normal(size=(3, 2, 2, 3)))
+    prob = Problem(n=n, h=h, edges=([3], [2], [2]), patch=((0, 0),) * 3, K=K, f=np.zeros((2, 2, 3)))
+    p_ref = np.ones(12)
+    p = p_ref.copy()
+    p[5] += 0.3
+    u_ref = np.ones((6, 2, 2, 3))
+    u = u_ref.copy()
+    u[3, 1, 0, 2] += 0.25                          # y-high face of cell (2, 0, 1)
+    ep, ev = oracle.relative_errors(prob, p, u, p_ref, u_ref)
+    assert abs(ep - np.sqrt(V * 0.09) / np.sqrt(12 * V)) <= 1e-14
+    num = 0.5 * V * 0.25 ** 2 / K[1, 1, 0, 2]
+    den = sum(2 * 0.5 * V * (1.0 / K[a]).sum() for a in range(3))     # two faces per axis and cell
+    assert abs(ev - np.sqrt(num / den)) <= 1e-14
+
+
+def test_pooled_oracle_equals_serial():
+    """The worker pool changes where the per-subdomain work runs, not what it computes."""
+    prob = _prob(**CASES[1])
+    r1 = oracle.solve_mrcm(prob)
+    r2 = oracle.solve_mrcm(prob, processes=2)
+    assert np.array_equal(r1.p, r2.p) and np.array_equal(r1.u, r2.u) and np.array_equal(r1.X, r2.X)
+    assert (r1.A_int_raw != r2.A_int_raw).nnz == 0

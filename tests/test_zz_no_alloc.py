@@ -7,7 +7,8 @@ cudaMalloc cannot use the workspace-based entry points.  For them the library
 offers mrcm_box_solve_noalloc, which keeps its scratch in a fixed array inside
 the library.  This test calls it through the C ABI and checks it against the
 MBF columns that the regular entry points (mrcm_factor_local +
-mrcm_solve_mbf) compute for the same subdomain, on two calls in a row.
+mrcm_solve_mbf) compute for the same subdomain, and against the CPU
+oracle's local solve, on two calls in a row.
 """
 import ctypes as C
 
@@ -45,6 +46,7 @@ def _call(lib, box, h, side, K, f, g, beta, stream):
 
 def test_noalloc_matches_regular_local_solve():
     import oracle
+    from oracle.mrcm import local_problem, solve_local
     from oracle.problem import build_bases
     from paper_2103_08513_gb300 import MRCM, _lib, build
     from synth.configs import small
@@ -54,7 +56,7 @@ def test_noalloc_matches_regular_local_solve():
     w = small(n=(9, 7, 5), edges=([4, 5], [2, 3, 2], [5]), patch=((2, 2), (3, 2), (2, 3)), beta_const=0.7,
               h=(0.5, 1.0, 2.0))
     prob = oracle.from_workload(w)
-    bases, sub_bases, _ = build_bases(prob)
+    bases, sub_bases, face_basis = build_bases(prob)
     s = MRCM(w.n, w.edges, w.patch, h=w.h, beta_const=w.beta_const, precision="fp64")
     K = torch.from_numpy(prob.K).cuda()
     f = torch.from_numpy(prob.f).cuda()
@@ -104,9 +106,11 @@ def test_noalloc_matches_regular_local_solve():
     assert rc == 0
     torch.cuda.synchronize()
     assert int(fl1.cpu()[0]) == 0 and int(fl2.cpu()[0]) == 0
+    Xo = solve_local(local_problem(prob, l, sub_bases, face_basis))     # oracle columns, same cell order
     for got, col in ((p1, 0), (p2, m - 1)):
         want = ref[col]
         assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-10 * np.linalg.norm(want)
+        assert np.linalg.norm(got.cpu().numpy() - Xo[:, col]) <= 1e-10 * np.linalg.norm(Xo[:, col])
     # conservation of the particular solution: the outward Robin fluxes carry the sources out
     vol = w.h[0] * w.h[1] * w.h[2]
     assert abs(q2.cpu().numpy().sum() - prob.f[sl].sum() * vol) <= 1e-10 * max(1.0, np.abs(prob.f[sl]).sum() * vol)
@@ -124,3 +128,54 @@ def test_noalloc_rejects_boxes_beyond_its_scratch():
     g = torch.zeros(nf, dtype=torch.float64, device="cuda")
     rc, *_ = _call(lib, box, (1.0, 1.0, 1.0), [1] * 6, K, f, g, g, torch.cuda.current_stream().cuda_stream)
     assert rc == 7                            # MRCM_ERR_OOM
+
+
+def test_noalloc_dirichlet_sides_at_the_scratch_limits():
+    """A box at the documented limits (8 x 16 x 16: slab block 128, 16 slabs,
+    16 x 128^2 = 262144 block-inverse entries) with Dirichlet, Robin and no-flow
+    sides, against the oracle's local solve (particular and P-MBF columns)."""
+    import oracle
+    from oracle.mrcm import local_problem, solve_local
+    from oracle.problem import DIRICHLET, Problem, build_bases
+    from paper_2103_08513_gb300 import _lib, build
+    from synth.fields import lognormal_K
+
+    build()
+    lib = _lib.load()
+    n = (16, 16, 16)
+    h = (0.7, 1.0, 1.3)
+    K = lognormal_K((16, 16, 16), 1.5, 4.0, 0.2, seed=3)
+    rng = np.random.default_rng(4)
+    f = rng.normal(size=(16, 16, 16))
+    bc_t = ((DIRICHLET, 0), (0, 0), (0, DIRICHLET))
+    bc_v = ((1.0, 0.0), (0.0, 0.0), (0.0, -0.5))
+    prob = Problem(n=n, h=h, edges=([8, 8], [16], [16]), patch=((0, 0),) * 3, K=K, f=f, beta_const=0.4,
+                   bc_type=bc_t, bc_value=bc_v)
+    bases, sub_bases, face_basis = build_bases(prob)
+    lp = local_problem(prob, 0, sub_bases, face_basis)     # the box x in [0, 8): Robin on its x-high side
+    Xo = solve_local(lp)
+    box = [8, 16, 16]
+    offs, nf = _side_faces(box)
+    side = [2, 1, 0, 0, 0, 2]                 # x-lo Dirichlet, x-hi Robin, y no-flow, z-lo no-flow, z-hi Dirichlet
+    Kb = torch.from_numpy(np.ascontiguousarray(K[:, :, :, :8])).cuda()
+    fb = torch.from_numpy(np.ascontiguousarray(f[:, :, :8])).cuda()
+    beta = torch.full((nf,), 0.4, dtype=torch.float64, device="cuda")
+    g_part = np.zeros(nf)
+    g_part[offs[0]:offs[1]] = 1.0             # x-lo wall pressure
+    g_part[offs[5]:] = -0.5                   # z-hi wall pressure
+    g_mbf = np.zeros(nf)
+    g_mbf[offs[1]:offs[2]] = 1.0              # the whole x-high face is the one basis function
+    stream = torch.cuda.current_stream().cuda_stream
+    rc1, p1, q1, fl1 = _call(lib, box, h, side, Kb, fb, torch.from_numpy(g_part).cuda(), beta, stream)
+    rc2, p2, q2, fl2 = _call(lib, box, h, side, Kb, torch.zeros_like(fb), torch.from_numpy(g_mbf).cuda(),
+                             beta, stream)
+    assert rc1 == 0 and rc2 == 0
+    torch.cuda.synchronize()
+    assert int(fl1.cpu()[0]) == 0 and int(fl2.cpu()[0]) == 0
+    for got, col in ((p1, Xo.shape[1] - 1), (p2, 0)):
+        want = Xo[:, col]
+        assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-10 * np.linalg.norm(want)
+    # every outward flux leaves through the Robin and Dirichlet faces: their sum is the source
+    V = h[0] * h[1] * h[2]
+    total = f[:, :, :8].sum() * V
+    assert abs(q1.cpu().numpy().sum() - total) <= 1e-10 * np.abs(f[:, :, :8]).sum() * V
