@@ -206,6 +206,30 @@ mrcm_status mrcm_solve_interface(mrcm_handle* h, double* X, void* ws, void* stre
 mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double* u,
                              double* mass_residual_max, void* ws, void* stream);
 
+/* Mean velocity post-processing (Eq. locprob_submean; the "Mean" method of
+ * the paper's two-phase section), for a transport step that needs a velocity
+ * conservative on the fine grid.  On every fine Gamma face the two sides'
+ * velocities of `u` are averaged, Ubar = (u+ + u-)/2; every subdomain then
+ * re-solves its TPFA problem (Eq. aijk, harmonic means) with Neumann data:
+ * Ubar.n on its Gamma faces and u.n on the domain walls.  The pure Neumann
+ * matrix is factored and solved like the local problems (cfg.precision;
+ * mixed precision with max(ir_max_sweeps, 8) FP64 refinement sweeps); the
+ * subdomain's pressure constant is fixed internally (it does not affect the
+ * velocity).
+ *  u      device FP64 [6][nz][ny][nx]: the multiscale velocity as written by
+ *         mrcm_reconstruct (input)
+ *  u_out  device FP64 [6][nz][ny][nx] (output, must not overlap u): TPFA of the
+ *         new pressure on interior faces, Ubar on Gamma faces (one value, both
+ *         sides), u on walls
+ *  mass_residual_max  device FP64 [1] (output, may be NULL): max over cells of
+ *         |sum of outward fluxes of u_out - f V|
+ * Needs a completed solve (after mrcm_reconstruct or mrcm_solve); it
+ * overwrites the local coefficients, factors and MBF columns, so the next
+ * solve must start again from mrcm_factor_local (MRCM_ERR_STATE otherwise).
+ * Unconverged refinement columns are reported by mrcm_read_status. */
+mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u_out, double* mass_residual_max,
+                                      void* ws, void* stream);
+
 /* The whole pressure solve: mrcm_factor_local, mrcm_solve_mbf,
  * mrcm_assemble_interface, mrcm_solve_interface and mrcm_reconstruct in
  * order (arguments as there).  With flags & MRCM_SOLVE_GRAPH the sequence is

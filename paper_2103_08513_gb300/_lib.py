@@ -65,6 +65,7 @@ SIGNATURES = {
     "mrcm_assemble_interface": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrcm_solve_interface": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrcm_reconstruct": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
+    "mrcm_postprocess_velocity": (C.c_int, [C.c_void_p] * 6),
     "mrcm_read_status": (C.c_int, [C.c_void_p, C.c_void_p] + [C.POINTER(C.c_int)] * 4),
     "mrcm_read_work": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "mrcm_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t]),

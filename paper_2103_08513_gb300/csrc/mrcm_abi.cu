@@ -304,6 +304,26 @@ mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double*
     return after_launch(h, rc, "mrcm_reconstruct");
 }
 
+mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u_out, double* mres, void* ws,
+                                      void* stream) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (!u || !u_out) return fail(h, MRCM_ERR_INVALID_ARG, "u and u_out must be non-NULL");
+    const size_t ub = (size_t)6 * h->t.n_cells * sizeof(double);
+    const char* a = (const char*)u;
+    const char* b = (const char*)u_out;
+    if (a < b + ub && b < a + ub) return fail(h, MRCM_ERR_INVALID_ARG, "u and u_out overlap");
+    if (h->stage < 4) return fail(h, MRCM_ERR_STATE, "the multiscale solve must run first");
+    const int precision = h->t.cfg.precision;
+    const int sweeps = precision == MRCM_FP64 ? 0 : std::max(h->t.cfg.ir_max_sweeps, 8);
+    const double tol = h->t.cfg.ir_tol > 0 ? h->t.cfg.ir_tol : 1e-14;
+    int rc = mrcm::launch_postprocess(h->t, h->d, h->lay, (char*)ws, u, u_out, mres, h->f, precision, sweeps, tol,
+                                      stream, h->prof);
+    h->stage = 0;                        // coefficients, factors and MBF columns are overwritten
+    return after_launch(h, rc, "mrcm_postprocess_velocity");
+}
+
 mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconverged, int* zero_piv,
                              int* sweeps) {
     if (!h) return MRCM_ERR_INVALID_ARG;

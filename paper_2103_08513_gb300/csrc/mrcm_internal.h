@@ -293,6 +293,9 @@ int configure_reconstruct(const Tables& t);
 int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, const double* f,
                    void* stream, int reps, int* best_solve, int* best_sweep, int* best_factor, int* best_factor_mid,
                    float* ms_out);
+int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* u,
+                       double* u_out, double* mres, const double* f, int precision, int sweeps, double tol,
+                       void* stream, Prof& P);
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P);

@@ -1145,6 +1145,7 @@ struct LocalArgs {
     int* queue;           // work-queue counter (reset to 0 before each launch)
     int count_unconverged;  // add this sweep's unconverged columns to the status word
     int bar_off;          // shared-memory offset of the two mbarriers (after the largest layout)
+    int last_only;        // solve only the last (particular) column of every subdomain
 };
 
 
@@ -1214,7 +1215,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         int base = 0;
         for (int j0 = 0; j0 < m; j0 += 32) {
             const int j = j0 + threadIdx.x;
-            const bool act = j < m && (!kSweep || conv[j] == 0);
+            const bool act = j < m && (!g.last_only || j == m - 1) && (!kSweep || conv[j] == 0);
             const unsigned bal = __ballot_sync(0xffffffffu, act);
             if (act) cols[base + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
             base += __popc(bal);
@@ -1563,6 +1564,134 @@ static size_t element_smem(const Tables& t) {
     return (size_t)mx * (2 * sizeof(double) + sizeof(int));
 }
 
+// ---------------------------------------------------------------------------
+// Mean velocity post-processing (Eq. locprob_submean, the "Mean" method of the
+// paper's two-phase section).  On every fine Gamma face the two sides'
+// velocities are averaged, Ubar = (u^+ + u^-) / 2; every subdomain then
+// re-solves its TPFA problem with Neumann data: Ubar on Gamma, the multiscale
+// velocity on the walls.  The local matrix keeps the interior
+// transmissibilities and loses the Robin and Dirichlet terms; the pure
+// Neumann matrix is singular and the data compatible (the outward fluxes sum
+// to the sources, Eq. weakcont_f), so the subdomain's last cell (slab order)
+// is tied to pressure 0 by adding its own diagonal once more (exact for
+// compatible data: the tie carries no flux).  The right-hand side goes into
+// the particular column's Dirichlet slot: f V + rhs, rhs = -(prescribed
+// outward fluxes).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_pp_coefficients(const SubInfo* __restrict__ subs, const double* __restrict__ u_in, Geo geo,
+                  double* __restrict__ coef, double* __restrict__ scale, double* __restrict__ rhs_part,
+                  long long nct) {
+    const SubInfo s = subs[blockIdx.x];
+    const long long ncells = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const long long stride[3] = {1, geo.n[0], (long long)geo.n[0] * geo.n[1]};
+    int lstride[3];
+    lstride[s.ua] = 1; lstride[s.va] = s.su; lstride[s.sa] = s.b;
+    const double* tp[3];
+    tp[s.ua] = coef + nct + s.cell_off;
+    tp[s.va] = coef + 2 * nct + s.cell_off;
+    tp[s.sa] = coef + 3 * nct + s.cell_off;
+    for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
+        int lc[3];
+        local_coords(s, c, lc);
+        const long long g = global_cell(s, lc, geo.n);
+        double d = 0.0, rd = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double* ulo = u_in + (long long)(2 * a) * ncells;
+            const double* uhi = u_in + (long long)(2 * a + 1) * ncells;
+            if (lc[a] + 1 < s.sz[a]) {
+                d += tp[a][c];
+            } else {                                     // box face on the +a side: Gamma (mean) or wall
+                double v = uhi[g];
+                if (s.o[a] + lc[a] + 1 < geo.n[a]) v = 0.5 * (v + ulo[g + stride[a]]);
+                rd -= v * geo.area[a];
+            }
+            if (lc[a] > 0) {
+                d += tp[a][c - lstride[a]];
+            } else {                                     // box face on the -a side
+                double v = ulo[g];
+                if (s.o[a] + lc[a] > 0) v = 0.5 * (v + uhi[g - stride[a]]);
+                rd += v * geo.area[a];
+            }
+        }
+        if (c == s.N - 1) d += d > 0.0 ? d : 1.0;        // the tie
+        const long long i = s.cell_off + c;
+        coef[i] = d;
+        scale[i] = f32_to_f64(rsqrtf(f64_to_f32_rz(d)));
+        rhs_part[i] = rd;
+    }
+}
+
+// Post-processed velocity: TPFA of the Neumann solution (the particular column
+// of the MBF array) on interior faces, Ubar on Gamma faces (both sides write the
+// same value), the multiscale velocity on walls; then the per-cell mass balance
+// sum(out-fluxes) - f V, reduced to its maximum (atomicMax on the bits of a
+// non-negative double: order-independent).
+__global__ void __launch_bounds__(kThreads)
+k_pp_velocity(const SubInfo* __restrict__ subs, const double* __restrict__ X, const double* __restrict__ coef,
+              const double* __restrict__ u_in, const double* __restrict__ f, Geo geo, long long nct,
+              double* __restrict__ u_out, unsigned long long* __restrict__ mres_bits) {
+    const SubInfo s = subs[blockIdx.x];
+    const long long ncells = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const long long stride[3] = {1, geo.n[0], (long long)geo.n[0] * geo.n[1]};
+    int lstride[3];
+    lstride[s.ua] = 1; lstride[s.va] = s.su; lstride[s.sa] = s.b;
+    const double* tp[3];
+    tp[s.ua] = coef + nct + s.cell_off;
+    tp[s.va] = coef + 2 * nct + s.cell_off;
+    tp[s.sa] = coef + 3 * nct + s.cell_off;
+    const double* pl = X + s.x_off + (long long)(s.m - 1) * s.N;
+    double inv_area[3];
+    for (int a = 0; a < 3; ++a) inv_area[a] = 1.0 / geo.area[a];
+    for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
+        int lc[3];
+        local_coords(s, c, lc);
+        const long long g = global_cell(s, lc, geo.n);
+        const double pc = pl[c];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double* ulo = u_in + (long long)(2 * a) * ncells;
+            const double* uhi = u_in + (long long)(2 * a + 1) * ncells;
+            double vhi, vlo;
+            if (lc[a] + 1 < s.sz[a]) {
+                vhi = tp[a][c] * (pc - pl[c + lstride[a]]) * inv_area[a];
+            } else {
+                vhi = uhi[g];
+                if (s.o[a] + lc[a] + 1 < geo.n[a]) vhi = 0.5 * (vhi + ulo[g + stride[a]]);
+            }
+            if (lc[a] > 0) {
+                vlo = tp[a][c - lstride[a]] * (pl[c - lstride[a]] - pc) * inv_area[a];
+            } else {
+                vlo = ulo[g];
+                if (s.o[a] + lc[a] > 0) vlo = 0.5 * (vlo + uhi[g - stride[a]]);
+            }
+            u_out[(long long)(2 * a + 1) * ncells + g] = vhi;
+            u_out[(long long)(2 * a) * ncells + g] = vlo;
+        }
+    }
+    __syncthreads();                                      // this CTA wrote every face of its cells
+    const double vol = geo.h[0] * geo.h[1] * geo.h[2];
+    double mx = 0.0;
+    for (int c = threadIdx.x; c < s.N; c += blockDim.x) {
+        int lc[3];
+        local_coords(s, c, lc);
+        const long long g = global_cell(s, lc, geo.n);
+        double div = -f[g] * vol;
+        for (int a = 0; a < 3; ++a)
+            div += (u_out[(long long)(2 * a + 1) * ncells + g] - u_out[(long long)(2 * a) * ncells + g]) * geo.area[a];
+        mx = (div == div) ? fmax(mx, fabs(div)) : __longlong_as_double(0x7ff0000000000000LL);
+    }
+    __shared__ double red[kThreads];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(mres_bits, (unsigned long long)__double_as_longlong(red[0]));
+}
+
 Geo make_geo(const mrcm_config& c) {
     Geo g;
     g.h[0] = c.hx; g.h[1] = c.hy; g.h[2] = c.hz;
@@ -1714,6 +1843,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.queue = (int*)(ws + L.status) + ST_QUEUE;
     g.count_unconverged = 0;
     g.bar_off = (int)d.solve_smem - 16;
+    g.last_only = 0;
     return g;
 }
 
@@ -1758,6 +1888,48 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
                                         (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+    return (int)cudaGetLastError();
+}
+
+// Mean velocity post-processing: Neumann coefficients and right-hand sides
+// from the multiscale velocity, then per wave the block factor of the Neumann
+// matrices and the solve of the one (particular) column, refined like the
+// MBF columns in mixed precision; then the post-processed velocity.  Leaves
+// the local coefficients, factors and MBF array overwritten.
+int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* u,
+                       double* u_out, double* mres, const double* f, int precision, int sweeps, double tol,
+                       void* stream, Prof& P) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nsub = (int)t.subs.size();
+    int* status = (int*)(ws + L.status);
+    double* coef = (double*)(ws + L.coef);
+    const Geo geo = make_geo(t.cfg);
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
+    MRCM_LAUNCH(P, "k_pp_coefficients", st, k_pp_coefficients<<<nsub, kThreads, 0, st>>>(d.subs, u, geo, coef,
+                (double*)(ws + L.scale), (double*)(ws + L.rhs_part), t.n_cells));
+    LocalArgs g = local_args(t, d, L, ws, f);
+    g.tol2 = tol * tol;
+    g.last_only = 1;
+    const void* W = (const void*)(ws + L.W);
+    for (int w = 0; w < t.n_waves; ++w) {
+        launch_factor_wave(t, d, L, ws, precision, w, st, P);
+        g.list = d.solve_list + t.wave_off[w];
+        g.nlist = t.wave_off[w + 1] - t.wave_off[w];
+        g.count_unconverged = 0;
+        launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
+        if (precision != MRCM_FP64) {
+            for (int it = 0; it < sweeps; ++it) {
+                g.count_unconverged = it + 1 == sweeps ? 1 : 0;
+                launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+            }
+        }
+    }
+    double* psum = (double*)(ws + L.psum);
+    unsigned long long* mbits = (unsigned long long*)(psum + nsub + 1);
+    MRCM_LAUNCH(P, "k_zero_int", st, k_zero_int<<<1, 32, 0, st>>>((int*)mbits, 2));
+    MRCM_LAUNCH(P, "k_pp_velocity", st, k_pp_velocity<<<nsub, kThreads, 0, st>>>(d.subs, (const double*)(ws + L.X), coef, u,
+                f, geo, t.n_cells, u_out, mbits));
+    if (mres) cudaMemcpyAsync(mres, mbits, sizeof(double), cudaMemcpyDeviceToDevice, st);
     return (int)cudaGetLastError();
 }
 

@@ -127,6 +127,19 @@ class MRCM:
                                           _stream(stream)), self.handle)
         return p, u, mres
 
+    def postprocess_velocity(self, u, out=None, mres=None, stream=None):
+        """Mean velocity post-processing of a reconstructed velocity u (6, nz, ny, nx);
+        returns (u_pp, mass_residual_max).  Overwrites the local factors: the next
+        solve starts again from factor_local."""
+        assert u.dtype == torch.float64 and u.is_cuda and u.is_contiguous()
+        if out is None:
+            out = torch.empty_like(u)
+        if mres is None:
+            mres = torch.empty(1, dtype=torch.float64, device=self.device)
+        L.check(self.lib.mrcm_postprocess_velocity(self.handle, _ptr(u), _ptr(out), _ptr(mres), self.ws_ptr,
+                                                   _stream(stream)), self.handle)
+        return out, mres
+
     def outputs(self):
         """Preallocated (X, p, u, mres) device buffers for solve(..., out=...)."""
         nx, ny, nz = self.n

@@ -1,8 +1,8 @@
 """Full-size workloads in the benchmark's own launch configuration, against the oracle.
 
 * C2 (60x220x85, 2244 subdomains): the mixed solve exactly as the benchmark
-  times it (autotuned kernels, CUDA-graph replay, 3 FP64 refinement sweeps,
-  per-column stop 1e-9) against the whole staged oracle run over all host
+  times it (autotuned kernels, CUDA-graph replay, the FP64 refinement sweeps
+  and per-column stop of BENCH_SETTINGS) against the whole staged oracle run over all host
   cores: p, u, X at 1e-8 relative L2, A^int and b^int entrywise.  The FP64 GPU
   form at 1e-10.
 * C3 (uneven 8/12/16 blocks) and C5 (32768 blocks of 16x16x8 in
@@ -10,7 +10,8 @@
   seeded 1 % sample of subdomains gets full MBF parity (every column of the
   sample against the oracle's local solve), and the whole GPU result is
   checked by properties that hold at any size: the FP64 residual of the
-  interface system at the GPU's X, per-cell mass balance, and zero-mean p.
+  interface system at the GPU's X (every row but the F row that the pressure
+  constant replaces), per-cell mass balance, and zero-mean p.
 
 Tolerances: mixed mode 1e-8 (the metric's bar) on p, u and X; per-column MBF
 parity 1e-8 of the column's largest entry; FP64 mode 1e-10; interface entries
@@ -78,7 +79,8 @@ def test_c2_benchmarked_configuration_matches_oracle():
     s = _solver(w, "fp32_ir", BENCH_SETTINGS["c2"])
     p, u, X, mres = _bench_solve(s, K, f)
     code, st = s.read_status()
-    assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
+    print(f"C2 mixed status: {st}")
+    assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0 and st["unconverged"] == 0
     ep, eu, ex = rel_l2(p, r.p), rel_l2(u.ravel(), r.u.ravel()), rel_l2(X, r.X)
     print(f"C2 mixed vs oracle: p {ep:.3e}  u {eu:.3e}  X {ex:.3e}  mass residual {mres:.3e}")
     assert ep < 1e-8 and eu < 1e-8 and ex < 1e-8
@@ -104,6 +106,7 @@ def _sampled_parity(name, frac=0.01, seed=0):
     s = _solver(w, "fp32_ir", settings)
     p, u, X, mres = _bench_solve(s, K, f)
     code, st = s.read_status()
+    print(f"{name} status: {st}")
     assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
     prob = oracle.from_workload(w, K=K, f=f)
     bases, sub_bases, face_basis = build_bases(prob)
@@ -116,9 +119,12 @@ def _sampled_parity(name, frac=0.01, seed=0):
         G = s.mbf_block(int(l), Xo.shape[1], Xo.shape[0]).T
         err = np.abs(G - Xo).max(axis=0) / np.maximum(np.abs(Xo).max(axis=0), 1e-300)
         worst = max(worst, float(err.max()))
-    # the FP64 interface residual at the GPU's X (the system is consistent; X has pi^p_0 = 0)
+    # the FP64 interface residual at the GPU's X.  With no-flow walls the F rows sum
+    # to the (zero) total source only up to the MBFs' accuracy, so F row 0 is the
+    # one the pressure constant replaces (pi^p_0 = 0): it is left out
     A, b = _csr(s)
-    res = np.linalg.norm(A @ X - b) / np.linalg.norm(b)
+    rows = np.arange(1, len(b))
+    res = np.linalg.norm((A @ X - b)[rows]) / np.linalg.norm(b[rows])
     mbal = mres / (np.abs(prob.f).max() * prob.cell_volume)
     print(f"{name}: {len(sample)} sampled subdomains, worst MBF column error {worst:.3e}; "
           f"interface residual {res:.3e}; mass residual {mbal:.3e} of max |f| V; mean p {p.mean():.3e}")
