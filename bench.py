@@ -318,6 +318,95 @@ def learned_form(dev, stream, train_fields=200, epochs=2, eval_fields=4):
     }
 
 
+def _timed_graph(s, Kd, fd, stream, steps=5):
+    """Median CUDA-event time (ms) of graph-replayed full solves (after one capture run)."""
+    import torch
+    out = s.outputs()
+    s.solve(Kd, fd, out=out, stream=stream, graph=True)
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve(Kd, fd, out=out, stream=stream, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), out
+
+
+def _rel(a, b):
+    import torch
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def variants_sections(make, w, K, dev, stream, fd, u_ms, n_sub):
+    """The rows after the solve itself, measured on the timed workload:
+    mean velocity post-processing, the alpha / Hbar variants of the Robin
+    parameter and interface spaces, and the permeability-contrast sweep K^theta
+    with the FP64 fallback."""
+    import numpy as np
+    import torch
+    out = {}
+    # --- mean velocity post-processing (after a mixed solve; it re-factors the Neumann problems)
+    s = make("fp32_ir")
+    Kd = torch.from_numpy(K).to(dev)
+    ms = []
+    for i in range(6):
+        _, u, _, _ = s.solve(Kd, fd, stream=stream)
+        u = u.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        up, mres = s.postprocess_velocity(u, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            ms.append(e0.elapsed_time(e1))
+    code, st = s.read_status()
+    out["postprocess_mean_velocity"] = {
+        "ms": round(statistics.median(ms), 4), "subdomains_per_s": round(n_sub / (statistics.median(ms) / 1e3), 1),
+        "mass_residual_max": float(mres.cpu()[0]), "unconverged": st["unconverged"],
+        "what": "Eq. locprob_submean: Gamma faces averaged, Neumann TPFA re-solve of every subdomain "
+                "(mixed factor + FP64 refinement), fine-scale conservative velocity"}
+    del s, up, u
+    # --- alpha / Hbar variants (beta = alpha H / K)
+    rows = []
+    for alpha in (1e-6, 1.0, 1e6):
+        for patch in (w.patch, ((0, 0),) * 3):
+            kw = dict(beta_mode=1, alpha=alpha, patch=patch)
+            s64 = make("fp64", **kw)
+            t64, o64 = _timed_graph(s64, Kd, fd, stream, steps=3)
+            sm = make("fp32_ir", **kw)
+            tm, om = _timed_graph(sm, Kd, fd, stream, steps=5)
+            code, st = sm.read_status()
+            fb, lost = sm.read_fallback()
+            rows.append({"alpha": alpha, "patch": [list(p) for p in patch], "interface_unknowns": sm.n_interface,
+                         "ms_mixed": round(tm, 4), "ms_fp64": round(t64, 4),
+                         "rel_err_vs_fp64": {"p": _rel(om[1], o64[1]), "u": _rel(om[2], o64[2])},
+                         "fallback_subdomains": fb, "unconverged": st["unconverged"]})
+            del s64, sm, o64, om
+            torch.cuda.empty_cache()
+    out["alpha_variants"] = rows
+    # --- contrast sweep K^theta (Table tab:time-amg-contrast's theta values)
+    rows = []
+    for theta in (0.3, 0.48, 0.65, 0.83, 1.0, 1.17, 1.35):
+        Kt = torch.from_numpy(K ** theta).to(dev)
+        s64 = make("fp64")
+        t64, o64 = _timed_graph(s64, Kt, fd, stream, steps=3)
+        sm = make("fp32_ir")
+        tm, om = _timed_graph(sm, Kt, fd, stream, steps=5)
+        code, st = sm.read_status()
+        fb, lost = sm.read_fallback()
+        rows.append({"theta": theta, "contrast": float(K.max() ** theta / K.min() ** theta),
+                     "ms_mixed": round(tm, 4), "ms_fp64": round(t64, 4),
+                     "rel_err_vs_fp64": {"p": _rel(om[1], o64[1]), "u": _rel(om[2], o64[2])},
+                     "fallback_subdomains": fb, "fallback_rate": round(fb / n_sub, 5),
+                     "unconverged": st["unconverged"]})
+        del s64, sm, o64, om, Kt
+        torch.cuda.empty_cache()
+    out["contrast_sweep"] = rows
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,6 +426,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start section")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the post-processing, alpha / Hbar and contrast-sweep sections")
     ap.add_argument("--wave-gb", type=float, default=None,
                     help="memory budget of the local block factors per wave (GB); default 16 for c5, else none")
     return ap.parse_args()
@@ -442,10 +533,12 @@ def main():
     wave_gb = args.wave_gb if args.wave_gb is not None else bs["wave_gb"]
     wave_bytes = int(wave_gb * (1 << 30))
 
-    def make(precision):
-        return MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const,
-                    precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=args.ir_tol, device=dev,
-                    wave_bytes=wave_bytes)
+    def make(precision, **kw):
+        cfg = dict(h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const, patch=w.patch)
+        cfg.update(kw)
+        patch = cfg.pop("patch")
+        return MRCM(w.n, w.edges, patch, precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=args.ir_tol,
+                    device=dev, wave_bytes=wave_bytes, **cfg)
 
     Kd = torch.from_numpy(K).to(dev)
     fd = torch.from_numpy(f).to(dev)
@@ -630,6 +723,8 @@ def main():
                        "ms_per_step": round(e2e_ms / e2e[1], 4)}
     if cpu:
         line["cpu_baseline"] = cpu
+    if not args.no_variants and args.workload == "c2":
+        line.update(variants_sections(make, w, K, dev, stream, fd, outs[2], n_sub))
     if not args.no_learned and args.workload == "c2":
         line["learned"] = learned_form(dev, stream)
     print(json.dumps(line), flush=True)

@@ -68,7 +68,7 @@ typedef enum {
 enum { MRCM_BETA_CONST = 0, MRCM_BETA_ALPHA_H_OVER_K = 1 };
 enum { MRCM_BC_NOFLOW = 0, MRCM_BC_DIRICHLET = 1 };
 enum {
-    MRCM_FP64 = 0,          /* local factor and solves in FP64 */
+    MRCM_FP64 = 0,          /* local factor and solves in FP64 (one FP64 refinement step) */
     MRCM_FP32_IR = 1,       /* FP32 factor/solves + FP64 iterative refinement */
     MRCM_TF32_IR = 2,       /* tensor-core TF32 solves + FP64 iterative refinement */
     MRCM_LEARNED_PCG = 3    /* learned warm start + PCG (reserved) */
@@ -91,7 +91,8 @@ enum {
  *                     normal to axis a: MRCM_BC_NOFLOW or MRCM_BC_DIRICHLET
  *  bc_value[a][side]  Dirichlet pressure of that wall
  *  precision          MRCM_FP64 / MRCM_FP32_IR / MRCM_TF32_IR
- *  ir_max_sweeps      refinement sweeps after the first solve (mixed modes)
+ *  ir_max_sweeps      refinement sweeps after the first solve (mixed modes;
+ *                     MRCM_FP64 always takes one)
  *  ir_tol             per-column stop: ||r||_2 <= ir_tol * ||b||_2
  *  wave_bytes         memory budget (bytes) of the local block factors: when
  *                     positive, subdomains are processed in waves whose
@@ -100,7 +101,16 @@ enum {
  *  tune_cache         path of the autotuner cache (text), or NULL; read at
  *                     the first device call, written by mrcm_autotune
  *  interface_refine   FP64 refinement steps of the interface solve after the
- *                     LDL^T solve: 0 = default (1), -1 = none, k > 0 = k   */
+ *                     LDL^T solve: 0 = default (1), -1 = none, k > 0 = k
+ *  fallback_cap       mixed modes: subdomains whose columns are still above
+ *                     ir_tol after ir_max_sweeps are factored and solved again
+ *                     in FP64 (the direct fallback), at most this many per
+ *                     wave (their FP64 block factors take a workspace region
+ *                     of that many slots); 0 = default max(16, n_sub / 64)
+ *                     (at most n_sub), -1 = no fallback.  Subdomains beyond
+ *                     the cap, or with slab blocks above 224 (the FP64 factor's
+ *                     limit), stay unconverged and are counted by
+ *                     mrcm_read_status */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -117,6 +127,7 @@ typedef struct {
     size_t wave_bytes;
     const char* tune_cache;
     int interface_refine;
+    int fallback_cap;
 } mrcm_config;
 
 /* Sizes derived by mrcm_setup (host-side; no GPU needed). */
@@ -264,6 +275,12 @@ mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* swe
  * pivots and the refinement sweeps used. */
 mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconverged,
                              int* interface_zero_pivots, int* sweeps_used);
+
+/* FP64 fallback of the last solve, read back synchronously: subdomains that
+ * were re-solved in FP64 after the mixed refinement left columns above
+ * ir_tol, and subdomains that needed it but could not have it (over the
+ * cap, or slab block above 224); the latter's columns count as unconverged. */
+mrcm_status mrcm_read_fallback(mrcm_handle* h, void* ws, int* fallback_subdomains, int* not_recovered);
 
 /* Work counters of the last solve, read back synchronously: MBF entries
  * (cell x right-hand side) swept by the FP64-residual refinement sweeps, summed

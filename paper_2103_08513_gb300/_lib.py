@@ -37,6 +37,7 @@ class mrcm_config(C.Structure):
         ("wave_bytes", C.c_size_t),
         ("tune_cache", C.c_char_p),
         ("interface_refine", C.c_int),
+        ("fallback_cap", C.c_int),
     ]
 
 
@@ -67,6 +68,7 @@ SIGNATURES = {
     "mrcm_reconstruct": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "mrcm_postprocess_velocity": (C.c_int, [C.c_void_p] * 6),
     "mrcm_read_status": (C.c_int, [C.c_void_p, C.c_void_p] + [C.POINTER(C.c_int)] * 4),
+    "mrcm_read_fallback": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_read_work": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "mrcm_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t]),
     "mrcm_solve": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7 + [C.c_size_t, C.c_void_p, C.c_int]),

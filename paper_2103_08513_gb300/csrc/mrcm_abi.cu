@@ -342,6 +342,18 @@ mrcm_status mrcm_read_status(mrcm_handle* h, void* ws, int* not_spd, int* unconv
     return MRCM_OK;
 }
 
+mrcm_status mrcm_read_fallback(mrcm_handle* h, void* ws, int* fallback_subdomains, int* not_recovered) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    int w[mrcm::ST_COUNT];
+    cudaError_t e = cudaMemcpy(w, (char*)ws + h->lay.status, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mrcm_read_fallback");
+    if (fallback_subdomains) *fallback_subdomains = w[mrcm::ST_FB_TOTAL];
+    if (not_recovered) *not_recovered = w[mrcm::ST_FB_LOST];
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_read_work(mrcm_handle* h, void* ws, long long* swept) {
     if (!h || !swept) return MRCM_ERR_INVALID_ARG;
     mrcm_status st = check_ws(h, ws);

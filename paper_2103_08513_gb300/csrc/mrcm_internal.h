@@ -36,6 +36,7 @@ struct SubInfo {
     int el_dim;        // 2|I^l|
     long long cell_off;   // offset into per-cell arrays
     long long x_off;      // offset (doubles) into the MBF array [m][N]
+    long long y_off;      // offset (elements) of the forward-sweep values Y (= x_off; a slot for the FP64 fallback)
     long long w_off;      // offset (elements) into the block factor array
     long long el_off;     // offset (doubles) into element matrices
     int elb_off;          // offset (doubles) into element right-hand sides
@@ -127,6 +128,7 @@ struct Layout {
     size_t coef, scale, scf, tsc, rhs_part, face_tr, face_beta, face_u, face_bst, W, X, R, colnorm, conv;
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t bpart, bcnt;    // row-chunk partial sums and counters of the split boundary back substitution
+    size_t fb_W, fb_Y, fb_subs, fb_list;   // FP64 fallback: block factors, forward values, subdomain records, slots
     size_t total;
 };
 
@@ -156,6 +158,8 @@ struct DeviceTables {
     int* front_inv = nullptr;
     int* front_dofs = nullptr;
     int* level_ids = nullptr;                  // fronts of all levels, concatenated
+    size_t fb_solve_smem = 0;                  // dynamic shared memory of the FP64 fallback solve
+    int fb_occ = 1;
     std::vector<int> level_off;                // host: offsets of each level in level_ids
     int device = -1;
     bool ready = false;
@@ -248,7 +252,32 @@ inline void bwd_split_sizes(const std::vector<std::vector<int>>& levels, const s
 // Device status words at Layout::status.
 enum StatusWord { ST_NOT_SPD = 0, ST_UNCONVERGED = 1, ST_ZERO_PIVOT = 2, ST_SWEEPS = 3,
                   ST_TIMEOUT = 4, ST_QUEUE = 5 /* work-queue counter */,
-                  ST_SWEPT = 8 /* 64-bit counter at words 8-9 */, ST_COUNT = 16 };
+                  ST_FB_WAVE = 6 /* fallback slots taken in the current wave */,
+                  ST_FB_TOTAL = 7 /* subdomains re-solved in FP64 */,
+                  ST_SWEPT = 8 /* 64-bit counter at words 8-9 */,
+                  ST_FB_LOST = 10 /* subdomains that needed the fallback and could not have it */,
+                  ST_COUNT = 16 };
+
+// FP64 fallback of the mixed modes: slots per wave and FP64 block-factor
+// doubles per slot (the largest n_s x padded b^2 among blocks the FP64 factor
+// takes, b <= kMaxBlock64); cap 0 = no fallback.
+inline void fallback_params(const Tables& t, int* cap, long long* stride, long long* ystride = nullptr) {
+    *cap = 0;
+    *stride = 0;
+    if (ystride) *ystride = 0;
+    const int nsub = (int)t.subs.size();
+    if (t.cfg.precision == MRCM_FP64 || t.cfg.fallback_cap < 0 || nsub == 0) return;
+    long long st = 0, yst = 0;
+    for (const SubInfo& s : t.subs)
+        if (s.b <= kMaxBlock64) {
+            st = std::max(st, (long long)s.ns * wstride<double>(s.b));
+            yst = std::max(yst, (long long)s.m * s.N);
+        }
+    if (st == 0) return;
+    *stride = (st + 31) / 32 * 32;
+    if (ystride) *ystride = (yst + 31) / 32 * 32;
+    *cap = t.cfg.fallback_cap > 0 ? std::min(t.cfg.fallback_cap, nsub) : std::min(nsub, std::max(16, nsub / 64));
+}
 
 }  // namespace mrcm
 

@@ -187,8 +187,10 @@ template <typename T, bool kScaled>
 __global__ void __launch_bounds__(kThreads)
 k_block_factor(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                const double* __restrict__ scale, T* __restrict__ Wall, int* __restrict__ status,
-               long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all) {
+               long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all,
+               const int* __restrict__ limit /* CTAs from *limit on have no subdomain; may be NULL */) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (limit && (int)blockIdx.x >= *limit) return;
     const SubInfo s = subs[list[blockIdx.x]];
     const int b = s.b, su = s.su;
     T* Lp = reinterpret_cast<T*>(smem_raw);                  // packed lower triangle
@@ -1146,6 +1148,7 @@ struct LocalArgs {
     int count_unconverged;  // add this sweep's unconverged columns to the status word
     int bar_off;          // shared-memory offset of the two mbarriers (after the largest layout)
     int last_only;        // solve only the last (particular) column of every subdomain
+    const int* nlist_dev; // when set: the list holds min(nlist, *nlist_dev) subdomains (written by an earlier kernel)
 };
 
 
@@ -1206,7 +1209,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     else { cp.cs = cs; }
     const T* W = Wall + s.w_off;
     double* Xs = g.X + s.x_off;
-    T* Ys = reinterpret_cast<T*>(g.Ybuf) + s.x_off;
+    T* Ys = reinterpret_cast<T*>(g.Ybuf) + s.y_off;
     int* conv = g.conv + s.rhs_off;
     const double vol = g.geo.h[0] * g.geo.h[1] * g.geo.h[2];
 
@@ -1427,12 +1430,13 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     pipe.phase[0] = pipe.phase[1] = 0u;
     pipe.pending[0] = pipe.pending[1] = 0;
     pipe.abort = 0;
+    const int nlist = g.nlist_dev ? min(g.nlist, *g.nlist_dev) : g.nlist;
     for (;;) {
         if (threadIdx.x == 0) item = atomicAdd(g.queue, 1);
         __syncthreads();
         const int it = item;
         __syncthreads();
-        if (it >= g.nlist || pipe.abort) break;
+        if (it >= nlist || pipe.abort) break;
         solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it], smem_raw, pipe);
     }
     drain_pipe(pipe, bar);
@@ -1692,6 +1696,40 @@ k_pp_velocity(const SubInfo* __restrict__ subs, const double* __restrict__ X, co
     if (threadIdx.x == 0) atomicMax(mres_bits, (unsigned long long)__double_as_longlong(red[0]));
 }
 
+// FP64 fallback (mixed modes): after the last refinement sweep of a wave, every
+// subdomain with a column still above the tolerance takes a slot (atomic
+// ticket) whose record is a copy of its own with the block-factor and
+// forward-value offsets moved into the fallback regions; the FP64 factor and
+// solve kernels then run on the slots.  Which slot a subdomain gets does not
+// change its result.  Subdomains without a slot (over the cap, or blocks the
+// FP64 factor does not take) keep their mixed columns and count as
+// unconverged.
+__global__ void k_fb_collect(const SubInfo* __restrict__ subs, const int* __restrict__ list, int nlist,
+                             const int* __restrict__ conv, int* __restrict__ status, SubInfo* __restrict__ fb_subs,
+                             int* __restrict__ fb_list, int cap, long long wstride_slot, long long ystride_slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nlist) return;
+    SubInfo s = subs[list[i]];
+    int bad = 0;
+    for (int j = 0; j < s.m; ++j) bad += conv[s.rhs_off + j] == 0;
+    if (!bad) return;
+    int slot = -1;
+    if (s.b <= kMaxBlock64) {
+        slot = atomicAdd(&status[ST_FB_WAVE], 1);
+        if (slot >= cap) slot = -1;
+    }
+    if (slot < 0) {
+        atomicAdd(&status[ST_FB_LOST], 1);
+        atomicAdd(&status[ST_UNCONVERGED], bad);
+        return;
+    }
+    atomicAdd(&status[ST_FB_TOTAL], 1);
+    s.w_off = (long long)slot * wstride_slot;
+    s.y_off = (long long)slot * ystride_slot;
+    fb_subs[slot] = s;
+    fb_list[slot] = slot;
+}
+
 Geo make_geo(const mrcm_config& c) {
     Geo g;
     g.h[0] = c.hx; g.h[1] = c.hy; g.h[2] = c.hz;
@@ -1717,7 +1755,7 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
         if (n_large > 0) {
             size_t sm = factor_smem<double>(t.max_b);
             MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
-                (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc)));
+                (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc), nullptr));
         }
     } else {
         if (n_small > 0) {
@@ -1757,7 +1795,7 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
             case 544: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<544><<<n, 544, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
             default: {
                 size_t sm = factor_smem<float>(t.max_b);
-                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n, kThreads, sm, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc));
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n, kThreads, sm, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc, nullptr));
             }
             }
             q = e;
@@ -1810,7 +1848,7 @@ int configure_local(const Tables& t, DeviceTables& d) {
     d.solve_smem = solve_smem_bytes(t, t.cfg.precision);
     for (int v = 0; v < kNumSolveVariants; ++v) {
         const void* k0 = f64 ? solve_kernel<double, false, false>(v) : solve_kernel<float, true, false>(v);
-        const void* k1 = f64 ? solve_kernel<double, false, false>(v) : solve_kernel<float, true, true>(v);
+        const void* k1 = f64 ? solve_kernel<double, false, true>(v) : solve_kernel<float, true, true>(v);
         cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.solve_smem);
         cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.solve_smem);
         int occ0 = 0, occ1 = 0;
@@ -1818,6 +1856,24 @@ int configure_local(const Tables& t, DeviceTables& d) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k1, variant_threads(v), d.solve_smem);
         d.solve_occ[v] = std::max(1, occ0);
         d.sweep_occ[v] = std::max(1, occ1);
+    }
+    {
+        int cap;
+        long long stride;
+        fallback_params(t, &cap, &stride);
+        if (cap > 0) {
+            const int mpad = (t.max_m + 3) & ~3;
+            size_t sm = 0;
+            for (const SubInfo& sb : t.subs)
+                if (sb.b <= kMaxBlock64) sm = std::max(sm, solve_smem_layout<double>(sb.b, mpad, sb.N).total);
+            d.fb_solve_smem = sm + 16;
+            const void* k = solve_kernel<double, false, false>(0);
+            const size_t cur = f64 ? d.solve_smem : 0;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(cur, d.fb_solve_smem));
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, variant_threads(0), d.fb_solve_smem);
+            d.fb_occ = std::max(1, occ);
+        }
     }
     cudaFuncSetAttribute(k_block_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem<double>(std::min(t.max_b, kMaxBlock64)));
@@ -1844,6 +1900,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.count_unconverged = 0;
     g.bar_off = (int)d.solve_smem - 16;
     g.last_only = 0;
+    g.nlist_dev = nullptr;
     return g;
 }
 
@@ -1851,7 +1908,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
 static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs& g, const void* W, bool sweep,
                               int v, cudaStream_t st, Prof& P) {
     const bool f64 = t.cfg.precision == MRCM_FP64;
-    const void* k = f64 ? solve_kernel<double, false, false>(v)
+    const void* k = f64 ? (sweep ? solve_kernel<double, false, true>(v) : solve_kernel<double, false, false>(v))
                         : (sweep ? solve_kernel<float, true, true>(v) : solve_kernel<float, true, false>(v));
     const int occ = sweep ? d.sweep_occ[v] : d.solve_occ[v];
     const int grid = std::max(1, std::min(g.nlist, d.sms * occ));
@@ -1859,6 +1916,37 @@ static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs&
     void* args[] = {(void*)&g, (void*)&W};
     MRCM_LAUNCH(P, sweep ? "k_ir_sweep" : "k_local_solve", st,
                 cudaLaunchKernel(k, dim3(grid), dim3(variant_threads(v)), args, d.solve_smem, st));
+}
+
+// FP64 fallback of one wave (see k_fb_collect): slots, FP64 block factors of
+// the slots, FP64 solve of all their columns (replacing the mixed ones).
+static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const LocalArgs& g0,
+                            int cap, long long wstride_slot, long long ystride_slot, cudaStream_t st, Prof& P) {
+    int* status = (int*)(ws + L.status);
+    SubInfo* fb_subs = (SubInfo*)(ws + L.fb_subs);
+    int* fb_list = (int*)(ws + L.fb_list);
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_WAVE, 0));
+    MRCM_LAUNCH(P, "k_fb_collect", st, k_fb_collect<<<(g0.nlist + 127) / 128, 128, 0, st>>>(d.subs, g0.list, g0.nlist,
+                g0.conv, status, fb_subs, fb_list, cap, wstride_slot, ystride_slot));
+    int bmax = 0;
+    for (const SubInfo& s : t.subs) if (s.b <= kMaxBlock64) bmax = std::max(bmax, s.b);
+    MRCM_LAUNCH(P, "k_fb_factor", st, k_block_factor<double, false><<<cap, kThreads, factor_smem<double>(bmax), st>>>(
+                fb_subs, fb_list, g0.coef, g0.scale, (double*)(ws + L.fb_W), status, t.n_cells, nullptr, nullptr,
+                status + ST_FB_WAVE));
+    LocalArgs g = g0;
+    g.subs = fb_subs;
+    g.list = fb_list;
+    g.nlist = cap;
+    g.nlist_dev = status + ST_FB_WAVE;
+    g.Ybuf = (void*)(ws + L.fb_Y);
+    g.last_only = 0;
+    g.bar_off = (int)d.fb_solve_smem - 16;
+    const void* k = solve_kernel<double, false, false>(0);
+    const int grid = std::max(1, std::min(cap, d.sms * d.fb_occ));
+    const void* Wfb = (const void*)(ws + L.fb_W);
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+    void* args[] = {(void*)&g, (void*)&Wfb};
+    MRCM_LAUNCH(P, "k_fb_solve", st, cudaLaunchKernel(k, dim3(grid), dim3(variant_threads(0)), args, d.fb_solve_smem, st));
 }
 
 int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
@@ -1869,7 +1957,12 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     LocalArgs g = local_args(t, d, L, ws, f);
     g.tol2 = tol * tol;
     const void* W = (const void*)(ws + L.W);
+    int fb_cap = 0;
+    long long fb_stride = 0, fb_ystride = 0;
+    fallback_params(t, &fb_cap, &fb_stride, &fb_ystride);
     MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_TOTAL, 0));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_LOST, 0));
     for (int w = 0; w < t.n_waves; ++w) {
         // one memory-bounded wave: factor (when waves share the W region), solve, refine
         if (t.n_waves > 1) launch_factor_wave(t, d, L, ws, precision, w, st, P);
@@ -1879,12 +1972,18 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
         launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
         if (precision != MRCM_FP64) {
             for (int it = 0; it < sweeps; ++it) {
-                g.count_unconverged = it + 1 == sweeps ? 1 : 0;
+                g.count_unconverged = it + 1 == sweeps && fb_cap == 0 ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
             }
+            if (fb_cap > 0) launch_fallback(t, d, L, ws, g, fb_cap, fb_stride, fb_ystride, st, P);
+        } else {
+            // FP64 form: the direct solve through the explicit block inverses plus one
+            // FP64 refinement step (the same residual sweep), for FP64-level MBFs
+            g.count_unconverged = 0;
+            launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
         }
     }
-    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 0 : sweeps));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 1 : sweeps));
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
                                         (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));

@@ -86,6 +86,7 @@ struct TreeBuilder {
 mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
     if (!cfg) { err = "config is NULL"; return MRCM_ERR_INVALID_ARG; }
     if (cfg->interface_refine < -1) { err = "interface_refine must be >= -1"; return MRCM_ERR_INVALID_ARG; }
+    if (cfg->fallback_cap < -1) { err = "fallback_cap must be >= -1"; return MRCM_ERR_INVALID_ARG; }
     t.cfg = *cfg;
     if (cfg->tune_cache) t.tune_cache = cfg->tune_cache;
     t.cfg.tune_cache = nullptr;
@@ -230,7 +231,7 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         }
         s.nface = (int)t.faces.size() - s.face_off;
         s.cell_off = cell_off;  cell_off += s.N;
-        s.x_off = x_off;        x_off += (long long)s.m * s.N;
+        s.x_off = x_off;        s.y_off = x_off;        x_off += (long long)s.m * s.N;
         s.el_off = el_off;      el_off += (long long)s.el_dim * s.el_dim;
         s.elb_off = elb_off;    elb_off += s.el_dim;
         s.rhs_off = (int)t.total_rhs;
@@ -442,6 +443,15 @@ void compute_layout(const Tables& t, Layout& L) {
         bwd_split_sizes(t.levels, t.fronts, &parts, &cnts);
         L.bpart = take(parts * sizeof(double));
         L.bcnt = take(cnts * sizeof(unsigned));
+    }
+    {
+        int cap;
+        long long stride, ystride;
+        fallback_params(t, &cap, &stride, &ystride);
+        L.fb_W = take((size_t)cap * stride * sizeof(double));
+        L.fb_Y = take((size_t)cap * ystride * sizeof(double));
+        L.fb_subs = take((size_t)cap * sizeof(SubInfo));
+        L.fb_list = take((size_t)cap * sizeof(int));
     }
     L.total = off;
 }

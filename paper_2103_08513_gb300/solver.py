@@ -33,7 +33,7 @@ class MRCM:
     def __init__(self, n, edges, patch=((0, 0),) * 3, h=(1.0, 1.0, 1.0), beta_mode=0, alpha=1.0,
                  beta_const=1.0, bc_type=((0, 0),) * 3, bc_value=((0.0, 0.0),) * 3,
                  precision="fp64", ir_max_sweeps=4, ir_tol=1e-14, device=None, allocate=True, tune_cache=None,
-                 wave_bytes=0, interface_refine=0):
+                 wave_bytes=0, interface_refine=0, fallback_cap=0):
         self.lib = L.load()
         cfg = L.mrcm_config()
         cfg.nx, cfg.ny, cfg.nz = (int(v) for v in n)
@@ -55,6 +55,7 @@ class MRCM:
         cfg.ir_tol = float(ir_tol)
         cfg.wave_bytes = int(wave_bytes)
         cfg.interface_refine = int(interface_refine)
+        cfg.fallback_cap = int(fallback_cap)
         self._tune_cache = tune_cache.encode() if tune_cache else None
         cfg.tune_cache = self._tune_cache
         self.cfg = cfg
@@ -208,6 +209,12 @@ class MRCM:
         code = self.lib.mrcm_read_status(self.handle, self.ws_ptr, *[C.byref(x) for x in v])
         return code, {"not_spd": v[0].value, "unconverged": v[1].value, "interface_zero_pivots": v[2].value,
                       "sweeps": v[3].value}
+
+    def read_fallback(self):
+        """(subdomains re-solved in FP64 by the fallback, subdomains that needed it and could not have it)."""
+        a, b = C.c_int(), C.c_int()
+        L.check(self.lib.mrcm_read_fallback(self.handle, self.ws_ptr, C.byref(a), C.byref(b)), self.handle)
+        return int(a.value), int(b.value)
 
     def read_work(self):
         """MBF entries swept by the refinement sweeps of the last solve."""

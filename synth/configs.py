@@ -189,7 +189,7 @@ BENCH_SETTINGS = {
     "c1": dict(ir_sweeps=3, ir_tol=1e-9, wave_gb=0.0),
     "c2": dict(ir_sweeps=5, ir_tol=1e-9, wave_gb=0.0),
     "c2_betaHK": dict(ir_sweeps=5, ir_tol=1e-9, wave_gb=0.0),
-    "c3": dict(ir_sweeps=3, ir_tol=1e-9, wave_gb=0.0),
+    "c3": dict(ir_sweeps=4, ir_tol=1e-9, wave_gb=0.0),
     "c5": dict(ir_sweeps=6, ir_tol=1e-9, wave_gb=16.0),
     "c5_slab": dict(ir_sweeps=6, ir_tol=1e-9, wave_gb=0.0),
 }

@@ -1,0 +1,36 @@
+"""The alpha / Hbar variants of Sec. "Choice of multiscale method" on the GPU,
+against the oracle: beta = alpha H / K at the paper's extreme alpha = 1e-6 and
+1e+6 (the pressure- and velocity-continuous limits) and halved interface
+elements (Hbar = H/2).  FP64 mode at 1e-10, mixed mode at 1e-8 (relative L2)."""
+import numpy as np
+import pytest
+
+import oracle
+from synth.configs import BETA_ALPHA_H_OVER_K, small
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from gpu_helpers import rel_l2, run_gpu  # noqa: E402
+
+BASE = dict(n=(24, 20, 12), edges=([6, 6, 7, 5], [5, 5, 5, 5], [4, 4, 4]), sigma=2.0, lam=4.0,
+            beta_mode=BETA_ALPHA_H_OVER_K)
+VARIANTS = {
+    "alpha_1e-6": dict(alpha=1e-6, patch=((0, 0), (0, 0), (0, 0))),
+    "alpha_1e+6": dict(alpha=1e6, patch=((0, 0), (0, 0), (0, 0))),
+    "alpha_1e-6_half": dict(alpha=1e-6, patch=((3, 2), (3, 2), (3, 3))),     # Hbar = H/2 on most faces
+    "alpha_1_half": dict(alpha=1.0, patch=((3, 2), (3, 2), (3, 3))),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32_ir", 1e-8)])
+@pytest.mark.parametrize("name", list(VARIANTS))
+def test_alpha_variants_match_oracle(name, prec, tol):
+    w = small(**BASE, **VARIANTS[name])
+    prob = oracle.from_workload(w)
+    r = oracle.solve_mrcm(prob)
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, prec, ir_max_sweeps=10, ir_tol=1e-13)
+    ep, eu = rel_l2(p, r.p), rel_l2(u.ravel(), r.u.ravel())
+    print(f"{name} {prec}: p {ep:.3e} u {eu:.3e} status {st}")
+    assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
+    assert ep < tol and eu < tol
