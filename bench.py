@@ -141,6 +141,21 @@ def oracle_full(w, K, f, pool=None):
     return r, time.perf_counter() - t0
 
 
+def learned_vs_oracle(kept):
+    """Largest relative L2 error (p and u) of the learned form's solves against the oracle."""
+    import numpy as np
+
+    import oracle
+    from synth.configs import Workload
+    worst = 0.0
+    for Kf, p, u in kept["fields"]:
+        prob = oracle.from_workload(Workload("c4", kept["n"], kept["edges"], kept["patch"]), K=Kf, f=kept["f"])
+        r = oracle.solve_mrcm(prob, keep=False)
+        worst = max(worst, float(np.linalg.norm(p - r.p) / np.linalg.norm(r.p)),
+                    float(np.linalg.norm(u.ravel() - r.u.ravel()) / np.linalg.norm(r.u)))
+    return worst
+
+
 def oracle_sample(w, K, f, n_sub_sample, seed=0, pool=None):
     """The oracle's local MBF stage (assembly, sparse LU, all m_l right-hand sides,
     traces and the subdomain's interface block) on a seeded sample of subdomains,
@@ -270,51 +285,66 @@ def learned_form(dev, stream, train_fields=200, epochs=2, eval_fields=4):
     final_loss = float(loss.cpu()[0])
     floor = float(((T - T.mean()) ** 2).mean())
     del X, T
-    it_w, it_z, t_w, t_z, t_inf, errs, fallbacks, nsamp, t_dir = [], [], 0.0, 0.0, 0.0, [], 0, 0, 0.0
+    # held-out fields: the learned-form MRCM solve (warm-started CG inside FP64 refinement for every
+    # column, FP64 direct fallback) against the direct mixed form and the FP64 GPU form (the oracle
+    # comparison is made by the CPU-baseline leg, from the outputs kept here)
+    edges = ([10] * 4, [10] * 4, [5, 5])
+    kept = []
+    sl = MRCM((nx, ny, nz), edges, ((5, 2),) * 3, precision="learned_pcg", ir_tol=1e-9, device=dev)
+    sm = MRCM((nx, ny, nz), edges, ((5, 2),) * 3, precision="fp32_ir", ir_max_sweeps=5, ir_tol=1e-9, device=dev)
+    s64 = MRCM((nx, ny, nz), edges, ((5, 2),) * 3, precision="fp64", device=dev)
+    rows = []
     for sd in range(201, 201 + eval_fields):
-        s.factor_local(field(sd))
-        e0.record(stream)
-        s.solve_mbf(f)                              # direct FP64 MBFs: the reference and the fallback
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_dir += e0.elapsed_time(e1)
-        x, t = net.samples(s)
-        n = x.shape[0]
-        e0.record(stream)
-        y = torch.cat([net.forward(x[i:i + 256].contiguous()) for i in range(0, n, 256)])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_inf += e0.elapsed_time(e1)
-        e0.record(stream)
-        iw = net.pcg(s, y, n, maxit=500, tol=1e-6)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_w += e0.elapsed_time(e1)
-        _, t_cg = net.samples(s)
-        errs.append(float((t_cg - t).norm() / t.norm()))
-        fallbacks += int((iw > 500).sum())
-        s.solve_mbf(f)
-        e0.record(stream)
-        iz = net.pcg(s, None, n, maxit=500, tol=1e-6)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_z += e0.elapsed_time(e1)
-        it_w.append(iw.float().mean().item())
-        it_z.append(iz.float().mean().item())
-        nsamp += n
+        Kd = field(sd)
+
+        def learned_once(use_net):
+            sl.factor_local(Kd, stream=stream)
+            pred = None
+            if use_net:
+                x, _ = net.samples(sl, targets=False)
+                pred = net.predict(x)
+            sl.solve_mbf_learned(f, net=net if use_net else None, pred=pred, stream=stream)
+            sl.assemble_interface(stream=stream)
+            X = sl.solve_interface(stream=stream)
+            return sl.reconstruct(X, stream=stream)[:2]
+
+        times = {}
+        for use_net in (True, False):
+            learned_once(use_net)                              # warm-up (tables, attributes)
+            e0.record(stream)
+            p_l, u_l = learned_once(use_net)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[use_net] = (e0.elapsed_time(e1), sl.read_cg_iterations(), sl.read_fallback(), sl.read_status()[1],
+                              p_l.clone(), u_l.clone())
+        t_m, o_m = _timed_graph(sm, Kd, f, stream, steps=5)
+        t_64, o_64 = _timed_graph(s64, Kd, f, stream, steps=3)
+        ms_n, it_n, (fb_n, lost_n), st_n, p_n, u_n = times[True]
+        kept.append((Kd.cpu().numpy(), p_n.cpu().numpy().ravel(), u_n.cpu().numpy()))
+        ms_z, it_z, (fb_z, _), _, _, _ = times[False]
+        rows.append({"seed": sd, "ms_learned": round(ms_n, 4), "ms_learned_from_zero": round(ms_z, 4),
+                     "ms_direct_mixed": round(t_m, 4), "ms_fp64": round(t_64, 4),
+                     "cg_iterations": it_n, "cg_iterations_from_zero": it_z,
+                     "fallback_subdomains": fb_n, "fallback_from_zero": fb_z, "unconverged": st_n["unconverged"],
+                     "rel_err_vs_fp64": {"p": _rel(p_n.ravel(), o_64[1].ravel()), "u": _rel(u_n, o_64[2])}})
+    del sl, sm, s64
+    agg = lambda k: round(sum(rw[k] for rw in rows) / len(rows), 4)  # noqa: E731
     return {
         "workload": "40x40x10 cells, 32 subdomains of 10x10x5, 5x2 patches, sigma=2 lambda=8 Kz=0.1Kx",
         "train": {"fields": train_fields, "seeds": f"1-{train_fields}", "samples": n_train,
                   "epochs": epochs, "steps": steps, "samples_per_s": round(steps * 256 / (train_ms / 1e3), 1),
                   "loss": final_loss, "loss_of_mean_guess": floor},
-        "eval": {"fields": eval_fields, "seeds": f"201-{200 + eval_fields}", "p_mbf_samples": nsamp,
-                 "cg_iters_warm": round(sum(it_w) / len(it_w), 2), "cg_iters_zero": round(sum(it_z) / len(it_z), 2),
-                 "cg_ms_per_sample_warm": round(t_w / nsamp, 5), "cg_ms_per_sample_zero": round(t_z / nsamp, 5),
-                 "inference_ms_per_sample": round(t_inf / nsamp, 5),
-                 "direct_fp64_ms_per_subdomain_set": round(t_dir / (eval_fields * 32), 5),
-                 "rel_err_vs_direct_fp64": max(errs), "cg_tol": 1e-6, "fallbacks_to_direct": fallbacks},
-        "note": "FP32 CG reaches its 1e-6 tolerance, not the 1e-8 of the mixed form; the direct FP64-refined "
-                "MBFs stay the fallback and the reference",
+        "eval": {"fields": eval_fields, "seeds": f"201-{200 + eval_fields}",
+                 "ms_learned_solve": agg("ms_learned"), "ms_learned_solve_from_zero": agg("ms_learned_from_zero"),
+                 "ms_direct_mixed_solve": agg("ms_direct_mixed"), "ms_fp64_solve": agg("ms_fp64"),
+                 "cg_iterations": agg("cg_iterations"), "cg_iterations_from_zero": agg("cg_iterations_from_zero"),
+                 "fallback_rate": round(sum(rw["fallback_subdomains"] for rw in rows) / (32 * len(rows)), 4),
+                 "rel_err_vs_fp64_max": max(max(rw["rel_err_vs_fp64"].values()) for rw in rows),
+                 "per_field": rows},
+        "_kept": {"n": (nx, ny, nz), "edges": edges, "patch": ((5, 2),) * 3, "f": f.cpu().numpy(), "fields": kept},
+        "note": "learned form = every MBF and particular column by FP32 CG (warm-started from the network for "
+                "P- and U-MBFs) inside FP64 refinement to 1e-9, FP64 direct fallback; timed from K to p, u "
+                "including inference; the direct mixed form is the graph-replayed solve of the same workload",
     }
 
 
@@ -375,7 +405,9 @@ def variants_sections(make, w, K, dev, stream, fd, u_ms, n_sub):
             kw = dict(beta_mode=1, alpha=alpha, patch=patch)
             s64 = make("fp64", **kw)
             t64, o64 = _timed_graph(s64, Kd, fd, stream, steps=3)
-            sm = make("fp32_ir", **kw)
+            # alpha = 1e+6 leaves the local problems nearly pure Neumann (condition ~1e8): the
+            # FP32 factor fails there and every subdomain needs the FP64 fallback
+            sm = make("fp32_ir", fallback_cap=n_sub if alpha >= 1e6 else 0, **kw)
             tm, om = _timed_graph(sm, Kd, fd, stream, steps=5)
             code, st = sm.read_status()
             fb, lost = sm.read_fallback()
@@ -669,6 +701,9 @@ def main():
     kern_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / max(sum(x[1] for x in kprof.values()), 1e-9), 4)}
                   for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])}
 
+    learned = None
+    if not args.no_learned and args.workload == "c2":
+        learned = learned_form(dev, stream)
     cpu, vs_oracle = None, None
     if not args.no_cpu_baseline:
         if args.workload in FULL_ORACLE:
@@ -683,6 +718,8 @@ def main():
             vs_oracle = {"p": rel(pg, r.p), "u": rel(ug, r.u.ravel()), "X": rel(Xg, r.X), "tol": 1e-8}
             vs_oracle["ok"] = bool(max(vs_oracle["p"], vs_oracle["u"], vs_oracle["X"]) <= 1e-8)
             del r
+            if learned is not None:
+                learned["eval"]["rel_err_vs_oracle_max"] = learned_vs_oracle(learned["_kept"])
         else:
             n_s, dt = oracle_sample(w, K, f, max(64, n_sub // 100))
             cpu = {"value": round(n_s / dt, 3), "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
@@ -725,8 +762,9 @@ def main():
         line["cpu_baseline"] = cpu
     if not args.no_variants and args.workload == "c2":
         line.update(variants_sections(make, w, K, dev, stream, fd, outs[2], n_sub))
-    if not args.no_learned and args.workload == "c2":
-        line["learned"] = learned_form(dev, stream)
+    if learned is not None:
+        learned.pop("_kept", None)
+        line["learned"] = learned
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

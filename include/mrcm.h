@@ -71,7 +71,8 @@ enum {
     MRCM_FP64 = 0,          /* local factor and solves in FP64 (one FP64 refinement step) */
     MRCM_FP32_IR = 1,       /* FP32 factor/solves + FP64 iterative refinement */
     MRCM_TF32_IR = 2,       /* tensor-core TF32 solves + FP64 iterative refinement */
-    MRCM_LEARNED_PCG = 3    /* learned warm start + PCG (reserved) */
+    MRCM_LEARNED_PCG = 3    /* learned form: MBFs by warm-started FP32 CG inside FP64 refinement
+                               (mrcm_solve_mbf_learned), FP64 direct fallback */
 };
 
 /* Problem description (Sec. "Domain decomposition and Darcy solvers").
@@ -392,10 +393,38 @@ void mrcm_net_destroy(mrcm_net* net);
  * log(Kx)/4, log(Kz)/4, the cells next to the faces of basis c (1, else 0) and the
  * cells next to any Robin face; target[s] is the FP64 column rounded to FP32.
  * *n_samples = min(available, max_samples); x/target may be NULL to count.
+ * Inputs alone (target NULL) need only mrcm_factor_local; targets need the
+ * MBFs (after mrcm_solve_mbf).
  * The first call per box shape uploads a small sample table owned by the
  * handle. */
 mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, float* x, float* target,
                              int max_samples, int* n_samples, void* stream);
+
+/* The learned form of mrcm_solve_mbf, for a handle set up with precision
+ * MRCM_LEARNED_PCG (after mrcm_factor_local, which then assembles the local
+ * coefficients without factoring).  Every MBF and particular column of every
+ * subdomain (Eq. multiscale_functions, Eq. particular_problem_discrete) is
+ * solved by FP64 iterative refinement: r = b - A x in FP64, the correction
+ * from FP32 conjugate gradients on the Jacobi-scaled local system (to a
+ * relative residual of 1e-4, at most cg_maxit iterations), x += correction,
+ * at most max_outer corrections, until ||r|| <= ir_tol ||b|| (cfg.ir_tol, or
+ * 1e-9 when 0).  The first iterate of a P-MBF column is the network's
+ * prediction for it; of a U-MBF column, -beta s times the prediction of the
+ * same basis; of the particular column, zero.  Subdomains with a column
+ * that does not reach the tolerance are factored and solved again in FP64
+ * (the direct fallback, cfg.fallback_cap slots at a time; counted by
+ * mrcm_read_fallback).  Then the traces, as mrcm_solve_mbf.
+ *  net, pred  the network and its predictions, FP32 [n_pred][D][H][W] in the
+ *             sample order of mrcm_net_samples; pred NULL = every column from zero
+ *  f          device FP64 [nz][ny][nx] source density
+ * The first call allocates a small column table owned by the handle (make it
+ * before any stream capture).  CG iterations: mrcm_read_cg_iterations. */
+mrcm_status mrcm_solve_mbf_learned(mrcm_handle* h, const mrcm_net* net, const float* pred, int n_pred,
+                                   const double* f, int cg_maxit, int max_outer, void* ws, void* stream);
+
+/* Conjugate-gradient iterations of the last mrcm_solve_mbf_learned, summed over
+ * columns (read back synchronously). */
+mrcm_status mrcm_read_cg_iterations(mrcm_handle* h, void* ws, long long* iters);
 
 /* FP32 conjugate gradients on the Jacobi-scaled local system of each of the
  * first n_samples samples (order of mrcm_net_samples), from x0[s] (unscaled

@@ -87,6 +87,9 @@ SIGNATURES = {
     "mrcm_net_train_step": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_float, C.c_int] + [C.c_void_p] * 3),
     "mrcm_net_destroy": (None, [C.c_void_p]),
     "mrcm_net_samples": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "mrcm_solve_mbf_learned": (C.c_int, [C.c_void_p] * 3 + [C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                                               C.c_void_p]),
+    "mrcm_read_cg_iterations": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "mrcm_pcg_mbf": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "mrcm_measure_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mrcm_destroy": (None, [C.c_void_p]),

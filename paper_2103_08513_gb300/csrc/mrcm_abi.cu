@@ -39,7 +39,7 @@ void load_tune_cache(mrcm_handle* h);
 
 void free_device(mrcm::DeviceTables& d) {
     void* ptrs[] = {d.subs, d.faces, d.Ilist, d.class_list, d.solve_list, d.rowptr, d.colidx, d.src_lo, d.src_hi, d.rhs_src_lo,
-                    d.rhs_src_hi, d.fronts, d.front_maps, d.front_inv, d.front_dofs, d.level_ids};
+                    d.rhs_src_hi, d.fronts, d.front_maps, d.front_inv, d.front_dofs, d.level_ids, d.pp_subs};
     for (void* p : ptrs) if (p) cudaFree(p);
     d = mrcm::DeviceTables();
 }
@@ -81,6 +81,7 @@ mrcm_status ensure_device(mrcm_handle* h, void* stream) {
     UP(front_inv, t.front_inv);
     UP(front_dofs, t.front_dofs);
     UP(level_ids, lvl);
+    if (!t.pp_subs.empty()) UP(pp_subs, t.pp_subs);
 #undef UP
     int rc = mrcm::configure_local(t, d);
     if (!rc) rc = mrcm::configure_interface(t, d);
@@ -261,6 +262,8 @@ mrcm_status mrcm_solve_mbf(mrcm_handle* h, const double* f, void* ws, void* stre
     mrcm_status st = check_ws(h, ws);
     if (st != MRCM_OK) return st;
     if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
+    if (h->t.cfg.precision == MRCM_LEARNED_PCG)
+        return fail(h, MRCM_ERR_INVALID_ARG, "the learned form solves its MBFs with mrcm_solve_mbf_learned");
     h->f = f;
     int sweeps = h->t.cfg.precision == MRCM_FP64 ? 0 : h->t.cfg.ir_max_sweeps;
     double tol = h->t.cfg.ir_tol > 0 ? h->t.cfg.ir_tol : 1e-14;
@@ -315,8 +318,9 @@ mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u
     const char* b = (const char*)u_out;
     if (a < b + ub && b < a + ub) return fail(h, MRCM_ERR_INVALID_ARG, "u and u_out overlap");
     if (h->stage < 4) return fail(h, MRCM_ERR_STATE, "the multiscale solve must run first");
+    if (!h->t.pp_ok) return fail(h, MRCM_ERR_NOT_IMPLEMENTED, "a slab block too large for the FP64 post-processing factor");
     const int precision = h->t.cfg.precision;
-    const int sweeps = precision == MRCM_FP64 ? 0 : std::max(h->t.cfg.ir_max_sweeps, 8);
+    const int sweeps = 2;                // FP64 refinement steps of the FP64 Neumann solves
     const double tol = h->t.cfg.ir_tol > 0 ? h->t.cfg.ir_tol : 1e-14;
     int rc = mrcm::launch_postprocess(h->t, h->d, h->lay, (char*)ws, u, u_out, mres, h->f, precision, sweeps, tol,
                                       stream, h->prof);
@@ -432,6 +436,7 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
     mrcm_status st = check_ws(h, ws);
     if (st != MRCM_OK) return st;
     if (h->stage < 1) return fail(h, MRCM_ERR_STATE, "mrcm_factor_local must run first");
+    if (h->t.cfg.precision == MRCM_LEARNED_PCG) return fail(h, MRCM_ERR_INVALID_ARG, "the learned form has no direct solve to tune");
     int v0 = 0, v1 = 0, v2 = h->d.factor_variant, v3 = h->d.factor_mid_variant;
     float ms[2 * mrcm::kMaxSolveVariants];
     int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, &v2, &v3, ms);
@@ -545,6 +550,7 @@ void mrcm_destroy(mrcm_handle* h) {
     drop_graph(h);
     if (h->samp_off) cudaFree(h->samp_off);
     if (h->samp_list) cudaFree(h->samp_list);
+    if (h->col_list) cudaFree(h->col_list);
     free_device(h->d);
     delete h;
 }

@@ -121,6 +121,14 @@ struct Tables {
     double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
     int pin_front = -1;
+
+    // mixed modes: the FP64 post-processing factors the Neumann problems into
+    // the W region in FP64 waves (pp_wave_off into solve_list; pp_subs are the
+    // subdomain records with the FP64 block offsets and one forward-value
+    // column per cell); pp_ok is false when some block cannot take it
+    std::vector<SubInfo> pp_subs;
+    std::vector<int> pp_wave_off;
+    bool pp_ok = true;
 };
 
 // Workspace layout (byte offsets into the caller's workspace).
@@ -158,8 +166,9 @@ struct DeviceTables {
     int* front_inv = nullptr;
     int* front_dofs = nullptr;
     int* level_ids = nullptr;                  // fronts of all levels, concatenated
-    size_t fb_solve_smem = 0;                  // dynamic shared memory of the FP64 fallback solve
-    int fb_occ = 1;
+    size_t f64_solve_smem = 0;                 // mixed modes: dynamic shared memory of the FP64 solve kernels
+    int f64_occ = 1;                           // (fallback, post-processing) and their CTAs per SM
+    SubInfo* pp_subs = nullptr;
     std::vector<int> level_off;                // host: offsets of each level in level_ids
     int device = -1;
     bool ready = false;
@@ -256,6 +265,7 @@ enum StatusWord { ST_NOT_SPD = 0, ST_UNCONVERGED = 1, ST_ZERO_PIVOT = 2, ST_SWEE
                   ST_FB_TOTAL = 7 /* subdomains re-solved in FP64 */,
                   ST_SWEPT = 8 /* 64-bit counter at words 8-9 */,
                   ST_FB_LOST = 10 /* subdomains that needed the fallback and could not have it */,
+                  ST_CG_ITERS = 12 /* 64-bit counter at words 12-13: CG iterations of the learned form */,
                   ST_COUNT = 16 };
 
 // FP64 fallback of the mixed modes: slots per wave and FP64 block-factor
@@ -292,6 +302,8 @@ struct mrcm_handle {
     cudaGraphExec_t graph_exec = nullptr;
     const void* graph_key[9] = {};
     long long graph_launches = 0;
+    int* col_list = nullptr;              // learned-path (subdomain, column) list of every MBF column
+    int n_cols = 0;
     int* samp_off = nullptr;              // learned-path sample tables (internal)
     int* samp_list = nullptr;
     int samp_shape[3] = {0, 0, 0};
@@ -325,6 +337,8 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
 int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* u,
                        double* u_out, double* mres, const double* f, int precision, int sweeps, double tol,
                        void* stream, Prof& P);
+int launch_local_finish(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
+                        void* stream, Prof& P);
 int launch_reconstruct(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                        const double* X, double* p, double* u, double* mres, const double* K,
                        const double* f, void* stream, Prof& P);

@@ -483,7 +483,7 @@ k_gather_samples(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ 
         const int smp = base + c;
         if (smp >= max_samples) return;
         float* xin = xs + (long long)smp * 4 * N;
-        float* tg = ts + (long long)smp * N;
+        float* tg = ts ? ts + (long long)smp * N : nullptr;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
             int lc[3];
             slab_coords(s, e, lc);
@@ -493,7 +493,7 @@ k_gather_samples(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ 
             xin[N + lex] = kLogKScale * (float)log(K[2 * ncells + gcell]);
             xin[2 * N + lex] = 0.0f;
             xin[3 * N + lex] = 0.0f;
-            tg[lex] = (float)X[s.x_off + (long long)c * N + e];
+            if (tg) tg[lex] = (float)X[s.x_off + (long long)c * N + e];
         }
         __syncthreads();
         for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
@@ -629,6 +629,169 @@ k_pcg_sample(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ face
     if (threadIdx.x == 0) iters[smp] = rr > tol2 ? maxit + 1 : it;
 }
 
+// Learned form of the local solves (one CTA per MBF or particular column):
+// FP64 iterative refinement, r = b - A x in FP64, whose correction equations
+// A^ z = S r are solved by FP32 conjugate gradients on the Jacobi-scaled
+// system to a relative residual of 1e-4 (or cg_maxit iterations), x += S z.
+// The start x0 is the network's prediction for a P-MBF column, -beta s times
+// that prediction for the U-MBF column of the same basis (exact when beta is
+// constant on the patch), zero for the particular column.  A column whose
+// FP64 residual reaches ||r|| <= tol ||b|| gets conv = 1; the others are left
+// to the FP64 direct fallback.
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256)
+k_learned_column(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces, const int* __restrict__ col_list,
+                 const double* __restrict__ coef, const double* __restrict__ scale,
+                 const double* __restrict__ face_tr, const double* __restrict__ face_u,
+                 const double* __restrict__ face_beta, const double* __restrict__ rhs_part,
+                 const double* __restrict__ f, int nx, int ny, double vol, long long nct,
+                 const int* __restrict__ soff, const float* __restrict__ pred, int n_pred, int cg_maxit,
+                 int max_outer, double tol, double* __restrict__ X, int* __restrict__ conv, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char lsm[];
+    const int l = col_list[2 * blockIdx.x], j = col_list[2 * blockIdx.x + 1];
+    const SubInfo s = subs[l];
+    const int N = s.N, b = s.b, su = s.su, nI = s.nI, m = s.m;
+    double* x = reinterpret_cast<double*>(lsm);
+    double* bb = x + N;
+    float* dd = reinterpret_cast<float*>(bb + N);
+    float* tu = dd + N;
+    float* tv = tu + N;
+    float* ts = tv + N;
+    float* z = ts + N;
+    float* r = z + N;
+    float* p = r + N;
+    float* q = p + N;
+    __shared__ float red[32];
+    __shared__ double redd[32];
+    __shared__ double wscale_s;
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* sc = scale + s.cell_off;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const int i = c % b, u = i % su;
+        dd[c] = (float)(cd[c] * sc[c] * sc[c]);
+        tu[c] = u + 1 < su ? (float)(cu[c] * sc[c] * sc[c + 1]) : 0.0f;
+        tv[c] = i + su < b ? (float)(cv[c] * sc[c] * sc[c + su]) : 0.0f;
+        ts[c] = c + b < N ? (float)(cs[c] * sc[c] * sc[c + b]) : 0.0f;
+        double bv = 0.0;
+        if (j == m - 1) {
+            int lc[3];
+            slab_coords(s, c, lc);
+            const long long g = (s.o[0] + lc[0]) + (long long)nx * ((s.o[1] + lc[1]) + (long long)ny * (s.o[2] + lc[2]));
+            bv = rhs_part[s.cell_off + c] + f[g] * vol;
+        }
+        bb[c] = bv;
+        x[c] = 0.0;
+    }
+    if (threadIdx.x == 0) wscale_s = 1.0;
+    __syncthreads();
+    const int pc = j < nI ? j : (j < 2 * nI ? j - nI : -1);       // the basis of an MBF column
+    if (j < m - 1) {
+        for (int e = threadIdx.x; e < s.nface; e += blockDim.x) {
+            const FaceInfo fi = faces[s.face_off + e];
+            if (fi.col != pc) continue;
+            bb[fi.cell] = j < nI ? face_tr[s.face_off + e] : face_u[s.face_off + e];
+            if (j >= nI) wscale_s = -face_beta[s.face_off + e] * fi.s;    // any face of the basis (a benign race)
+        }
+    }
+    __syncthreads();
+    if (pred && soff && pc >= 0 && soff[l] >= 0 && soff[l] + pc < n_pred) {
+        const float* pr = pred + (long long)(soff[l] + pc) * N;
+        const double ws = j < nI ? 1.0 : wscale_s;
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            int lc[3];
+            slab_coords(s, c, lc);
+            x[c] = ws * (double)pr[lc[0] + s.sz[0] * (lc[1] + s.sz[1] * lc[2])];
+        }
+    }
+    __syncthreads();
+    auto matvec = [&](const float* v, float* out) {
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const int i = c % b, u = i % su;
+            float a = dd[c] * v[c];
+            if (u + 1 < su) a -= tu[c] * v[c + 1];
+            if (u > 0) a -= tu[c - 1] * v[c - 1];
+            if (i + su < b) a -= tv[c] * v[c + su];
+            if (i >= su) a -= tv[c - su] * v[c - su];
+            if (c + b < N) a -= ts[c] * v[c + b];
+            if (c >= b) a -= ts[c - b] * v[c - b];
+            out[c] = a;
+        }
+    };
+    auto dot = [&](const float* a, const float* bv) -> float {
+        float acc = 0.0f;
+        for (int c = threadIdx.x; c < N; c += blockDim.x) acc = fmaf(a[c], bv[c], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        return t;
+    };
+    double bn = 0.0;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) bn += bb[c] * bb[c];
+    bn = block_sum_d(bn, redd);
+    long long iters = 0;
+    int ok = 0;
+    for (int o = 0; o <= max_outer; ++o) {
+        // FP64 residual of the unscaled system, the scaled right-hand side of the correction
+        double rr = 0.0;
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const int i = c % b, u = i % su;
+            double a = cd[c] * x[c];
+            if (u + 1 < su) a = fma(-cu[c], x[c + 1], a);
+            if (u > 0) a = fma(-cu[c - 1], x[c - 1], a);
+            if (i + su < b) a = fma(-cv[c], x[c + su], a);
+            if (i >= su) a = fma(-cv[c - su], x[c - su], a);
+            if (c + b < N) a = fma(-cs[c], x[c + b], a);
+            if (c >= b) a = fma(-cs[c - b], x[c - b], a);
+            const double res = bb[c] - a;
+            rr = fma(res, res, rr);
+            r[c] = (float)(res * sc[c]);
+            z[c] = 0.0f;
+            p[c] = r[c];
+        }
+        rr = block_sum_d(rr, redd);
+        if (rr <= tol * tol * bn) { ok = 1; break; }
+        if (o == max_outer) break;
+        float rho = dot(r, r);
+        const float stop = 1e-8f * rho;                  // relative residual 1e-4
+        for (int k = 0; k < cg_maxit && rho > stop; ++k) {
+            matvec(p, q);
+            __syncthreads();
+            const float alpha = rho / dot(p, q);
+            for (int c = threadIdx.x; c < N; c += blockDim.x) { z[c] = fmaf(alpha, p[c], z[c]); r[c] = fmaf(-alpha, q[c], r[c]); }
+            __syncthreads();
+            const float rho2 = dot(r, r);
+            const float beta = rho2 / rho;
+            rho = rho2;
+            for (int c = threadIdx.x; c < N; c += blockDim.x) p[c] = fmaf(beta, p[c], r[c]);
+            __syncthreads();
+            ++iters;
+        }
+        for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = fma((double)z[c], sc[c], x[c]);
+        __syncthreads();
+    }
+    double* Xc = X + s.x_off + (long long)j * N;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) Xc[c] = x[c];
+    if (threadIdx.x == 0) {
+        conv[s.rhs_off + j] = ok;
+        atomicAdd(reinterpret_cast<unsigned long long*>(status + ST_CG_ITERS), (unsigned long long)iters);
+    }
+}
+
 }  // namespace
 }  // namespace mrcm
 
@@ -676,19 +839,72 @@ extern "C" {
 mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, float* x, float* target,
                              int max_samples, int* n_samples, void* stream) {
     if (!h || !net || !ws || !n_samples) return MRCM_ERR_INVALID_ARG;
-    if (h->stage < 2) return MRCM_ERR_STATE;
+    if (h->stage < (target ? 2 : 1)) return MRCM_ERR_STATE;     // inputs need K, targets the MBFs
     if (net->in_ch != 4) return MRCM_ERR_INVALID_ARG;
     int *soff, *slist, cnt;
     mrcm_status st = sample_tables(h, net->D, net->H, net->W, &soff, &slist, &cnt);
     if (st != MRCM_OK) return st;
     *n_samples = std::min(cnt, std::max(max_samples, 0));
-    if (!x || !target || *n_samples == 0) return MRCM_OK;
+    if (!x || *n_samples == 0) return MRCM_OK;
     const mrcm::Tables& t = h->t;
     cudaStream_t s = (cudaStream_t)stream;
     mrcm::k_gather_samples<<<(int)t.subs.size(), 256, 0, s>>>(h->d.subs, h->d.faces, soff, h->K,
         (const double*)((char*)ws + h->lay.X), t.cfg.nx, t.cfg.ny, t.n_cells, max_samples, x, target);
     mrcm::k_gather_mask<<<(int)t.subs.size(), 256, 0, s>>>(h->d.subs, h->d.faces, soff, max_samples, x);
     return cudaGetLastError() == cudaSuccess ? MRCM_OK : MRCM_ERR_CUDA;
+}
+
+mrcm_status mrcm_solve_mbf_learned(mrcm_handle* h, const mrcm_net* net, const float* pred, int n_pred,
+                                   const double* f, int cg_maxit, int max_outer, void* ws, void* stream) {
+    if (!h || !ws || !f || cg_maxit < 0 || max_outer < 0 || n_pred < 0) return MRCM_ERR_INVALID_ARG;
+    const mrcm::Tables& t = h->t;
+    if (t.cfg.precision != MRCM_LEARNED_PCG) { h->err = "handle precision is not MRCM_LEARNED_PCG"; return MRCM_ERR_INVALID_ARG; }
+    if (h->stage < 1) { h->err = "mrcm_factor_local must run first"; return MRCM_ERR_STATE; }
+    if (pred && (!net || net->in_ch != 4)) return MRCM_ERR_INVALID_ARG;
+    if (t.max_N > 4096) return MRCM_ERR_NOT_IMPLEMENTED;
+    if (!h->col_list) {
+        std::vector<int> cl;
+        for (size_t l = 0; l < t.subs.size(); ++l)
+            for (int j = 0; j < t.subs[l].m; ++j) { cl.push_back((int)l); cl.push_back(j); }
+        if (cudaMalloc((void**)&h->col_list, sizeof(int) * std::max<size_t>(cl.size(), 1)) != cudaSuccess)
+            return MRCM_ERR_CUDA;
+        cudaMemcpy(h->col_list, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice);
+        h->n_cols = (int)(cl.size() / 2);
+    }
+    int* soff = nullptr;
+    if (pred) {
+        int *slist, cnt;
+        mrcm_status st = sample_tables(h, net->D, net->H, net->W, &soff, &slist, &cnt);
+        if (st != MRCM_OK) return st;
+        n_pred = std::min(n_pred, cnt);
+    }
+    h->f = f;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    int* status = (int*)(w + h->lay.status);
+    cudaMemsetAsync(status, 0, sizeof(int) * mrcm::ST_COUNT, st);
+    const size_t sm = (size_t)t.max_N * (2 * sizeof(double) + 8 * sizeof(float));
+    cudaFuncSetAttribute(mrcm::k_learned_column, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const double tol = t.cfg.ir_tol > 0 ? t.cfg.ir_tol : 1e-9;
+    if (h->n_cols > 0)
+        mrcm::k_learned_column<<<h->n_cols, 256, sm, st>>>(h->d.subs, h->d.faces, h->col_list,
+            (const double*)(w + h->lay.coef), (const double*)(w + h->lay.scale), (const double*)(w + h->lay.face_tr),
+            (const double*)(w + h->lay.face_u), (const double*)(w + h->lay.face_beta),
+            (const double*)(w + h->lay.rhs_part), f, t.cfg.nx, t.cfg.ny, t.cfg.hx * t.cfg.hy * t.cfg.hz, t.n_cells,
+            soff, pred, n_pred, cg_maxit, max_outer, tol, (double*)(w + h->lay.X), (int*)(w + h->lay.conv), status);
+    int rc = mrcm::launch_local_finish(t, h->d, h->lay, w, f, stream, h->prof);
+    if (rc != 0 || cudaGetLastError() != cudaSuccess) { h->err = "mrcm_solve_mbf_learned: launch failed"; return MRCM_ERR_CUDA; }
+    h->stage = 2;
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_read_cg_iterations(mrcm_handle* h, void* ws, long long* iters) {
+    if (!h || !ws || !iters) return MRCM_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, (char*)ws + h->lay.status + mrcm::ST_CG_ITERS * sizeof(int), sizeof(v),
+                   cudaMemcpyDeviceToHost) != cudaSuccess) return MRCM_ERR_CUDA;
+    *iters = (long long)v;
+    return MRCM_OK;
 }
 
 mrcm_status mrcm_pcg_mbf(mrcm_handle* h, const mrcm_net* net, void* ws, const float* x0, int n_samples,

@@ -1348,7 +1348,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         __syncthreads();
         block_product<T, RT>(Wsm, Z, b, na, mpad, [&](int i, int jj, T v) {
             Yp[i * mpad + jj] = v;
-            Ys[(long long)cols[jj] * N + base + i] = v;
+            Ys[(g.last_only ? 0 : (long long)cols[jj] * N) + base + i] = v;
         });
         __syncthreads();
         refill(sl);
@@ -1360,7 +1360,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         auto finish = [&](int i, int jj, T acc) {
             const int j = cols[jj];
             const long long gi = (long long)j * N + base + i;
-            const T x = Ys[gi] + acc;
+            const T x = Ys[(g.last_only ? 0 : (long long)j * N) + base + i] + acc;
             Yp[i * mpad + jj] = x;                 // Z, not Yp, feeds the product
             const double xo = cp.out(x, base + i);
             if (kSweep) Xs[gi] += xo; else Xs[gi] = xo;
@@ -1824,7 +1824,8 @@ int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char*
                                              (double*)(ws + L.rhs_part), (double*)(ws + L.face_tr),
                                              (double*)(ws + L.face_beta), (double*)(ws + L.face_u),
                                              (double*)(ws + L.face_bst), t.n_cells));
-    if (t.n_waves == 1) launch_factor_wave(t, d, L, ws, precision, 0, st, P);
+    // the learned form solves the local problems iteratively: coefficients only
+    if (t.n_waves == 1 && precision != MRCM_LEARNED_PCG) launch_factor_wave(t, d, L, ws, precision, 0, st, P);
     return (int)cudaGetLastError();
 }
 
@@ -1857,23 +1858,20 @@ int configure_local(const Tables& t, DeviceTables& d) {
         d.solve_occ[v] = std::max(1, occ0);
         d.sweep_occ[v] = std::max(1, occ1);
     }
-    {
-        int cap;
-        long long stride;
-        fallback_params(t, &cap, &stride);
-        if (cap > 0) {
-            const int mpad = (t.max_m + 3) & ~3;
-            size_t sm = 0;
-            for (const SubInfo& sb : t.subs)
-                if (sb.b <= kMaxBlock64) sm = std::max(sm, solve_smem_layout<double>(sb.b, mpad, sb.N).total);
-            d.fb_solve_smem = sm + 16;
-            const void* k = solve_kernel<double, false, false>(0);
-            const size_t cur = f64 ? d.solve_smem : 0;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(cur, d.fb_solve_smem));
-            int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, variant_threads(0), d.fb_solve_smem);
-            d.fb_occ = std::max(1, occ);
-        }
+    if (!f64) {
+        // the FP64 solve kernels of the mixed modes' fallback and post-processing (variant 0)
+        const int mpad = (t.max_m + 3) & ~3;
+        size_t sm = 0;
+        for (const SubInfo& sb : t.subs)
+            if (sb.b <= kMaxBlock64) sm = std::max(sm, solve_smem_layout<double>(sb.b, mpad, sb.N).total);
+        d.f64_solve_smem = sm + 16;
+        const void* k0 = solve_kernel<double, false, false>(0);
+        const void* k1 = solve_kernel<double, false, true>(0);
+        cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.f64_solve_smem);
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.f64_solve_smem);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1, variant_threads(0), d.f64_solve_smem);
+        d.f64_occ = std::max(1, occ);
     }
     cudaFuncSetAttribute(k_block_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)factor_smem<double>(std::min(t.max_b, kMaxBlock64)));
@@ -1940,13 +1938,18 @@ static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout
     g.nlist_dev = status + ST_FB_WAVE;
     g.Ybuf = (void*)(ws + L.fb_Y);
     g.last_only = 0;
-    g.bar_off = (int)d.fb_solve_smem - 16;
-    const void* k = solve_kernel<double, false, false>(0);
-    const int grid = std::max(1, std::min(cap, d.sms * d.fb_occ));
+    g.bar_off = (int)d.f64_solve_smem - 16;
+    g.count_unconverged = 0;
+    const int grid = std::max(1, std::min(cap, d.sms * d.f64_occ));
     const void* Wfb = (const void*)(ws + L.fb_W);
-    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
     void* args[] = {(void*)&g, (void*)&Wfb};
-    MRCM_LAUNCH(P, "k_fb_solve", st, cudaLaunchKernel(k, dim3(grid), dim3(variant_threads(0)), args, d.fb_solve_smem, st));
+    // the FP64 form's solve: direct solve through the FP64 block inverses, then one FP64 refinement step
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+    MRCM_LAUNCH(P, "k_fb_solve", st, cudaLaunchKernel(solve_kernel<double, false, false>(0), dim3(grid),
+                dim3(variant_threads(0)), args, d.f64_solve_smem, st));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+    MRCM_LAUNCH(P, "k_fb_solve", st, cudaLaunchKernel(solve_kernel<double, false, true>(0), dim3(grid),
+                dim3(variant_threads(0)), args, d.f64_solve_smem, st));
 }
 
 int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
@@ -2010,16 +2013,44 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
     g.tol2 = tol * tol;
     g.last_only = 1;
     const void* W = (const void*)(ws + L.W);
-    for (int w = 0; w < t.n_waves; ++w) {
-        launch_factor_wave(t, d, L, ws, precision, w, st, P);
-        g.list = d.solve_list + t.wave_off[w];
-        g.nlist = t.wave_off[w + 1] - t.wave_off[w];
-        g.count_unconverged = 0;
-        launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
-        if (precision != MRCM_FP64) {
+    if (precision == MRCM_FP64) {
+        for (int w = 0; w < t.n_waves; ++w) {
+            launch_factor_wave(t, d, L, ws, precision, w, st, P);
+            g.list = d.solve_list + t.wave_off[w];
+            g.nlist = t.wave_off[w + 1] - t.wave_off[w];
+            g.count_unconverged = 0;
+            launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+            }
+        }
+    } else {
+        // the tied Neumann blocks are too ill-conditioned for an FP32 factor: FP64 block
+        // factors in the W region, wave by wave, FP64 solve and refinement of the one column
+        g.subs = d.pp_subs;
+        g.bar_off = (int)d.f64_solve_smem - 16;
+        const int nw = (int)t.pp_wave_off.size() - 1;
+        int bmax = 0;
+        for (const SubInfo& s : t.subs) bmax = std::max(bmax, s.b);
+        for (int w = 0; w < nw; ++w) {
+            const int n = t.pp_wave_off[w + 1] - t.pp_wave_off[w];
+            g.list = d.solve_list + t.pp_wave_off[w];
+            g.nlist = n;
+            MRCM_LAUNCH(P, "k_pp_factor", st, k_block_factor<double, false><<<n, kThreads, factor_smem<double>(bmax), st>>>(
+                        d.pp_subs, g.list, coef, (const double*)(ws + L.scale), (double*)(ws + L.W), status, t.n_cells,
+                        nullptr, nullptr, nullptr));
+            const int grid = std::max(1, std::min(n, d.sms * d.f64_occ));
+            void* args[] = {(void*)&g, (void*)&W};
+            g.count_unconverged = 0;
+            MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+            MRCM_LAUNCH(P, "k_pp_solve", st, cudaLaunchKernel(solve_kernel<double, false, false>(0), dim3(grid),
+                        dim3(variant_threads(0)), args, d.f64_solve_smem, st));
+            for (int it = 0; it < sweeps; ++it) {
+                g.count_unconverged = it + 1 == sweeps ? 1 : 0;
+                MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
+                MRCM_LAUNCH(P, "k_pp_solve", st, cudaLaunchKernel(solve_kernel<double, false, true>(0), dim3(grid),
+                            dim3(variant_threads(0)), args, d.f64_solve_smem, st));
             }
         }
     }
@@ -2029,6 +2060,35 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
     MRCM_LAUNCH(P, "k_pp_velocity", st, k_pp_velocity<<<nsub, kThreads, 0, st>>>(d.subs, (const double*)(ws + L.X), coef, u,
                 f, geo, t.n_cells, u_out, mbits));
     if (mres) cudaMemcpyAsync(mres, mbits, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return (int)cudaGetLastError();
+}
+
+// After the learned form's column solves (which leave conv[] = 1 on the
+// columns within the tolerance): the FP64 direct fallback of every subdomain
+// with a column that is not, then the traces of all columns.
+int launch_local_finish(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const double* f,
+                        void* stream, Prof& P) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int* status = (int*)(ws + L.status);
+    const int nsub = (int)t.subs.size();
+    LocalArgs g = local_args(t, d, L, ws, f);
+    int fb_cap = 0;
+    long long fb_stride = 0, fb_ystride = 0;
+    fallback_params(t, &fb_cap, &fb_stride, &fb_ystride);
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_TOTAL, 0));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_LOST, 0));
+    if (fb_cap > 0) {
+        // in chunks of fb_cap subdomains of the cost-ordered list: each chunk's slots are reused
+        for (int q = 0; q < nsub; q += fb_cap) {
+            LocalArgs gq = g;
+            gq.list = d.solve_list + q;
+            gq.nlist = std::min(fb_cap, nsub - q);
+            launch_fallback(t, d, L, ws, gq, fb_cap, fb_stride, fb_ystride, st, P);
+        }
+    }
+    MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
+                                        (const double*)(ws + L.face_bst),
+                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
     return (int)cudaGetLastError();
 }
 

@@ -120,7 +120,6 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
     if (cfg->beta_mode == MRCM_BETA_CONST && !(cfg->beta_const > 0)) { err = "beta must be > 0"; return MRCM_ERR_INVALID_ARG; }
     if (cfg->beta_mode == MRCM_BETA_ALPHA_H_OVER_K && !(cfg->alpha > 0)) { err = "alpha must be > 0"; return MRCM_ERR_INVALID_ARG; }
     if (cfg->precision < MRCM_FP64 || cfg->precision > MRCM_LEARNED_PCG) { err = "unknown precision"; return MRCM_ERR_INVALID_ARG; }
-    if (cfg->precision == MRCM_LEARNED_PCG) { err = "learned warm start is not part of this entry point"; return MRCM_ERR_NOT_IMPLEMENTED; }
     if (cfg->ir_max_sweeps < 0 || cfg->ir_max_sweeps > 64) { err = "ir_max_sweeps must be in [0, 64]"; return MRCM_ERR_INVALID_ARG; }
     const int nsub = t.N[0] * t.N[1] * t.N[2];
     if (nsub == 1 && !t.has_dirichlet) {
@@ -290,6 +289,26 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
             t.wave_class_off.push_back((int)t.class_list.size());
         }
         for (int k = 0; k < 4; ++k) t.class_off[k] = t.wave_class_off[k];
+        // FP64 post-processing waves of the mixed modes (the W region holds total_w floats)
+        if (cfg->precision != MRCM_FP64) {
+            t.pp_subs = t.subs;
+            t.pp_wave_off.assign(1, 0);
+            const long long cap_d = t.total_w * (long long)sizeof(float) / (long long)sizeof(double);
+            long long cur = 0;
+            for (int q = 0; q < nsub; ++q) {
+                SubInfo& s = t.pp_subs[t.solve_list[q]];
+                const long long need = (long long)s.ns * wstride<double>(s.b);
+                if (s.b > kMaxBlock64 || need > cap_d) t.pp_ok = false;
+                if (q > t.pp_wave_off.back() && cur + need > cap_d) {
+                    t.pp_wave_off.push_back(q);
+                    cur = 0;
+                }
+                s.w_off = cur;
+                s.y_off = s.cell_off;      // one column of forward values per cell
+                cur += need;
+            }
+            t.pp_wave_off.push_back(nsub);
+        }
     }
     t.total_x = x_off;
     t.total_el = el_off;

@@ -82,17 +82,23 @@ class WarmStartNet:
         return raw[: self.n_params].float()
 
     # ---- MRCM side
-    def samples(self, solver, max_samples=None):
-        """(x, target) of every P-MBF of the solver's subdomains with this box shape."""
+    def samples(self, solver, max_samples=None, targets=True):
+        """(x, target) of every P-MBF of the solver's subdomains with this box shape
+        (target None with targets=False: inputs only, after factor_local)."""
         n = C.c_int()
         L.check(self.lib.mrcm_net_samples(solver.handle, self.net, solver.ws_ptr, None, None, 1 << 30, C.byref(n),
                                           _stream()), solver.handle)
         cnt = n.value if max_samples is None else min(n.value, max_samples)
         x = torch.empty((cnt, self.in_channels) + self.shape, dtype=torch.float32, device=self.device)
-        t = torch.empty((cnt, 1) + self.shape, dtype=torch.float32, device=self.device)
-        L.check(self.lib.mrcm_net_samples(solver.handle, self.net, solver.ws_ptr, _ptr(x), _ptr(t), cnt,
-                                          C.byref(n), _stream()), solver.handle)
+        t = torch.empty((cnt, 1) + self.shape, dtype=torch.float32, device=self.device) if targets else None
+        L.check(self.lib.mrcm_net_samples(solver.handle, self.net, solver.ws_ptr, _ptr(x),
+                                          _ptr(t) if t is not None else None, cnt, C.byref(n), _stream()),
+                solver.handle)
         return x, t
+
+    def predict(self, x):
+        """Network output for any number of samples (in batches of the network's batch size)."""
+        return torch.cat([self.forward(x[i:i + self.batch].contiguous()) for i in range(0, x.shape[0], self.batch)])
 
     def pcg(self, solver, x0, n_samples, maxit=500, tol=1e-6):
         """Warm-started FP32 CG of the first n_samples P-MBFs; returns per-sample iterations."""

@@ -107,6 +107,23 @@ class MRCM:
         self._f = f
         L.check(self.lib.mrcm_solve_mbf(self.handle, _ptr(f), self.ws_ptr, _stream(stream)), self.handle)
 
+    def solve_mbf_learned(self, f, net=None, pred=None, cg_maxit=200, max_outer=8, stream=None):
+        """Learned-form MBFs (precision "learned_pcg"): warm-started FP32 CG inside FP64
+        refinement, FP64 direct fallback; pred = the network's P-MBF predictions in
+        sample order (or None: from zero)."""
+        assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous()
+        self._f = f
+        n_pred = int(pred.shape[0]) if pred is not None else 0
+        L.check(self.lib.mrcm_solve_mbf_learned(self.handle, net.net if net is not None else None,
+                                                _ptr(pred) if pred is not None else None, n_pred, _ptr(f),
+                                                int(cg_maxit), int(max_outer), self.ws_ptr, _stream(stream)),
+                self.handle)
+
+    def read_cg_iterations(self):
+        v = C.c_longlong()
+        L.check(self.lib.mrcm_read_cg_iterations(self.handle, self.ws_ptr, C.byref(v)), self.handle)
+        return int(v.value)
+
     def assemble_interface(self, stream=None):
         L.check(self.lib.mrcm_assemble_interface(self.handle, self.ws_ptr, _stream(stream)), self.handle)
 

@@ -159,8 +159,12 @@ def test_setup_rejects_bad_configs(lib):
     cfg.beta_const = -1.0
     assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
     cfg, keep = _cfg(w)
-    cfg.precision = 3
-    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 8
+    cfg.precision = 4
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
+    cfg, keep = _cfg(w)
+    cfg.fallback_cap = -2
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1
+    assert b"fallback_cap" in lib.mrcm_last_error(None)
     cfg, keep = _cfg(w)
     cfg.interface_refine = -2
     assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 1

@@ -26,11 +26,21 @@ VARIANTS = {
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32_ir", 1e-8)])
 @pytest.mark.parametrize("name", list(VARIANTS))
 def test_alpha_variants_match_oracle(name, prec, tol):
+    """At alpha = 1e+6 the Robin transmissibility A/(h/2K + beta) is ~1e-7 of the
+    interior ones: the local matrices are nearly pure Neumann, with condition
+    numbers near 1e8 (the oracle's own LU then carries errors of 1e-16 x 1e8),
+    so the FP64 bar there is 1e-8; the FP32 factor is useless at that
+    conditioning, every subdomain takes the FP64 fallback (cap = all)."""
     w = small(**BASE, **VARIANTS[name])
     prob = oracle.from_workload(w)
     r = oracle.solve_mrcm(prob)
-    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, prec, ir_max_sweeps=10, ir_tol=1e-13)
+    extreme = VARIANTS[name]["alpha"] >= 1e6
+    if extreme:
+        tol = 1e-8
+    s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, prec, ir_max_sweeps=10, ir_tol=1e-13,
+                                         fallback_cap=w.n_sub if extreme else 0)
     ep, eu = rel_l2(p, r.p), rel_l2(u.ravel(), r.u.ravel())
-    print(f"{name} {prec}: p {ep:.3e} u {eu:.3e} status {st}")
+    fb = s.read_fallback()
+    print(f"{name} {prec}: p {ep:.3e} u {eu:.3e} status {st} fallback {fb}")
     assert st["not_spd"] == 0 and st["interface_zero_pivots"] == 0
     assert ep < tol and eu < tol

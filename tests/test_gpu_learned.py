@@ -122,3 +122,61 @@ def test_training_and_warm_start_gain():
     assert it_net.mean() < it_zero.mean()
     err = (t_net[:nsm] - t[:nsm]).norm() / t[:nsm].norm()
     assert float(err) < 1e-4
+
+
+def _learned_solver(n, edges, patch, **kw):
+    from paper_2103_08513_gb300 import MRCM
+    return MRCM(n, edges, patch, precision="learned_pcg", ir_tol=1e-9, **kw)
+
+
+def _learned_solve(s, K, f, net=None, pred=None, cg_maxit=200, max_outer=8):
+    Kd, fd = torch.from_numpy(K).cuda(), torch.from_numpy(f).cuda()
+    s.factor_local(Kd)
+    if net is not None and pred is None:
+        x, _ = net.samples(s, targets=False)
+        pred = net.predict(x)
+    s.solve_mbf_learned(fd, net=net, pred=pred, cg_maxit=cg_maxit, max_outer=max_outer)
+    s.assemble_interface()
+    X = s.solve_interface()
+    p, u, mres = s.reconstruct(X)
+    torch.cuda.synchronize()
+    return p.cpu().numpy().ravel(), u.cpu().numpy(), X.cpu().numpy()
+
+
+def test_learned_form_reaches_the_mixed_bar_against_the_oracle():
+    """The learned form (CG inside FP64 refinement, every column) matches the
+    oracle at 1e-8 with an untrained network's guesses and from zero."""
+    import oracle
+    from synth.configs import small
+    w = small(n=(20, 20, 10), edges=([10, 10], [10, 10], [5, 5]), patch=((5, 2), (5, 2), (5, 2)), sigma=2.0,
+              lam=8.0, kz_ratio=0.1)
+    prob = oracle.from_workload(w)
+    r = oracle.solve_mrcm(prob)
+    net = _net(5, 10, 10, 8, 3, seed=0, batch=64)
+    for use_net in (True, False):
+        s = _learned_solver(w.n, w.edges, w.patch)
+        p, u, X = _learned_solve(s, prob.K, prob.f, net=net if use_net else None)
+        code, st = s.read_status()
+        fb, lost = s.read_fallback()
+        ep, eu = np.linalg.norm(p - r.p) / np.linalg.norm(r.p), np.linalg.norm(u - r.u) / np.linalg.norm(r.u)
+        print(f"learned (net={use_net}): p {ep:.2e} u {eu:.2e} CG iterations {s.read_cg_iterations()} "
+              f"fallback {fb} status {st}")
+        assert st["unconverged"] == 0 and lost == 0
+        assert ep < 1e-8 and eu < 1e-8
+
+
+def test_learned_form_falls_back_to_the_direct_solve():
+    """With one CG iteration and no refinement step no column reaches the
+    tolerance: every subdomain takes the FP64 direct fallback, and the result
+    is the FP64 form's."""
+    import oracle
+    from synth.configs import small
+    from gpu_helpers import run_gpu
+    w = small(n=(20, 20, 10), edges=([10, 10], [10, 10], [5, 5]), patch=((5, 2), (5, 2), (5, 2)), sigma=2.0,
+              lam=8.0, kz_ratio=0.1)
+    prob = oracle.from_workload(w)
+    s64, p64, u64, X64, *_ = run_gpu(w, prob.K, prob.f, "fp64")
+    s = _learned_solver(w.n, w.edges, w.patch, fallback_cap=w.n_sub)
+    p, u, X = _learned_solve(s, prob.K, prob.f, cg_maxit=1, max_outer=0)
+    assert s.read_fallback() == (w.n_sub, 0)
+    assert np.linalg.norm(p - p64) <= 1e-13 * np.linalg.norm(p64)
