@@ -225,7 +225,8 @@ mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double*
  * re-solves its TPFA problem (Eq. aijk, harmonic means) with Neumann data:
  * Ubar.n on its Gamma faces and u.n on the domain walls.  The pure Neumann
  * matrix is factored and solved like the local problems (cfg.precision;
- * mixed precision with max(ir_max_sweeps, 8) FP64 refinement sweeps); the
+ * mixed precision: the tied Neumann blocks in FP64, in waves inside the
+ * factor region, each solve with three FP64 refinement steps); the
  * subdomain's pressure constant is fixed internally (it does not affect the
  * velocity).
  *  u      device FP64 [6][nz][ny][nx]: the multiscale velocity as written by

@@ -320,7 +320,7 @@ mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u
     if (h->stage < 4) return fail(h, MRCM_ERR_STATE, "the multiscale solve must run first");
     if (!h->t.pp_ok) return fail(h, MRCM_ERR_NOT_IMPLEMENTED, "a slab block too large for the FP64 post-processing factor");
     const int precision = h->t.cfg.precision;
-    const int sweeps = 2;                // FP64 refinement steps of the FP64 Neumann solves
+    const int sweeps = 3;                // FP64 refinement steps of the FP64 Neumann solves
     const double tol = h->t.cfg.ir_tol > 0 ? h->t.cfg.ir_tol : 1e-14;
     int rc = mrcm::launch_postprocess(h->t, h->d, h->lay, (char*)ws, u, u_out, mres, h->f, precision, sweeps, tol,
                                       stream, h->prof);
