@@ -243,6 +243,31 @@ mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double*
 mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u_out, double* mass_residual_max,
                                       void* ws, void* stream);
 
+/* Two-phase IMPES with a skipping constant (Alg. overview-code; Sec. "The
+ * fine grid transport solver", Eq. transporte_discreto, Eq. CFL).  Water
+ * saturation S (time rescaled by the porosity), total mobility
+ * lambda(S) = S^2/mu_w + (1-S)^2/mu_o, fractional flow
+ * phi(S) = M S^2 / (M S^2 + (1-S)^2), M = mu_o/mu_w.  For n_steps steps:
+ * every C steps (the first included) K_eff = lambda(S) K is formed, the MRCM
+ * pressure solve runs on it (mrcm_solve, not graph-captured) and its velocity
+ * is post-processed (mrcm_postprocess_velocity), the time step is
+ * dt = cfl min(h) / (phi'_max max|u|) (phi'_max = max of phi' over
+ * S = k/1000); then the explicit upwind step
+ *   S_c += -(dt/V) sum_faces (phi_upwind - phi(S_c)) q_out + dt max(f_c,0) (1 - phi(S_c))
+ * (injectors bring water, producers take the local mixture; walls no-flow).
+ *  K      device FP64 [3][nz][ny][nx] absolute permeability
+ *  f      device FP64 [nz][ny][nx] source density (sums to zero)
+ *  S      device FP64 [nz][ny][nx] saturation, in: S at t = 0, out: after n_steps
+ *  t_out  device FP64 [1] (output, may be NULL): the simulated time
+ *  tws    device transport workspace of mrcm_transport_query bytes (K_eff,
+ *         the solve's p, u, X, the post-processed u, a second S)
+ * NOT_IMPLEMENTED with Dirichlet walls.  The last post-processing leaves the
+ * handle needing mrcm_factor_local (see mrcm_postprocess_velocity). */
+mrcm_status mrcm_transport_query(const mrcm_handle* h, size_t* tws_bytes);
+mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double* S, double mu_w, double mu_o,
+                       double cfl, int C, int n_steps, double* t_out, void* tws, size_t tws_bytes, void* ws,
+                       size_t ws_bytes, void* stream);
+
 /* The whole pressure solve: mrcm_factor_local, mrcm_solve_mbf,
  * mrcm_assemble_interface, mrcm_solve_interface and mrcm_reconstruct in
  * order (arguments as there).  With flags & MRCM_SOLVE_GRAPH the sequence is

@@ -67,6 +67,9 @@ SIGNATURES = {
     "mrcm_solve_interface": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrcm_reconstruct": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "mrcm_postprocess_velocity": (C.c_int, [C.c_void_p] * 6),
+    "mrcm_transport_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "mrcm_impes": (C.c_int, [C.c_void_p] * 4 + [C.c_double] * 3 + [C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                                                   C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
     "mrcm_read_status": (C.c_int, [C.c_void_p, C.c_void_p] + [C.POINTER(C.c_int)] * 4),
     "mrcm_read_fallback": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_read_work": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),

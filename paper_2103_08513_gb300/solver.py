@@ -158,6 +158,22 @@ class MRCM:
                                                    _stream(stream)), self.handle)
         return out, mres
 
+    def impes(self, K, f, S, mu_w=1.0, mu_o=5.0, cfl=0.9, C_skip=10, n_steps=10, stream=None):
+        """Two-phase IMPES (Alg. overview-code): S (nz, ny, nx) is advanced in place by
+        n_steps transport steps, with the MRCM solve + post-processing every C_skip
+        steps; returns the simulated time (device tensor of one element)."""
+        assert S.dtype == torch.float64 and S.is_cuda and S.is_contiguous()
+        nb = C.c_size_t()
+        L.check(self.lib.mrcm_transport_query(self.handle, C.byref(nb)), self.handle)
+        if getattr(self, "_tws", None) is None or self._tws.numel() < nb.value:
+            self._tws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        t = torch.zeros(1, dtype=torch.float64, device=self.device)
+        L.check(self.lib.mrcm_impes(self.handle, _ptr(K), _ptr(f), _ptr(S), C.c_double(mu_w), C.c_double(mu_o),
+                                    C.c_double(cfl), int(C_skip), int(n_steps), _ptr(t), _ptr(self._tws),
+                                    C.c_size_t(self._tws.numel()), self.ws_ptr, C.c_size_t(self.ws_bytes),
+                                    _stream(stream)), self.handle)
+        return t
+
     def outputs(self):
         """Preallocated (X, p, u, mres) device buffers for solve(..., out=...)."""
         nx, ny, nz = self.n
