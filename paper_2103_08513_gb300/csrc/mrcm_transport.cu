@@ -79,27 +79,38 @@ __global__ void k_zero_doubles(double* p, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0.0;
 }
 
-// One upwind step S_in -> S_out with the frozen, single-valued velocity u.
+// phi(S) of every cell (one FP64 division each), read by the step for the
+// upwind faces
 __global__ void __launch_bounds__(kTThreads)
-k_transport_step(const double* __restrict__ S, double* __restrict__ Sn, const double* __restrict__ u,
-                 const double* __restrict__ f, const double* __restrict__ sc, TGeo g, double M) {
-    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+k_frac_flow(const double* __restrict__ S, double* __restrict__ phi, double M, long long n) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        phi[c] = frac_flow(S[c], M);
+}
+
+// One upwind step S_in -> S_out with the frozen, single-valued velocity u and
+// the cells' phi; cell coordinates in 32-bit arithmetic (n < 2^31 cells).
+__global__ void __launch_bounds__(kTThreads)
+k_transport_step(const double* __restrict__ S, double* __restrict__ Sn, const double* __restrict__ phi,
+                 const double* __restrict__ u, const double* __restrict__ f, const double* __restrict__ sc, TGeo g) {
+    const int n = g.n[0] * g.n[1] * g.n[2];
+    const int nxy = g.n[0] * g.n[1];
+    const int stride[3] = {1, g.n[0], nxy};
     const double dt = sc[1];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int co[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / stride[2])};
-        const double phic = frac_flow(S[c], M);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nxy, r = c - k * nxy, j = r / g.n[0];
+        const int co[3] = {r - j * g.n[0], j, k};
+        const double phic = phi[c];
         double acc = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (co[a] + 1 < g.n[a]) {                          // face on the +a side
-                const double q = u[(2 * a + 1) * n + c] * g.area[a];
-                const double phf = q >= 0.0 ? phic : frac_flow(S[c + stride[a]], M);
+                const double q = u[(long long)(2 * a + 1) * n + c] * g.area[a];
+                const double phf = q >= 0.0 ? phic : phi[c + stride[a]];
                 acc -= (phf - phic) * q;
             }
             if (co[a] > 0) {                                   // face on the -a side
-                const double q = -(u[(2 * a) * n + c] * g.area[a]);
-                const double phf = q >= 0.0 ? phic : frac_flow(S[c - stride[a]], M);
+                const double q = -(u[(long long)(2 * a) * n + c] * g.area[a]);
+                const double phf = q >= 0.0 ? phic : phi[c - stride[a]];
                 acc -= (phf - phic) * q;
             }
         }
@@ -120,7 +131,7 @@ double frac_flow_slope_max(double M) {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TLayout {
-    size_t ke, u, upp, p, X, S2, sc, total;
+    size_t ke, u, upp, p, X, S2, phi, sc, total;
 };
 
 TLayout transport_layout(const Tables& t) {
@@ -133,6 +144,7 @@ TLayout transport_layout(const Tables& t) {
     L.p = o; o = al256(o + n * sizeof(double));
     L.X = o; o = al256(o + std::max<size_t>(2 * (size_t)t.NV, 1) * sizeof(double));
     L.S2 = o; o = al256(o + n * sizeof(double));
+    L.phi = o; o = al256(o + n * sizeof(double));
     L.sc = o; o = al256(o + 8 * sizeof(double));
     L.total = o;
     return L;
@@ -159,6 +171,7 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
         return MRCM_ERR_INVALID_ARG;
     }
     if (t.has_dirichlet) { h->err = "mrcm_impes: the transport step takes no-flow walls only"; return MRCM_ERR_NOT_IMPLEMENTED; }
+    if (t.n_cells >= (1LL << 31) / 6) { h->err = "mrcm_impes: grid too large for 32-bit face indexing"; return MRCM_ERR_NOT_IMPLEMENTED; }
     const mrcm::TLayout L = mrcm::transport_layout(t);
     if (tws_bytes < L.total) { h->err = "transport workspace smaller than mrcm_transport_query"; return MRCM_ERR_OOM; }
     cudaStream_t st = (cudaStream_t)stream;
@@ -169,6 +182,7 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
     double* p = (double*)(w + L.p);
     double* X = (double*)(w + L.X);
     double* S2 = (double*)(w + L.S2);
+    double* phi = (double*)(w + L.phi);
     double* sc = (double*)(w + L.sc);         // [0] max|u| bits, [1] dt, [2] t, [3] mass residual
     const long long n = t.n_cells;
     const double M = mu_o / mu_w;
@@ -178,7 +192,10 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
     g.n[0] = t.cfg.nx; g.n[1] = t.cfg.ny; g.n[2] = t.cfg.nz;
     g.area[0] = t.cfg.hy * t.cfg.hz; g.area[1] = t.cfg.hx * t.cfg.hz; g.area[2] = t.cfg.hx * t.cfg.hy;
     g.inv_vol = 1.0 / (t.cfg.hx * t.cfg.hy * t.cfg.hz);
-    const int grid = 152 * 4;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = sms * 8;
     MRCM_LAUNCH(h->prof, "k_zero_int", st, mrcm::k_zero_doubles<<<1, 32, 0, st>>>(sc, 8));
     double* cur = S;
     double* nxt = S2;
@@ -193,7 +210,8 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
             MRCM_LAUNCH(h->prof, "k_cfl", st, mrcm::k_umax<<<grid, mrcm::kTThreads, 0, st>>>(upp, 6 * n, (unsigned long long*)sc));
             MRCM_LAUNCH(h->prof, "k_cfl", st, mrcm::k_dt<<<1, 1, 0, st>>>(sc, num));
         }
-        MRCM_LAUNCH(h->prof, "k_transport_step", st, mrcm::k_transport_step<<<grid, mrcm::kTThreads, 0, st>>>(cur, nxt, upp, f, sc, g, M));
+        MRCM_LAUNCH(h->prof, "k_frac_flow", st, mrcm::k_frac_flow<<<grid, mrcm::kTThreads, 0, st>>>(cur, phi, M, n));
+        MRCM_LAUNCH(h->prof, "k_transport_step", st, mrcm::k_transport_step<<<grid, mrcm::kTThreads, 0, st>>>(cur, nxt, phi, upp, f, sc, g));
         MRCM_LAUNCH(h->prof, "k_tadd", st, mrcm::k_tadd<<<1, 1, 0, st>>>(sc));
         std::swap(cur, nxt);
     }
