@@ -171,6 +171,15 @@ mrcm_status mrcm_query_workspace(const mrcm_handle* h, size_t* ws_bytes, size_t*
 /* Derived sizes (see mrcm_sizes). */
 mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* out);
 
+/* Algorithmic cost of the paper's local solver (host only): the flops of a
+ * sparse direct LDL^T of every subdomain's local matrix under exact minimum
+ * degree ordering (ties: lowest box-lexicographic cell index; the stand-in for
+ * the paper's AMD ordering, Sec. "MBFs: LocalSolver()"), column j costing
+ * c_j (c_j + 3) for its c_j below-diagonal entries, and of solving all m_l
+ * right-hand sides once with it (4 nnz(L) m_l).  Subdomains above 4096
+ * cells: NOT_IMPLEMENTED.  Computed once per box shape per call. */
+mrcm_status mrcm_query_local_ldl(const mrcm_handle* h, double* factor_flops, double* solve_flops);
+
 /* Basis function i of V_H: normal axis, lower/upper subdomain, fine faces. */
 mrcm_status mrcm_query_basis(const mrcm_handle* h, int i, int* axis, int* sub_lo, int* sub_hi, int* n_faces);
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "mrcm_setup": (C.c_int, [C.POINTER(mrcm_config), C.POINTER(C.c_void_p)]),
     "mrcm_query_workspace": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "mrcm_query_sizes": (C.c_int, [C.c_void_p, C.POINTER(mrcm_sizes)]),
+    "mrcm_query_local_ldl": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mrcm_query_basis": (C.c_int, [C.c_void_p, C.c_int] + [C.POINTER(C.c_int)] * 4),
     "mrcm_factor_local": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "mrcm_solve_mbf": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

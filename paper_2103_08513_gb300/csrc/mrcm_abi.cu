@@ -1,6 +1,9 @@
 // extern "C" entry points of libmrcm (declared in include/mrcm.h).
 #include <cuda_runtime.h>
 
+#include <map>
+#include <tuple>
+
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -230,6 +233,29 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
         o->max_front_ne = std::max(o->max_front_ne, f.ne);
         o->max_front_nb = std::max(o->max_front_nb, f.nb);
     }
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_query_local_ldl(const mrcm_handle* h, double* factor_flops, double* solve_flops) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    const Tables& t = h->t;
+    if (t.max_N > 4096) return fail(const_cast<mrcm_handle*>(h), MRCM_ERR_NOT_IMPLEMENTED, "subdomain above 4096 cells");
+    std::map<std::tuple<int, int, int>, std::pair<double, long long>> cache;
+    double ff = 0.0, sf = 0.0;
+    for (const auto& s : t.subs) {
+        const auto key = std::make_tuple(s.sz[0], s.sz[1], s.sz[2]);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            double fl;
+            long long nz;
+            mrcm::min_degree_cost(s.sz[0], s.sz[1], s.sz[2], &fl, &nz);
+            it = cache.emplace(key, std::make_pair(fl, nz)).first;
+        }
+        ff += it->second.first;
+        sf += 4.0 * (double)it->second.second * s.m;
+    }
+    if (factor_flops) *factor_flops = ff;
+    if (solve_flops) *solve_flops = sf;
     return MRCM_OK;
 }
 

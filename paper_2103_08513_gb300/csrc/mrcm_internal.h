@@ -315,6 +315,7 @@ struct mrcm_handle {
 // Host setup (mrcm_setup.cpp)
 namespace mrcm {
 mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err);
+void min_degree_cost(int sx, int sy, int sz, double* flops, long long* nnz);
 void compute_layout(const Tables& t, Layout& lay);
 }
 

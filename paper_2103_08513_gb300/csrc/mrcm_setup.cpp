@@ -425,6 +425,60 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Algorithmic cost of a sparse direct LDL^T of one box's local matrix (the
+// paper's local solver, Sec. "MBFs: LocalSolver()"): exact minimum degree on
+// the 7-point graph (ties: lowest box-lexicographic index), the neighbour
+// count c_j at elimination = below-diagonal entries of column j of L;
+// factor flops sum c_j (c_j + 3), nnz(L) = sum c_j.  Bitset rows (n <= 4096).
+void min_degree_cost(int sx, int sy, int sz, double* flops, long long* nnz) {
+    const int n = sx * sy * sz, W = (n + 63) / 64;
+    std::vector<uint64_t> G((size_t)n * W, 0ull);
+    auto setb = [&](int a, int b) { G[(size_t)a * W + b / 64] |= 1ull << (b % 64); };
+    for (int k = 0; k < sz; ++k)
+        for (int j = 0; j < sy; ++j)
+            for (int i = 0; i < sx; ++i) {
+                const int c = i + sx * (j + sy * k);
+                if (i + 1 < sx) { setb(c, c + 1); setb(c + 1, c); }
+                if (j + 1 < sy) { setb(c, c + sx); setb(c + sx, c); }
+                if (k + 1 < sz) { setb(c, c + sx * sy); setb(c + sx * sy, c); }
+            }
+    auto popc = [&](int a) {
+        int d = 0;
+        for (int w = 0; w < W; ++w) d += __builtin_popcountll(G[(size_t)a * W + w]);
+        return d;
+    };
+    std::vector<int> deg(n);
+    std::vector<char> alive(n, 1);
+    for (int a = 0; a < n; ++a) deg[a] = popc(a);
+    double fl = 0.0;
+    long long nz = 0;
+    std::vector<int> nb;
+    for (int step = 0; step < n; ++step) {
+        int v = -1;
+        for (int a = 0; a < n; ++a)
+            if (alive[a] && (v < 0 || deg[a] < deg[v])) v = a;
+        const long long c = deg[v];
+        fl += (double)c * (double)(c + 3);
+        nz += c;
+        nb.clear();
+        for (int w = 0; w < W; ++w) {
+            uint64_t x = G[(size_t)v * W + w];
+            while (x) { nb.push_back(w * 64 + __builtin_ctzll(x)); x &= x - 1; }
+        }
+        for (int a : nb) {
+            uint64_t* ra = &G[(size_t)a * W];
+            const uint64_t* rv = &G[(size_t)v * W];
+            for (int w = 0; w < W; ++w) ra[w] |= rv[w];
+            ra[a / 64] &= ~(1ull << (a % 64));
+            ra[v / 64] &= ~(1ull << (v % 64));
+            deg[a] = popc(a);
+        }
+        alive[v] = 0;
+    }
+    *flops = fl;
+    *nnz = nz;
+}
+
 void compute_layout(const Tables& t, Layout& L) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + std::max<size_t>(bytes, 1)); return o; };

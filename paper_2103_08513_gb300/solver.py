@@ -255,6 +255,12 @@ class MRCM:
         L.check(self.lib.mrcm_read_work(self.handle, self.ws_ptr, C.byref(v)), self.handle)
         return int(v.value)
 
+    def local_ldl_flops(self):
+        """(factor flops, all-columns solve flops) of the paper's sparse local LDL^T (minimum degree)."""
+        a, b = C.c_double(), C.c_double()
+        L.check(self.lib.mrcm_query_local_ldl(self.handle, C.byref(a), C.byref(b)), self.handle)
+        return float(a.value), float(b.value)
+
     def basis(self, i):
         v = [C.c_int() for _ in range(4)]
         L.check(self.lib.mrcm_query_basis(self.handle, int(i), *[C.byref(x) for x in v]), self.handle)

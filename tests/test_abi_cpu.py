@@ -205,3 +205,25 @@ def test_noalloc_rejects_oversized_boxes_before_any_device_work(lib, box):
     rc = lib.mrcm_box_solve_noalloc((C.c_int * 3)(*box), (C.c_double * 3)(1.0, 1.0, 1.0), (C.c_int * 6)(*[1] * 6),
                                     ptr, ptr, ptr, ptr, ptr, ptr, C.cast(flag, C.c_void_p), None)
     assert rc == 7                           # MRCM_ERR_OOM
+
+
+def test_local_ldl_cost_matches_oracle(lib):
+    """The library's count of the paper's sparse local LDL^T (minimum degree,
+    lowest-index ties) equals the oracle's, shape by shape and summed."""
+    from oracle.symbolic import ldl_cost
+    from paper_2103_08513_gb300 import MRCM
+    w = small(n=(14, 9, 7), edges=([4, 10], [3, 6], [7]), patch=((2, 2), (3, 2), (2, 3)))
+    s = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", allocate=False)
+    ff, sf = s.local_ldl_flops()
+    prob = oracle.from_workload(w, K=np.ones((3,) + tuple(w.n[::-1])), f=np.zeros(w.n[::-1]))
+    _, sub_bases, _ = build_bases(prob)
+    ef = es = 0.0
+    for l in range(prob.nsub):
+        lo, size = prob.sub_box(l)
+        fl, nz = ldl_cost(*size)
+        ef += fl
+        es += 4.0 * nz * (2 * len(sub_bases[l]) + 1)
+    assert ff == ef and sf == es
+    # a column of one cell (1-D chain): every vertex eliminated with one neighbour but the last
+    fl, nz = ldl_cost(5, 1, 1)
+    assert nz == 4 and fl == 4 * 1 * 4
