@@ -454,7 +454,7 @@ def variants_sections(make, w, K, dev, stream, fd, u_ms, n_sub):
     s.profile(False)
     tr_launches, tr_ms = kprof.get("k_transport_step", (0, 0.0))
     tr_avg = tr_ms / max(tr_launches, 1)
-    tr_bytes = 80.0 * w.cells             # per step: S, phi, six face velocities, f read; S written (8 B each)
+    tr_bytes = 88.0 * w.cells             # per step: S, phi, six face velocities, f read; S, phi written (8 B each)
     ff_launches, ff_ms = kprof.get("k_frac_flow", (0, 0.0))
     out["impes"] = {"C": C_skip, "steps": n_steps, "darcy_solves": n_steps // C_skip, "mu_w": 1.0, "mu_o": 5.0,
                     "cfl": 0.9, "ms_total": round(e0.elapsed_time(e1), 3), "t_simulated": float(t_sim.cpu()[0]),
@@ -464,7 +464,7 @@ def variants_sections(make, w, K, dev, stream, fd, u_ms, n_sub):
                                        "roofline": {"bound": "hbm", "achieved": round(tr_bytes / (tr_avg / 1e3) / 1e9, 1),
                                                     "peak": load_peaks()["hbm_gbs"], "unit": "GB/s",
                                                     "frac": round(tr_bytes / (tr_avg / 1e3) / 1e9 / load_peaks()["hbm_gbs"], 4),
-                                                    "bytes_per_cell": 80}},
+                                                    "bytes_per_cell": 88}},
                     "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])[:8]}}
     del s, S
     return out

@@ -88,10 +88,12 @@ k_frac_flow(const double* __restrict__ S, double* __restrict__ phi, double M, lo
 }
 
 // One upwind step S_in -> S_out with the frozen, single-valued velocity u and
-// the cells' phi; cell coordinates in 32-bit arithmetic (n < 2^31 cells).
+// the cells' phi (and phi of S_out for the next step); cell coordinates in
+// 32-bit arithmetic (n < 2^31 cells).
 __global__ void __launch_bounds__(kTThreads)
 k_transport_step(const double* __restrict__ S, double* __restrict__ Sn, const double* __restrict__ phi,
-                 const double* __restrict__ u, const double* __restrict__ f, const double* __restrict__ sc, TGeo g) {
+                 double* __restrict__ phin, const double* __restrict__ u, const double* __restrict__ f,
+                 const double* __restrict__ sc, TGeo g, double M) {
     const int n = g.n[0] * g.n[1] * g.n[2];
     const int nxy = g.n[0] * g.n[1];
     const int stride[3] = {1, g.n[0], nxy};
@@ -114,7 +116,9 @@ k_transport_step(const double* __restrict__ S, double* __restrict__ Sn, const do
                 acc -= (phf - phic) * q;
             }
         }
-        Sn[c] = S[c] + dt * g.inv_vol * acc + dt * fmax(f[c], 0.0) * (1.0 - phic);
+        const double sn = S[c] + dt * g.inv_vol * acc + dt * fmax(f[c], 0.0) * (1.0 - phic);
+        Sn[c] = sn;
+        phin[c] = frac_flow(sn, M);                            // phi of the next step
     }
 }
 
@@ -131,7 +135,7 @@ double frac_flow_slope_max(double M) {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TLayout {
-    size_t ke, u, upp, p, X, S2, phi, sc, total;
+    size_t ke, u, upp, p, X, S2, phi, phi2, sc, total;
 };
 
 TLayout transport_layout(const Tables& t) {
@@ -145,6 +149,7 @@ TLayout transport_layout(const Tables& t) {
     L.X = o; o = al256(o + std::max<size_t>(2 * (size_t)t.NV, 1) * sizeof(double));
     L.S2 = o; o = al256(o + n * sizeof(double));
     L.phi = o; o = al256(o + n * sizeof(double));
+    L.phi2 = o; o = al256(o + n * sizeof(double));
     L.sc = o; o = al256(o + 8 * sizeof(double));
     L.total = o;
     return L;
@@ -183,6 +188,7 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
     double* X = (double*)(w + L.X);
     double* S2 = (double*)(w + L.S2);
     double* phi = (double*)(w + L.phi);
+    double* phi2 = (double*)(w + L.phi2);
     double* sc = (double*)(w + L.sc);         // [0] max|u| bits, [1] dt, [2] t, [3] mass residual
     const long long n = t.n_cells;
     const double M = mu_o / mu_w;
@@ -210,8 +216,10 @@ mrcm_status mrcm_impes(mrcm_handle* h, const double* K, const double* f, double*
             MRCM_LAUNCH(h->prof, "k_cfl", st, mrcm::k_umax<<<grid, mrcm::kTThreads, 0, st>>>(upp, 6 * n, (unsigned long long*)sc));
             MRCM_LAUNCH(h->prof, "k_cfl", st, mrcm::k_dt<<<1, 1, 0, st>>>(sc, num));
         }
-        MRCM_LAUNCH(h->prof, "k_frac_flow", st, mrcm::k_frac_flow<<<grid, mrcm::kTThreads, 0, st>>>(cur, phi, M, n));
-        MRCM_LAUNCH(h->prof, "k_transport_step", st, mrcm::k_transport_step<<<grid, mrcm::kTThreads, 0, st>>>(cur, nxt, phi, upp, f, sc, g));
+        if (step == 0)
+            MRCM_LAUNCH(h->prof, "k_frac_flow", st, mrcm::k_frac_flow<<<grid, mrcm::kTThreads, 0, st>>>(cur, phi, M, n));
+        MRCM_LAUNCH(h->prof, "k_transport_step", st, mrcm::k_transport_step<<<grid, mrcm::kTThreads, 0, st>>>(cur, nxt, phi, phi2, upp, f, sc, g, M));
+        std::swap(phi, phi2);
         MRCM_LAUNCH(h->prof, "k_tadd", st, mrcm::k_tadd<<<1, 1, 0, st>>>(sc));
         std::swap(cur, nxt);
     }
