@@ -1225,9 +1225,10 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         }
         if (threadIdx.x == 0) na_s = base;
     }
-    for (int e = threadIdx.x; e < 6 * N; e += blockDim.x) cf[e] = -1;
     __syncthreads();
     const int na = na_s;
+    if (na == 0) { __syncthreads(); return; }      // nothing left to refine here (before any set-up work)
+    for (int e = threadIdx.x; e < 6 * N; e += blockDim.x) cf[e] = -1;
     for (int e = threadIdx.x; e < mpad; e += blockDim.x) {
         nrm[e] = 0.0f;
         float sc = 1.0f;
@@ -1237,7 +1238,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         }
         rsb[e] = sc;
     }
-    if (na == 0) { __syncthreads(); return; }
+    __syncthreads();                               // cf cleared before the faces are entered
     for (int q = threadIdx.x; q < s.nface; q += blockDim.x) {
         const FaceInfo fi = g.faces[s.face_off + q];
         cf[6 * fi.cell + 2 * fi.axis + (fi.s > 0 ? 1 : 0)] = (short)q;   // one face per cell side
@@ -1284,6 +1285,25 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     double* co_v = co_u + b;
     double* co_sp = co_v + b;
     double* co_sm = co_sp + b;
+    // the slab's Jacobi scale (mixed mode) and its coupling to the neighbouring slab of the sweep
+    T* t_s = reinterpret_cast<T*>(co_sm + b);
+    float* sc_s = reinterpret_cast<float*>(t_s + b);
+    auto stage_slab = [&](int base, int nb_off) {       // nb_off: -b (forward), +b (backward)
+        for (int i = threadIdx.x; i < b; i += blockDim.x) {
+            const int c = base + i;
+            if constexpr (kScaled) sc_s[i] = cp.scf[c];
+            const int ct = nb_off < 0 ? c - b : c;
+            t_s[i] = (nb_off < 0 ? c >= b : c + b < N) ? cp.t(ct) : (T)0;
+        }
+    };
+    auto zin = [&](double r, float rf, int i) -> T {
+        if constexpr (kScaled) return rf * sc_s[i];
+        else return (T)r;
+    };
+    auto xout = [&](T x, int i) -> double {
+        if constexpr (kScaled) return f32_to_f64(x * sc_s[i]);
+        else return (double)x;
+    };
     // ---- forward sweep
     for (int sl = 0; sl < s.ns; ++sl) {
         const int base = sl * b;
@@ -1296,8 +1316,9 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                 co_sp[i] = c + b < N ? cs[c] : 0.0;
                 co_sm[i] = c >= b ? cs[c - b] : 0.0;
             }
-            __syncthreads();
         }
+        stage_slab(base, -b);
+        __syncthreads();
         // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
         for (int jj = ty; jj < na; jj += NY) {
             const int j = cols[jj];
@@ -1337,8 +1358,8 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                 const float rf = f64_to_f32_rz(r);
                 const float rn = rf * rscale;
                 rr = fmaf(rn, rn, rr);
-                T z = cp.in(r, rf, c);
-                if (sl > 0) z += cp.t(c - b) * Yp[i * mpad + jj];
+                T z = zin(r, rf, i);
+                if (sl > 0) z += t_s[i] * Yp[i * mpad + jj];
                 Z[i * mpad + jj] = z;
             }
             for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
@@ -1357,18 +1378,20 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     for (int sl = s.ns - 1; sl >= 0; --sl) {
         const int base = sl * b;
         const bool last = sl == s.ns - 1;
+        stage_slab(base, b);
+        __syncthreads();
         auto finish = [&](int i, int jj, T acc) {
             const int j = cols[jj];
             const long long gi = (long long)j * N + base + i;
             const T x = Ys[(g.last_only ? 0 : (long long)j * N) + base + i] + acc;
             Yp[i * mpad + jj] = x;                 // Z, not Yp, feeds the product
-            const double xo = cp.out(x, base + i);
+            const double xo = xout(x, i);
             if (kSweep) Xs[gi] += xo; else Xs[gi] = xo;
         };
         if (!last) {
             const int q = 2 * s.ns - 2 - sl;
             for (int jj = ty; jj < na; jj += NY)
-                for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = cp.t(base + i) * Yp[i * mpad + jj];
+                for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = t_s[i] * Yp[i * mpad + jj];
             const T* Wsm = wblock(q);
             __syncthreads();
             block_product<T, RT>(Wsm, Z, b, na, mpad, finish);
@@ -2085,6 +2108,10 @@ int launch_local_finish(const Tables& t, const DeviceTables& d, const Layout& L,
             gq.nlist = std::min(fb_cap, nsub - q);
             launch_fallback(t, d, L, ws, gq, fb_cap, fb_stride, fb_ystride, st, P);
         }
+    } else {
+        // no fallback: the columns that did not converge are counted (no slot is taken)
+        MRCM_LAUNCH(P, "k_fb_collect", st, k_fb_collect<<<(nsub + 127) / 128, 128, 0, st>>>(d.subs, d.solve_list, nsub,
+                    g.conv, status, (SubInfo*)(ws + L.fb_subs), (int*)(ws + L.fb_list), 0, 0, 0));
     }
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
