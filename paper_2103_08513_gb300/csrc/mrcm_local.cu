@@ -1288,6 +1288,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     // the slab's Jacobi scale (mixed mode) and its coupling to the neighbouring slab of the sweep
     T* t_s = reinterpret_cast<T*>(co_sm + b);
     float* sc_s = reinterpret_cast<float*>(t_s + b);
+    signed char* fcol_s = reinterpret_cast<signed char*>(sc_s + b);   // basis column of each cell side's face, -1 none
     auto stage_slab = [&](int base, int nb_off) {       // nb_off: -b (forward), +b (backward)
         for (int i = threadIdx.x; i < b; i += blockDim.x) {
             const int c = base + i;
@@ -1295,6 +1296,11 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             const int ct = nb_off < 0 ? c - b : c;
             t_s[i] = (nb_off < 0 ? c >= b : c + b < N) ? cp.t(ct) : (T)0;
         }
+        if (nb_off < 0)
+            for (int k = threadIdx.x; k < 6 * b; k += blockDim.x) {
+                const int q = cf[6 * base + k];
+                fcol_s[k] = q >= 0 ? (signed char)g.faces[s.face_off + q].col : (signed char)-1;
+            }
     };
     auto zin = [&](double r, float rf, int i) -> T {
         if constexpr (kScaled) return rf * sc_s[i];
@@ -1319,13 +1325,16 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         }
         stage_slab(base, -b);
         __syncthreads();
-        // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}
-        for (int jj = ty; jj < na; jj += NY) {
-            const int j = cols[jj];
-            const double* x = Xs + (long long)j * N;
-            const float rscale = rsb[jj];
-            float rr = 0.0f;
-            for (int i = tx; i < b; i += 32) {
+        // r = B (- A X) of the slab in FP64, its squared norm, and Z = S r + t^ o Y_{s-1}.
+        // The (cell i, active column jj) entries are spread over the whole CTA, column by
+        // column (a warp reads consecutive cells); each entry's squared norm is parked in
+        // Yp[i][jj] by the thread that has just read Y_{s-1} there, and the columns' sums
+        // are taken afterwards in a fixed order.
+        {
+            int jj = threadIdx.x / b, i = threadIdx.x - jj * b;
+            const int dj = NT / b, di = NT - dj * b;
+            for (int e = threadIdx.x; e < na * b; e += NT) {
+                const int j = cols[jj];
                 const int c = base + i;
                 double r;
                 if (j == m - 1) {
@@ -1338,14 +1347,14 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                     r = 0.0;
 #pragma unroll
                     for (int a = 0; a < 6; ++a) {
-                        const int q = cf[6 * c + a];
-                        if (q < 0) continue;
-                        const int col = g.faces[s.face_off + q].col;
-                        if (j == col) r = g.face_tr[s.face_off + q];
-                        else if (j == nI + col) r = g.face_u[s.face_off + q];
+                        const int col = fcol_s[6 * i + a];
+                        if (col < 0) continue;
+                        if (j == col) r = g.face_tr[s.face_off + cf[6 * c + a]];
+                        else if (j == nI + col) r = g.face_u[s.face_off + cf[6 * c + a]];
                     }
                 }
                 if (kSweep) {                     // r - A x as one FMA chain
+                    const double* x = Xs + (long long)j * N;
                     const int u = i % su;
                     r = fma(-co_d[i], x[c], r);
                     if (u + 1 < su) r = fma(co_u[i], x[c + 1], r);
@@ -1356,14 +1365,23 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
                     if (c >= b) r = fma(co_sm[i], x[c - b], r);
                 }
                 const float rf = f64_to_f32_rz(r);
-                const float rn = rf * rscale;
-                rr = fmaf(rn, rn, rr);
+                const float rn = rf * rsb[jj];
                 T z = zin(r, rf, i);
-                if (sl > 0) z += t_s[i] * Yp[i * mpad + jj];
+                T* yp = &Yp[i * mpad + jj];
+                if (sl > 0) z += t_s[i] * *yp;
                 Z[i * mpad + jj] = z;
+                *yp = (T)(rn * rn);
+                i += di;
+                jj += dj;
+                if (i >= b) { i -= b; ++jj; }
             }
+        }
+        __syncthreads();
+        for (int jj = ty; jj < na; jj += NY) {
+            float rr = 0.0f;
+            for (int i = tx; i < b; i += 32) rr += (float)Yp[i * mpad + jj];
             for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
-            if (tx == 0) nrm[jj] += rr;          // column jj belongs to warp ty only: fixed order
+            if (tx == 0) nrm[jj] += rr;          // fixed order per column
         }
         const T* Wsm = wblock(sl);
         __syncthreads();
@@ -1390,16 +1408,20 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         };
         if (!last) {
             const int q = 2 * s.ns - 2 - sl;
-            for (int jj = ty; jj < na; jj += NY)
-                for (int i = tx; i < b; i += 32) Z[i * mpad + jj] = t_s[i] * Yp[i * mpad + jj];
+            for (int e = threadIdx.x; e < na * b; e += NT) {
+                const int jj = e / b, i = e - jj * b;
+                Z[i * mpad + jj] = t_s[i] * Yp[i * mpad + jj];
+            }
             const T* Wsm = wblock(q);
             __syncthreads();
             block_product<T, RT>(Wsm, Z, b, na, mpad, finish);
             __syncthreads();
             refill(q);
         } else {
-            for (int jj = ty; jj < na; jj += NY)
-                for (int i = tx; i < b; i += 32) finish(i, jj, (T)0);
+            for (int e = threadIdx.x; e < na * b; e += NT) {
+                const int jj = e / b, i = e - jj * b;
+                finish(i, jj, (T)0);
+            }
             __syncthreads();
         }
     }
