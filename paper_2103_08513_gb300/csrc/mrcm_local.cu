@@ -1552,12 +1552,13 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
     // on them is 1 (j = k, P-MBF), -beta s (j = nI + k, U-MBF) or 0, so the
     // traces are sum T_R x and sum beta s T_R x plus a correction on those two
     // columns: two FMAs per face and column.  Four faces' x values are read at
-    // once.
+    // once, into four partial sums per trace (four independent FMA chains; the
+    // partials are added in a fixed order).
     for (int e = threadIdx.x; e < nI * m; e += blockDim.x) {
         int k = e / m, j = e - (e / m) * m;
         int q0 = start[k], q1 = start[k + 1];
         const double* x = Xs + (long long)j * N;
-        double sf = 0.0, su = 0.0;
+        double pf[4] = {0.0, 0.0, 0.0, 0.0}, pu[4] = {0.0, 0.0, 0.0, 0.0};
         int q = q0;
         for (; q + 3 < q1; q += 4) {
             double xv[4];
@@ -1565,15 +1566,17 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
             for (int u = 0; u < 4; ++u) xv[u] = x[s_cell[q + u]];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                sf = fma(s_tr[q + u], xv[u], sf);
-                su = fma(s_bst[q + u], xv[u], su);
+                pf[u] = fma(s_tr[q + u], xv[u], pf[u]);
+                pu[u] = fma(s_bst[q + u], xv[u], pu[u]);
             }
         }
-        for (; q < q1; ++q) {
+        for (int u = 0; q < q1; ++q, ++u) {
             const double xv = x[s_cell[q]];
-            sf = fma(s_tr[q], xv, sf);
-            su = fma(s_bst[q], xv, su);
+            pf[u] = fma(s_tr[q], xv, pf[u]);
+            pu[u] = fma(s_bst[q], xv, pu[u]);
         }
+        double sf = (pf[0] + pf[1]) + (pf[2] + pf[3]);
+        double su = (pu[0] + pu[1]) + (pu[2] + pu[3]);
         double sdiag = 0.0;
         if (j == k || j == nI + k) {
             for (int q = q0; q < q1; ++q) {

@@ -58,9 +58,17 @@ k_reconstruct(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fac
     __syncthreads();
     const double* Xs = Xmbf + s.x_off;
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < m; ++j) acc += Xs[(long long)j * N + c] * cvec[j];
-        pl[c] = acc;
+        // four independent FMA chains over the columns, added in a fixed order
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = 0;
+        for (; j + 3 < m; j += 4) {
+            a0 = fma(Xs[(long long)j * N + c], cvec[j], a0);
+            a1 = fma(Xs[(long long)(j + 1) * N + c], cvec[j + 1], a1);
+            a2 = fma(Xs[(long long)(j + 2) * N + c], cvec[j + 2], a2);
+            a3 = fma(Xs[(long long)(j + 3) * N + c], cvec[j + 3], a3);
+        }
+        for (; j < m; ++j) a0 = fma(Xs[(long long)j * N + c], cvec[j], a0);
+        pl[c] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     const double* cu = coef + nct + s.cell_off;
