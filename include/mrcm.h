@@ -413,13 +413,19 @@ mrcm_status mrcm_net_sync_weights(mrcm_net* net, float* state, void* stream);
 /* y[batch][1][D][H][W] = net(x[batch][in][D][H][W]). */
 mrcm_status mrcm_net_forward(mrcm_net* net, const float* state, const float* x, float* y, int batch, void* ws,
                              void* stream);
-/* Mean-squared-error loss against target[batch][1][D][H][W] (*loss, device)
- * and its gradient with respect to the parameters (grad[params], device). */
-mrcm_status mrcm_net_gradient(mrcm_net* net, const float* state, const float* x, const float* target, int batch,
-                              float* grad, float* loss, void* ws, void* stream);
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1). */
-mrcm_status mrcm_net_train_step(mrcm_net* net, float* state, const float* x, const float* target, int batch,
-                                float lr, int step, float* loss, void* ws, void* stream);
+/* Loss against target[batch][1][D][H][W] (*loss, device) and its gradient
+ * with respect to the parameters (grad[params], device).  weight NULL: the
+ * pressure MSE, mean((y - t)^2).  weight[batch][1][D][H][W] (device, from
+ * mrcm_net_flux_weights): the face-flux term is added, mean((1 + w)(y - t)^2)
+ * with w = sum of T_R^2 over the cell's Robin faces, T_R (y - t) being the
+ * error of the outward flux through such a face. */
+mrcm_status mrcm_net_gradient(mrcm_net* net, const float* state, const float* x, const float* target,
+                              const float* weight, int batch, float* grad, float* loss, void* ws, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1) on the
+ * loss of mrcm_net_gradient. */
+mrcm_status mrcm_net_train_step(mrcm_net* net, float* state, const float* x, const float* target,
+                                const float* weight, int batch, float lr, int step, float* loss, void* ws,
+                                void* stream);
 void mrcm_net_destroy(mrcm_net* net);
 
 /* Training samples from the method itself (after mrcm_solve_mbf): sample s
@@ -434,6 +440,13 @@ void mrcm_net_destroy(mrcm_net* net);
  * handle. */
 mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, float* x, float* target,
                              int max_samples, int* n_samples, void* stream);
+
+/* The loss weights of the face-flux term for the same samples (after
+ * mrcm_factor_local): weight[s][cell] = sum of T_R^2 over the cell's Robin
+ * faces (0 for cells without one), [s][D][H][W] FP32 device, the first
+ * min(max_samples, available) samples. */
+mrcm_status mrcm_net_flux_weights(mrcm_handle* h, const mrcm_net* net, void* ws, float* weight, int max_samples,
+                                  void* stream);
 
 /* The learned form of mrcm_solve_mbf, for a handle set up with precision
  * MRCM_LEARNED_PCG (after mrcm_factor_local, which then assembles the local

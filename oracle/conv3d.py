@@ -44,13 +44,19 @@ def forward(params, x):
     return acts
 
 
-def loss_and_grad(params, x, t):
-    """Mean-squared error of the output against t and its parameter gradient."""
+def loss_and_grad(params, x, t, w=None):
+    """Loss of the output against t and its parameter gradient.
+
+    Without w the pressure MSE; with per-cell face-flux weights w (the sum of
+    T_R^2 over the cell's Robin faces) the squared flux errors T_R (y - t) of
+    those faces are added: mean((1 + w) (y - t)^2).
+    """
     acts = forward(params, x)
     y = acts[-1]
     n = y.size
-    loss = float(np.sum((y - t) ** 2) / n)
-    g = 2.0 * (y - t) / n * y * (1.0 - y)
+    wt = 1.0 if w is None else 1.0 + w
+    loss = float(np.sum(wt * (y - t) ** 2) / n)
+    g = 2.0 * wt * (y - t) / n * y * (1.0 - y)
     grads = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         w, b = params[l]

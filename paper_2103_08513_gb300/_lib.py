@@ -87,8 +87,9 @@ SIGNATURES = {
     "mrcm_net_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_ulonglong, C.c_void_p]),
     "mrcm_net_sync_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrcm_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
-    "mrcm_net_gradient": (C.c_int, [C.c_void_p] * 4 + [C.c_int] + [C.c_void_p] * 4),
-    "mrcm_net_train_step": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_float, C.c_int] + [C.c_void_p] * 3),
+    "mrcm_net_gradient": (C.c_int, [C.c_void_p] * 5 + [C.c_int] + [C.c_void_p] * 4),
+    "mrcm_net_train_step": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.c_float, C.c_int] + [C.c_void_p] * 3),
+    "mrcm_net_flux_weights": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_void_p]),
     "mrcm_net_destroy": (None, [C.c_void_p]),
     "mrcm_net_samples": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "mrcm_solve_mbf_learned": (C.c_int, [C.c_void_p] * 3 + [C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,

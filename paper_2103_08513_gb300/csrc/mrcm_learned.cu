@@ -178,17 +178,22 @@ k_conv_backward_weights(ConvShape sh, int Cin, int Cout, int batch, const float*
     }
 }
 
-// MSE loss over the batch and its gradient with respect to the logistic
-// output's pre-activation: d/dz of mean((y - t)^2) = 2 (y - t) y (1 - y) / n.
+// Loss over the batch and its gradient with respect to the logistic output's
+// pre-activation.  Without weights the pressure MSE, mean((y - t)^2); with
+// per-cell weights w (the sum of T_R^2 over the cell's Robin faces) the
+// squared face-flux errors are added, T_R (y_c - t_c) being the error of the
+// outward flux through a face of the cell: mean((1 + w) (y - t)^2), whose
+// derivative is 2 (1 + w) (y - t) y (1 - y) / n.
 __global__ void __launch_bounds__(kNetThreads)
-k_mse_loss(int n, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ g,
-           float* __restrict__ partial) {
+k_mse_loss(int n, const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ w,
+           float* __restrict__ g, float* __restrict__ partial) {
     __shared__ float red[kNetThreads];
     float acc = 0.0f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = y[i] - t[i];
-        acc += d * d;
-        g[i] = 2.0f * d * y[i] * (1.0f - y[i]) / (float)n;
+        const float wt = w ? 1.0f + w[i] : 1.0f;
+        acc += wt * d * d;
+        g[i] = 2.0f * wt * d * y[i] * (1.0f - y[i]) / (float)n;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -302,14 +307,15 @@ void forward(const mrcm_net* n, const NetPtrs& p, const float* x, int batch, flo
 }
 
 // loss and gradient of the parameters into `grad` (P floats)
-void backward(const mrcm_net* n, const NetPtrs& p, const float* x, const float* target, int batch, float* acts,
-              float* gbuf0, float* gbuf1, float* grad, float* partial, float* loss, cudaStream_t st) {
+void backward(const mrcm_net* n, const NetPtrs& p, const float* x, const float* target, const float* weight,
+              int batch, float* acts, float* gbuf0, float* gbuf1, float* grad, float* partial, float* loss,
+              cudaStream_t st) {
     ConvShape sh{n->D, n->H, n->W, n->S};
     const int L = n->layers;
     const float* y = acts + (long long)batch * n->act_off[L - 1];
     const int nout = batch * n->S;
     const int nb = 128;
-    mrcm::k_mse_loss<<<nb, mrcm::kNetThreads, 0, st>>>(nout, y, target, gbuf0, partial);
+    mrcm::k_mse_loss<<<nb, mrcm::kNetThreads, 0, st>>>(nout, y, target, weight, gbuf0, partial);
     mrcm::k_sum_partials<<<1, 32, 0, st>>>(nout, nb, partial, loss);
     float* g = gbuf0;
     float* gnext = gbuf1;
@@ -425,27 +431,28 @@ static float* ws_grad(const mrcm_net* n, void* ws, int batch, float** g0, float*
     return *partial + 1024;
 }
 
-mrcm_status mrcm_net_gradient(mrcm_net* n, const float* state, const float* x, const float* target, int batch,
-                              float* grad, float* loss, void* ws, void* stream) {
+mrcm_status mrcm_net_gradient(mrcm_net* n, const float* state, const float* x, const float* target,
+                              const float* weight, int batch, float* grad, float* loss, void* ws, void* stream) {
     if (!n || !state || !x || !target || !grad || !loss || !ws || batch < 1) return MRCM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     NetPtrs p = net_ptrs(n, state);
     float *g0, *g1, *partial;
     ws_grad(n, ws, batch, &g0, &g1, &partial);
     forward(n, p, x, batch, (float*)ws, st);
-    backward(n, p, x, target, batch, (float*)ws, g0, g1, grad, partial, loss, st);
+    backward(n, p, x, target, weight, batch, (float*)ws, g0, g1, grad, partial, loss, st);
     return cudaGetLastError() == cudaSuccess ? MRCM_OK : MRCM_ERR_CUDA;
 }
 
-mrcm_status mrcm_net_train_step(mrcm_net* n, float* state, const float* x, const float* target, int batch,
-                                float lr, int step, float* loss, void* ws, void* stream) {
+mrcm_status mrcm_net_train_step(mrcm_net* n, float* state, const float* x, const float* target,
+                                const float* weight, int batch, float lr, int step, float* loss, void* ws,
+                                void* stream) {
     if (!n || !state || !x || !target || !loss || !ws || batch < 1 || step < 1) return MRCM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     NetPtrs p = net_ptrs(n, state);
     float *g0, *g1, *partial;
     float* grad = ws_grad(n, ws, batch, &g0, &g1, &partial);
     forward(n, p, x, batch, (float*)ws, st);
-    backward(n, p, x, target, batch, (float*)ws, g0, g1, grad, partial, loss, st);
+    backward(n, p, x, target, weight, batch, (float*)ws, g0, g1, grad, partial, loss, st);
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)step), c2 = 1.0f - std::pow(b2, (float)step);
     mrcm::k_adam<<<128, 256, 0, st>>>(n->P, p.w, p.m, p.v, grad, p.wb, lr, b1, b2, 1e-8f, c1, c2);
@@ -525,6 +532,34 @@ k_gather_mask(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ fac
             const int smp = base + c;
             if (smp < max_samples) xs[(long long)smp * 4 * N + 3 * N + lex] = 1.0f;
         }
+    }
+}
+
+// Face-flux weights of the loss: per sample and cell, the sum of T_R^2 over
+// the cell's Robin faces (zero inside), the same for every sample of a
+// subdomain.  One thread per (sample of the subdomain, cell), summing the
+// cell's faces in face order (deterministic).
+__global__ void __launch_bounds__(256)
+k_gather_flux_weights(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
+                      const double* __restrict__ face_tr, const int* __restrict__ soff, int max_samples,
+                      float* __restrict__ wt) {
+    const SubInfo s = subs[blockIdx.x];
+    const int base = soff[blockIdx.x];
+    if (base < 0) return;
+    const int N = s.N;
+    for (int e = threadIdx.x; e < s.nI * N; e += blockDim.x) {
+        const int c = e / N, cell = e - c * N;          // cell in slab order
+        if (base + c >= max_samples) continue;
+        float acc = 0.0f;
+        for (int q = 0; q < s.nface; ++q) {
+            const FaceInfo fi = faces[s.face_off + q];
+            if (fi.cell != cell) continue;
+            const float tr = (float)face_tr[s.face_off + q];
+            acc = fmaf(tr, tr, acc);
+        }
+        int lc[3];
+        slab_coords(s, cell, lc);
+        wt[(long long)(base + c) * N + lc[0] + s.sz[0] * (lc[1] + s.sz[1] * lc[2])] = acc;
     }
 }
 
@@ -851,6 +886,19 @@ mrcm_status mrcm_net_samples(mrcm_handle* h, const mrcm_net* net, void* ws, floa
     mrcm::k_gather_samples<<<(int)t.subs.size(), 256, 0, s>>>(h->d.subs, h->d.faces, soff, h->K,
         (const double*)((char*)ws + h->lay.X), t.cfg.nx, t.cfg.ny, t.n_cells, max_samples, x, target);
     mrcm::k_gather_mask<<<(int)t.subs.size(), 256, 0, s>>>(h->d.subs, h->d.faces, soff, max_samples, x);
+    return cudaGetLastError() == cudaSuccess ? MRCM_OK : MRCM_ERR_CUDA;
+}
+
+mrcm_status mrcm_net_flux_weights(mrcm_handle* h, const mrcm_net* net, void* ws, float* weight, int max_samples,
+                                  void* stream) {
+    if (!h || !net || !ws || !weight || max_samples < 0) return MRCM_ERR_INVALID_ARG;
+    if (h->stage < 1) return MRCM_ERR_STATE;
+    int *soff, *slist, cnt;
+    mrcm_status st = sample_tables(h, net->D, net->H, net->W, &soff, &slist, &cnt);
+    if (st != MRCM_OK) return st;
+    if (max_samples == 0) return MRCM_OK;
+    mrcm::k_gather_flux_weights<<<(int)h->t.subs.size(), 256, 0, (cudaStream_t)stream>>>(h->d.subs, h->d.faces,
+        (const double*)((char*)ws + h->lay.face_tr), soff, std::min(max_samples, cnt), weight);
     return cudaGetLastError() == cudaSuccess ? MRCM_OK : MRCM_ERR_CUDA;
 }
 

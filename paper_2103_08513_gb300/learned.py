@@ -52,18 +52,27 @@ class WarmStartNet:
         L.check(self.lib.mrcm_net_forward(self.net, _ptr(self.state), _ptr(x), _ptr(y), n, _ptr(self.ws), _stream()))
         return y
 
-    def gradient(self, x, target):
+    def gradient(self, x, target, weight=None):
         n = x.shape[0]
         grad = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
-        L.check(self.lib.mrcm_net_gradient(self.net, _ptr(self.state), _ptr(x), _ptr(target), n, _ptr(grad),
+        L.check(self.lib.mrcm_net_gradient(self.net, _ptr(self.state), _ptr(x), _ptr(target),
+                                           _ptr(weight) if weight is not None else None, n, _ptr(grad),
                                            _ptr(self.loss), _ptr(self.ws), _stream()))
         return grad, self.loss
 
-    def train_step(self, x, target, lr=1e-3):
+    def train_step(self, x, target, lr=1e-3, weight=None):
         self.step += 1
-        L.check(self.lib.mrcm_net_train_step(self.net, _ptr(self.state), _ptr(x), _ptr(target), x.shape[0],
+        L.check(self.lib.mrcm_net_train_step(self.net, _ptr(self.state), _ptr(x), _ptr(target),
+                                             _ptr(weight) if weight is not None else None, x.shape[0],
                                              C.c_float(lr), self.step, _ptr(self.loss), _ptr(self.ws), _stream()))
         return self.loss
+
+    def flux_weights(self, solver, n_samples):
+        """Face-flux loss weights (sum of T_R^2 over each cell's Robin faces) of the first n samples."""
+        w = torch.empty((n_samples, 1) + self.shape, dtype=torch.float32, device=self.device)
+        L.check(self.lib.mrcm_net_flux_weights(solver.handle, self.net, solver.ws_ptr, _ptr(w), n_samples,
+                                               _stream()), solver.handle)
+        return w
 
     def set_output_bias(self, mean_target):
         """Start the logistic output at the training targets' mean."""

@@ -47,13 +47,17 @@ def test_gpu_forward_matches_oracle_elementwise(shape):
     assert np.abs(got - yref).max() <= 2e-6
 
 
-def test_gpu_gradient_matches_oracle():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_gpu_gradient_matches_oracle(weighted):
+    """Loss and gradient against the oracle, without and with the face-flux weights."""
     D, H, W, hidden, layers = 3, 4, 5, 8, 3
     net = _net(D, H, W, hidden, layers)
     rng = np.random.default_rng(1)
     x = torch.from_numpy(rng.normal(size=(3, 4, D, H, W)).astype(np.float32)).cuda()
     t = torch.from_numpy(rng.uniform(size=(3, 1, D, H, W)).astype(np.float32)).cuda()
-    grad, loss = net.gradient(x, t)
+    wn = (rng.uniform(size=(3, 1, D, H, W)) * (rng.uniform(size=(3, 1, D, H, W)) < 0.4)).astype(np.float32)
+    wt = torch.from_numpy(wn).cuda() if weighted else None
+    grad, loss = net.gradient(x, t, weight=wt)
     torch.cuda.synchronize()
     cin = [4] + [hidden] * (layers - 1)
     cout = [hidden] * (layers - 1) + [1]
@@ -67,7 +71,8 @@ def test_gpu_gradient_matches_oracle():
         flat[off: off + co] = master[off: off + co]
         off += co
     params = conv3d.unflatten(flat, cin, cout)
-    lref, gref = conv3d.loss_and_grad(params, x.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64))
+    lref, gref = conv3d.loss_and_grad(params, x.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64),
+                                      wn.astype(np.float64) if weighted else None)
     gref = conv3d.flatten(gref)
     g = grad.cpu().numpy()
     assert abs(float(loss.cpu()[0]) - lref) <= 1e-5 * lref
