@@ -137,7 +137,6 @@ struct Layout {
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t bpart, bcnt;    // row-chunk partial sums and counters of the split boundary back substitution
     size_t fb_W, fb_Y, fb_subs, fb_list;   // FP64 fallback: block factors, forward values, subdomain records, slots
-    size_t active;                         // subdomains with a column still refining, in list order
     size_t total;
 };
 
@@ -267,7 +266,6 @@ enum StatusWord { ST_NOT_SPD = 0, ST_UNCONVERGED = 1, ST_ZERO_PIVOT = 2, ST_SWEE
                   ST_FB_TOTAL = 7 /* subdomains re-solved in FP64 */,
                   ST_SWEPT = 8 /* 64-bit counter at words 8-9 */,
                   ST_FB_LOST = 10 /* subdomains that needed the fallback and could not have it */,
-                  ST_ACTIVE = 11 /* subdomains with a column still refining (the next sweep's list length) */,
                   ST_CG_ITERS = 12 /* 64-bit counter at words 12-13: CG iterations of the learned form */,
                   ST_COUNT = 16 };
 

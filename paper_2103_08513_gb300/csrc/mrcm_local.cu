@@ -1744,42 +1744,6 @@ k_pp_velocity(const SubInfo* __restrict__ subs, const double* __restrict__ X, co
     if (threadIdx.x == 0) atomicMax(mres_bits, (unsigned long long)__double_as_longlong(red[0]));
 }
 
-// The subdomains of a list that still have a column refining (conv = 0),
-// compacted in list order by one CTA (ballots and a running offset), with
-// their count in status[ST_ACTIVE]: the next sweep visits only those.
-__global__ void __launch_bounds__(1024)
-k_active_list(const SubInfo* __restrict__ subs, const int* __restrict__ list, int nlist, const int* __restrict__ conv,
-              int* __restrict__ out, int* __restrict__ status) {
-    __shared__ int wsum[32];
-    __shared__ int base_s;
-    if (threadIdx.x == 0) base_s = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q0 = 0; q0 < nlist; q0 += blockDim.x) {
-        const int q = q0 + threadIdx.x;
-        int act = 0, l = 0;
-        if (q < nlist) {
-            l = list[q];
-            const SubInfo& s = subs[l];
-            for (int j = 0; j < s.m && !act; ++j) act = conv[s.rhs_off + j] == 0;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, act);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = base_s;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        if (act) out[before + __popc(bal & ((1u << lane) - 1u))] = l;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < nw; ++w) tot += wsum[w];
-            base_s += tot;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) status[ST_ACTIVE] = base_s;
-}
-
 // FP64 fallback (mixed modes): after the last refinement sweep of a wave, every
 // subdomain with a column still above the tolerance takes a slot (atomic
 // ticket) whose record is a copy of its own with the block-factor and
@@ -2058,22 +2022,10 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
         g.count_unconverged = 0;
         launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
         if (precision != MRCM_FP64) {
-            const int* wave_list = g.list;
-            const int wave_n = g.nlist;
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps && fb_cap == 0 ? 1 : 0;
-                if (it > 0) {
-                    // later sweeps visit only the subdomains with a column still refining
-                    MRCM_LAUNCH(P, "k_active_list", st, k_active_list<<<1, 1024, 0, st>>>(d.subs, wave_list, wave_n, g.conv,
-                                (int*)(ws + L.active), status));
-                    g.list = (const int*)(ws + L.active);
-                    g.nlist_dev = status + ST_ACTIVE;
-                }
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
             }
-            g.list = wave_list;
-            g.nlist = wave_n;
-            g.nlist_dev = nullptr;
             if (fb_cap > 0) launch_fallback(t, d, L, ws, g, fb_cap, fb_stride, fb_ystride, st, P);
         } else {
             // FP64 form: the direct solve through the explicit block inverses plus one

@@ -526,7 +526,6 @@ void compute_layout(const Tables& t, Layout& L) {
         L.fb_subs = take((size_t)cap * sizeof(SubInfo));
         L.fb_list = take((size_t)cap * sizeof(int));
     }
-    L.active = take(t.subs.size() * sizeof(int));
     L.total = off;
 }
 
