@@ -616,8 +616,7 @@ def main():
         try:
             s64 = make("fp64")
         except Exception:
-            # the FP64 block factor keeps its packed block in shared memory (b <= 224);
-            # larger slab blocks are compared against a tightly refined mixed solve
+            # no FP64 handle for this problem: compare against a tightly refined mixed solve
             s64 = MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha,
                        beta_const=w.beta_const, precision=args.precision, ir_max_sweeps=12, ir_tol=1e-15,
                        device=dev, wave_bytes=wave_bytes)

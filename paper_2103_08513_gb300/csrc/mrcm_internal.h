@@ -11,7 +11,7 @@
 namespace mrcm {
 
 constexpr int kMaxBlock = 256;      // largest slab block b (FP32 factor; FP64 factor: kMaxBlock64)
-constexpr int kMaxBlock64 = 224;    // largest slab block b of the FP64 factor (packed triangle in shared memory)
+constexpr int kMaxBlock64 = 224;    // largest slab block b whose FP64 packed triangle fits shared memory (larger: global slot)
 constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the register-resident FP32 factor
 constexpr int kMaxSolveVariants = 16;  // capacity of the per-variant tables
 constexpr int kNumFactorVariants = 3;  // factor kernels for blocks with b <= 64
@@ -37,6 +37,8 @@ struct SubInfo {
     long long cell_off;   // offset into per-cell arrays
     long long x_off;      // offset (doubles) into the MBF array [m][N]
     long long y_off;      // offset (elements) of the forward-sweep values Y (= x_off; a slot for the FP64 fallback)
+    int big_slot;         // FP64 form, b > kMaxBlock64: the subdomain's slot (in its wave) of the factor's
+                          // packed triangle in global memory; -1 = the triangle fits shared memory
     long long w_off;      // offset (elements) into the block factor array
     long long el_off;     // offset (doubles) into element matrices
     int elb_off;          // offset (doubles) into element right-hand sides
@@ -129,6 +131,7 @@ struct Tables {
     std::vector<SubInfo> pp_subs;
     std::vector<int> pp_wave_off;
     bool pp_ok = true;
+    int big_slots = 0;             // FP64 form: most subdomains of one wave with b > kMaxBlock64
 };
 
 // Workspace layout (byte offsets into the caller's workspace).
@@ -137,6 +140,7 @@ struct Layout {
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t bpart, bcnt;    // row-chunk partial sums and counters of the split boundary back substitution
     size_t fb_W, fb_Y, fb_subs, fb_list;   // FP64 fallback: block factors, forward values, subdomain records, slots
+    size_t big;                            // FP64 form: packed triangles of blocks with b > kMaxBlock64 (one wave)
     size_t total;
 };
 

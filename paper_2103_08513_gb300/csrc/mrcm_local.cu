@@ -188,14 +188,17 @@ __global__ void __launch_bounds__(kThreads)
 k_block_factor(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
                const double* __restrict__ scale, T* __restrict__ Wall, int* __restrict__ status,
                long long nct, float* __restrict__ scf_all, float* __restrict__ tsc_all,
-               const int* __restrict__ limit /* CTAs from *limit on have no subdomain; may be NULL */) {
+               const int* __restrict__ limit /* CTAs from *limit on have no subdomain; may be NULL */,
+               T* __restrict__ big /* packed triangles of the blocks with a global slot; may be NULL */) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (limit && (int)blockIdx.x >= *limit) return;
     const SubInfo s = subs[list[blockIdx.x]];
     const int b = s.b, su = s.su;
-    T* Lp = reinterpret_cast<T*>(smem_raw);                  // packed lower triangle
-    T* rk = Lp + ((packed_len(b) + 3) & ~size_t(3));           // row k
+    T* rk = reinterpret_cast<T*>(smem_raw);                    // row k
     T* tv = rk + b;                                            // scaled couplings to the previous slab
+    // packed lower triangle: shared memory, or the subdomain's global slot (L2-resident) when it is too large
+    T* Lp = (big && s.big_slot >= 0) ? big + (size_t)s.big_slot * packed_len(kMaxBlock)
+                                     : tv + ((b + 1) & ~1);
     const double* cd = coef + s.cell_off;
     const double* cu = coef + nct + s.cell_off;
     const double* cv = coef + 2 * nct + s.cell_off;
@@ -270,7 +273,7 @@ k_block_factor(const SubInfo* __restrict__ subs, const int* __restrict__ list, c
 }
 
 template <typename T>
-size_t factor_smem(int b) { return sizeof(T) * (((packed_len(b) + 3) & ~size_t(3)) + 2 * (size_t)b); }
+size_t factor_smem(int b) { return sizeof(T) * (packed_len(b) + 2 * (size_t)b + 4); }
 
 // ---------------------------------------------------------------------------
 // Register-resident variant of the block factorisation for b <= 64 (FP32,
@@ -1801,9 +1804,10 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
     const int n_small = o1 - o0, n_mid = o2 - o1, n_large = o3 - o2;
     if (precision == MRCM_FP64) {
         if (n_large > 0) {
-            size_t sm = factor_smem<double>(t.max_b);
+            size_t sm = factor_smem<double>(std::min(t.max_b, kMaxBlock64));   // larger blocks: global slot
             MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<double, false><<<n_large, kThreads, sm, st>>>(d.subs, d.class_list + o2, coef, scale,
-                (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc), nullptr));
+                (double*)(ws + L.W), status, t.n_cells, (float*)(ws + L.scf), (float*)(ws + L.tsc), nullptr,
+                (double*)(ws + L.big)));
         }
     } else {
         if (n_small > 0) {
@@ -1843,7 +1847,7 @@ static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Lay
             case 544: MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor_tri<544><<<n, 544, 0, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc)); break;
             default: {
                 size_t sm = factor_smem<float>(t.max_b);
-                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n, kThreads, sm, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc, nullptr));
+                MRCM_LAUNCH(P, "k_block_factor", st, k_block_factor<float, true><<<n, kThreads, sm, st>>>(d.subs, lst, coef, scale, W, status, t.n_cells, scf, tsc, nullptr, nullptr));
             }
             }
             q = e;
@@ -1978,7 +1982,7 @@ static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout
     for (const SubInfo& s : t.subs) if (s.b <= kMaxBlock64) bmax = std::max(bmax, s.b);
     MRCM_LAUNCH(P, "k_fb_factor", st, k_block_factor<double, false><<<cap, kThreads, factor_smem<double>(bmax), st>>>(
                 fb_subs, fb_list, g0.coef, g0.scale, (double*)(ws + L.fb_W), status, t.n_cells, nullptr, nullptr,
-                status + ST_FB_WAVE));
+                status + ST_FB_WAVE, nullptr));
     LocalArgs g = g0;
     g.subs = fb_subs;
     g.list = fb_list;
@@ -2087,7 +2091,7 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
             g.nlist = n;
             MRCM_LAUNCH(P, "k_pp_factor", st, k_block_factor<double, false><<<n, kThreads, factor_smem<double>(bmax), st>>>(
                         d.pp_subs, g.list, coef, (const double*)(ws + L.scale), (double*)(ws + L.W), status, t.n_cells,
-                        nullptr, nullptr, nullptr));
+                        nullptr, nullptr, nullptr, nullptr));
             const int grid = std::max(1, std::min(n, d.sms * d.f64_occ));
             void* args[] = {(void*)&g, (void*)&W};
             g.count_unconverged = 0;

@@ -149,7 +149,8 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
                 s.b = s.su * s.sv;
                 s.ns = s.sz[sa];
                 s.N = s.b * s.ns;
-                const int bmax = cfg->precision == MRCM_FP64 ? kMaxBlock64 : kMaxBlock;
+                s.big_slot = -1;
+                const int bmax = kMaxBlock;
                 if (s.b > bmax) {
                     err = "subdomain slab block " + std::to_string(s.b) + " exceeds " + std::to_string(bmax);
                     return MRCM_ERR_NOT_IMPLEMENTED;
@@ -269,6 +270,17 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
         t.wave_off.push_back(nsub);
         t.n_waves = (int)t.wave_off.size() - 1;
         t.total_w = wmax;
+        // FP64 form: blocks above kMaxBlock64 keep their packed triangle in a global slot
+        if (cfg->precision == MRCM_FP64) {
+            for (int w = 0; w < t.n_waves; ++w) {
+                int k = 0;
+                for (int q = t.wave_off[w]; q < t.wave_off[w + 1]; ++q) {
+                    SubInfo& s = t.subs[t.solve_list[q]];
+                    if (s.b > kMaxBlock64) s.big_slot = k++;
+                }
+                t.big_slots = std::max(t.big_slots, k);
+            }
+        }
         t.class_list.clear();
         for (int w = 0; w < t.n_waves; ++w) {
             std::vector<std::tuple<int, double, int>> cls[3];
@@ -526,6 +538,7 @@ void compute_layout(const Tables& t, Layout& L) {
         L.fb_subs = take((size_t)cap * sizeof(SubInfo));
         L.fb_list = take((size_t)cap * sizeof(int));
     }
+    L.big = take((size_t)t.big_slots * ((size_t)kMaxBlock * (kMaxBlock + 1) / 2) * sizeof(double));
     L.total = off;
 }
 

@@ -141,8 +141,13 @@ def test_c3_uneven_setup(lib):
     lib.mrcm_query_sizes(h, C.byref(sz))
     assert sz.n_sub == w.n_sub and sz.max_block == 256
     lib.mrcm_destroy(h)
-    # the FP64 factor keeps its packed block in shared memory: 16x16 slabs do not fit
+    # FP64 form: 16x16 slabs (b = 256) factor their packed triangle in a global slot
     cfg, keep = _cfg(w, precision=0)
+    assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 0, lib.mrcm_last_error(None)
+    lib.mrcm_destroy(h)
+    # slab blocks above 256 are refused
+    big = small(n=(34, 17, 17), edges=([17, 17], [17], [17]))
+    cfg, keep = _cfg(big, precision=1)
     assert lib.mrcm_setup(C.byref(cfg), C.byref(h)) == 8
 
 

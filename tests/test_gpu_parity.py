@@ -117,8 +117,11 @@ def test_uneven_blocks_mixed(name):
     assert rel_l2(u.ravel(), r.u.ravel()) < 1e-8
 
 
-def test_uneven_blocks_fp64():
-    w = small(**UNEVEN["uneven_mix"])
+@pytest.mark.parametrize("name", ["uneven_mix", "big_blocks", "odd_large"])
+def test_uneven_blocks_fp64(name):
+    """FP64 form on uneven blocks, including b = 256 (16 x 16 slabs), whose packed
+    FP64 triangle does not fit shared memory and is factored in a global slot."""
+    w = small(**UNEVEN[name])
     prob, r = _oracle(w)
     s, p, u, X, mres, code, st = run_gpu(w, prob.K, prob.f, "fp64")
     assert code == 0, st
