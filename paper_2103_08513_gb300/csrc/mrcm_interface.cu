@@ -52,19 +52,26 @@ __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const 
                                const long long* __restrict__ src_hi, const int* __restrict__ rsl,
                                const int* __restrict__ rsh, const int* __restrict__ colidx,
                                const double* __restrict__ elem, const double* __restrict__ elem_b,
-                               double* __restrict__ val, double* __restrict__ b, double* __restrict__ dscale) {
+                               double* __restrict__ val, double* __restrict__ b, double* __restrict__ dscale,
+                               int pin) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    double diag = 0.0;
+    double diag = 0.0, rowmax = 0.0;
     for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) {
         double v = 0.0;
         if (src_lo[q] >= 0) v += elem[src_lo[q]];
         if (src_hi[q] >= 0) v += elem[src_hi[q]];
         val[q] = v;
         if (colidx[q] == r) diag = v;
+        rowmax = fmax(rowmax, fabs(v));
     }
     b[r] = elem_b[rsl[r]] + elem_b[rsh[r]];
     double ad = fabs(diag);
+    // The pressure constant is removed by -c e_0 e_0^T with c = 1 / dscale[0]^2 (the factorisation
+    // subtracts 1 from the scaled pinned entry); any c > 0 gives the solution with pi^p_0 = 0.  c is
+    // the row's largest entry: |A_00| itself unless A_00 vanishes, which it does when the
+    // subdomains around basis 0 carry no other basis (their P-MBF is the constant 1, no flux).
+    if (pin && r == 0) ad = rowmax;
     dscale[r] = ad > 0.0 ? rsqrt(ad) : 1.0;
 }
 
@@ -1019,7 +1026,7 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
     MRCM_LAUNCH(P, "k_assemble_csr", st, k_assemble_csr<<<(nd + 127) / 128, 128, 0, st>>>(nd, d.rowptr, d.src_lo, d.src_hi, d.rhs_src_lo, d.rhs_src_hi,
                                                    d.colidx, (const double*)(ws + L.elem),
                                                    (const double*)(ws + L.elem_b), (double*)(ws + L.csr_val),
-                                                   (double*)(ws + L.b_int), dscale));
+                                                   (double*)(ws + L.b_int), dscale, t.has_dirichlet ? 0 : 1));
     // numeric multifrontal factorisation, leaves to root
     double* F = (double*)(ws + L.fronts);
     double* Pv = (double*)(ws + L.panel);       // inverse diagonal blocks of the panels
