@@ -599,7 +599,8 @@ def main():
     wave_bytes = int(wave_gb * (1 << 30))
 
     def make(precision, **kw):
-        cfg = dict(h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const, patch=w.patch)
+        cfg = dict(h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const, patch=w.patch,
+                   interface_refine=bs["interface_refine"])
         cfg.update(kw)
         patch = cfg.pop("patch")
         return MRCM(w.n, w.edges, patch, precision=precision, ir_max_sweeps=args.ir_sweeps, ir_tol=args.ir_tol,
@@ -783,6 +784,7 @@ def main():
                    "execution": "CUDA graph of the five device calls, replayed per step",
                    "autotuned_variants": s.tuning(),
                    "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
+                   "interface_refine_steps": max(0, bs["interface_refine"]) if bs["interface_refine"] else 1,
                    "ir_tol": args.ir_tol if args.precision != "fp64" else None,
                    "waves": {"budget_bytes": wave_bytes, "count": s.sizes.get("n_waves", 1)},
                    "parallelism": "replicas" if ws > 1 else "single",

@@ -64,7 +64,7 @@ def test_contrast_stress_mixed_matches_oracle(theta):
     r = oracle.solve_mrcm(prob)
     bs = BENCH_SETTINGS["c2"]
     s, p, u, X, mres, code, st = run_gpu(w, K, prob.f, "fp32_ir", ir_max_sweeps=bs["ir_sweeps"],
-                                         ir_tol=bs["ir_tol"])
+                                         ir_tol=bs["ir_tol"], interface_refine=bs["interface_refine"])
     fb, lost = s.read_fallback()
     ep, eu = rel_l2(p, r.p), rel_l2(u.ravel(), r.u.ravel())
     print(f"theta {theta}: contrast {K.max() / K.min():.2e}  p {ep:.2e}  u {eu:.2e}  fallback {fb}  lost {lost}  {st}")

@@ -1,8 +1,8 @@
 """Full-size workloads in the benchmark's own launch configuration, against the oracle.
 
 * C2 (60x220x85, 2244 subdomains): the mixed solve exactly as the benchmark
-  times it (autotuned kernels, CUDA-graph replay, the FP64 refinement sweeps
-  and per-column stop of BENCH_SETTINGS) against the whole staged oracle run over all host
+  times it (autotuned kernels, CUDA-graph replay, the FP64 refinement sweeps,
+  per-column stop and interface refinement steps of BENCH_SETTINGS) against the whole staged oracle run over all host
   cores: p, u, X at 1e-8 relative L2, A^int and b^int entrywise.  The FP64 GPU
   form at 1e-10.
 * C3 (uneven 8/12/16 blocks) and C5 (32768 blocks of 16x16x8 in
@@ -40,7 +40,7 @@ def _solver(w, precision, settings):
     from paper_2103_08513_gb300 import MRCM
     return MRCM(w.n, w.edges, w.patch, h=w.h, beta_mode=w.beta_mode, alpha=w.alpha, beta_const=w.beta_const,
                 precision=precision, ir_max_sweeps=settings["ir_sweeps"], ir_tol=settings["ir_tol"],
-                wave_bytes=int(settings["wave_gb"] * (1 << 30)))
+                wave_bytes=int(settings["wave_gb"] * (1 << 30)), interface_refine=settings["interface_refine"])
 
 
 def _bench_solve(s, K, f):
