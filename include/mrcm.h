@@ -248,7 +248,9 @@ mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double*
  * Needs a completed solve (after mrcm_reconstruct or mrcm_solve); it
  * overwrites the local coefficients, factors and MBF columns, so the next
  * solve must start again from mrcm_factor_local (MRCM_ERR_STATE otherwise).
- * Unconverged refinement columns are reported by mrcm_read_status. */
+ * The refinement stops on the normwise backward error,
+ * ||r|| <= cfg.ir_tol || |b| + |A||x| || (1e-14 when ir_tol is 0); columns that
+ * miss it after the three steps are reported by mrcm_read_status. */
 mrcm_status mrcm_postprocess_velocity(mrcm_handle* h, const double* u, double* u_out, double* mass_residual_max,
                                       void* ws, void* stream);
 
@@ -290,7 +292,8 @@ mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double*
 
 /* Autotuner (run after mrcm_factor_local): times every variant of the local
  * solve kernels (128, 256 or 512 threads per CTA x SIMT block products with
- * 1, 2 or 4 rows per thread or 3xTF32 tensor-core block products) on
+ * 1, 2 or 4 rows per thread, 2 adjacent rows per thread (even blocks) or
+ * 3xTF32 tensor-core block products) on
  * this problem, keeps the fastest first-solve and refinement-sweep variants
  * for the handle, and appends them to cfg.tune_cache when one was given (a
  * later mrcm_setup with the same cache and problem shape reuses them without
@@ -298,9 +301,16 @@ mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double*
 mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
                           int* sweep_variant);
 
+/* Median times (ms) of every local-solve variant in the last mrcm_autotune
+ * of this handle (host only): solve_ms[v] the first solve, sweep_ms[v] the
+ * cfg.ir_max_sweeps refinement sweeps (-1 where not timed: FP64 handles time
+ * no sweeps).  Writes min(*n, cap) entries of each non-NULL array; *n = the
+ * number of variants (0 before any autotune). */
+mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int cap, int* n);
+
 /* The kernel variants the handle uses (host only; after mrcm_autotune or a
  * tune-cache hit, else the defaults): local solve first pass and refinement
- * sweep (0-9), factor for blocks with b <= 64 (0 a row per thread, 1 8x8
+ * sweep (0-11), factor for blocks with b <= 64 (0 a row per thread, 1 8x8
  * register tiles, 2 4x4 tiles) and for 64 < b <= 128 (0 register tiles,
  * 1 tensor cores with the block in tensor memory).  Any pointer may be NULL. */
 mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* sweep_variant, int* factor_small,

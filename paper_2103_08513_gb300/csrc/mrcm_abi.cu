@@ -455,6 +455,16 @@ mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* swe
     return MRCM_OK;
 }
 
+mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int cap, int* n) {
+    if (!h || cap < 0) return MRCM_ERR_INVALID_ARG;
+    if (n) *n = h->tune_n;
+    for (int v = 0; v < h->tune_n && v < cap; ++v) {
+        if (solve_ms) solve_ms[v] = h->tune_ms[2 * v];
+        if (sweep_ms) sweep_ms[v] = h->tune_ms[2 * v + 1];
+    }
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* stream, int* solve_variant,
                           int* sweep_variant) {
     if (!h) return MRCM_ERR_INVALID_ARG;
@@ -465,8 +475,11 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
     if (h->t.cfg.precision == MRCM_LEARNED_PCG) return fail(h, MRCM_ERR_INVALID_ARG, "the learned form has no direct solve to tune");
     int v0 = 0, v1 = 0, v2 = h->d.factor_variant, v3 = h->d.factor_mid_variant;
     float ms[2 * mrcm::kMaxSolveVariants];
+    for (float& x : ms) x = -1.0f;
     int rc = mrcm::autotune_local(h->t, h->d, h->lay, (char*)ws, f, stream, 3, &v0, &v1, &v2, &v3, ms);
     if ((st = after_launch(h, rc, "mrcm_autotune")) != MRCM_OK) return st;
+    for (int i = 0; i < 2 * mrcm::kMaxSolveVariants; ++i) h->tune_ms[i] = ms[i];
+    h->tune_n = mrcm::num_solve_variants();
     h->d.solve_variant = v0;
     h->d.sweep_variant = v1;
     h->d.factor_variant = v2;

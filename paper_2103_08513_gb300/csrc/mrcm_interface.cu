@@ -309,11 +309,43 @@ __device__ __forceinline__ void oz_slice_row(double x, int j, int W, bool store,
     if (j == 0) *exp_out = E;
 }
 
+// Slices of one panel row held as pairs: lane p of a 16-lane segment holds
+// columns p and 31 - p (values x1, x2).  Same slices and exponent as
+// oz_slice_row over the full row.
+__device__ __forceinline__ unsigned long long oz_fixed(unsigned long long mag, int E) {   // floor(|x| 2^{56-E})
+    const int ex = (int)(mag >> 52);
+    if (ex == 0) return 0ull;
+    const unsigned long long mant = (mag & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1023 + 4 - E;                                      // <= 3
+    return sh >= 0 ? (mant << sh) : (-sh < 64 ? (mant >> -sh) : 0ull);
+}
+__device__ __forceinline__ void oz_slice_pair(double x1, double x2, int p, bool store, __nv_bfloat16* dst,
+                                              int* exp_out) {
+    const unsigned long long b1 = (unsigned long long)__double_as_longlong(x1);
+    const unsigned long long b2 = (unsigned long long)__double_as_longlong(x2);
+    const unsigned long long m1 = b1 & 0x7FFFFFFFFFFFFFFFull, m2 = b2 & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long mx = seg_max_u64(m1 > m2 ? m1 : m2, 16);
+    const int E = mx == 0 ? 0 : (int)(mx >> 52) - 1023 + 1;
+    const unsigned long long F1 = oz_fixed(m1, E), F2 = oz_fixed(m2, E);
+    if (!store) return;                                                    // after the segment reduction
+    const bool n1 = (b1 >> 63) != 0, n2 = (b2 >> 63) != 0;
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t) {
+        const int v1 = (int)((F1 >> (49 - 7 * t)) & 127ull), v2 = (int)((F2 >> (49 - 7 * t)) & 127ull);
+        dst[t * kPanel + p] = __float2bfloat16_rn((float)(n1 ? -v1 : v1));
+        dst[t * kPanel + kPanel - 1 - p] = __float2bfloat16_rn((float)(n2 ? -v2 : v2));
+    }
+    if (p == 0) *exp_out = E;
+}
+
 // Panel step of the blocked LDL^T: the rows below the (already factored)
 // diagonal block, l = a L11^{-T} D^{-1}, i.e. l_j = sum_{k <= j} a_k V[j][k] / d_j
-// with V = L11^{-1}.  A warp holds 32 / W rows at once, W = the panel width
-// rounded up to a power of two (one lane per column), so narrow panels do
-// not waste FP64 issue slots; kPanelRows x 32 / W rows per CTA.
+// with V = L11^{-1}.  Panels wider than 16 columns: a warp holds two rows,
+// lane p of each half computes columns p and 31 - p (p + 1 and 32 - p terms of
+// the triangular product, 33 FMAs in two chains instead of 32 per column), 8
+// rows per CTA.  Narrower panels: a warp holds 32 / W rows at once, W = the
+// panel width rounded up to a power of two (one lane per column), so narrow
+// panels do not waste FP64 issue slots; kPanelRows x 32 / W rows per CTA.
 __global__ void __launch_bounds__(128)
 k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
             const double* __restrict__ P, __nv_bfloat16* __restrict__ oz, int* __restrict__ oz_exp) {
@@ -324,7 +356,7 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
     const int k1 = k0 + nbk;
     const int W = nbk <= 1 ? 1 : 1 << (32 - __clz(nbk - 1));
     const int R = kPanel / W;                                   // rows per warp pass
-    const int rows = kPanelRows * R;                            // rows of this CTA
+    const int rows = W == kPanel ? 2 * kPanelRows : kPanelRows * R;   // rows of this CTA
     const int r0 = k1 + blockIdx.x * rows;
     if (r0 >= n) return;
     const int r_end = min(n, r0 + rows);
@@ -340,8 +372,39 @@ k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, i
         Dinv[threadIdx.x] = threadIdx.x < nbk ? rcp64(d) : 0.0;
     }
     __syncthreads();
-    const int rs = lane / W, j = lane % W;
     const bool oz_on = oz_step(fr, n - k1, nbk);
+    if (W == kPanel) {
+        __shared__ double As[kPanelRows][2][kPanel];
+        const int h = lane >> 4, p = lane & 15, p2 = kPanel - 1 - p;
+        const int r = r0 + 2 * w + h;
+        const bool live = r < r_end;
+        double* row = A + (long long)min(r, r_end - 1) * n + k0;
+        double* as = As[w][h];
+        as[p] = (live && p < nbk) ? row[p] : 0.0;
+        as[p2] = (live && p2 < nbk) ? row[p2] : 0.0;
+        __syncwarp();
+        // chain A: terms q = 0 .. 16 (column p while q <= p, then column p2);
+        // chain B: q = 17 .. 32, all of column p2 (k = q - p - 1)
+        double x1 = 0.0, x2 = 0.0, y2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 17; ++q) {
+            const bool f = q <= p;
+            const int k = f ? q : q - p - 1;
+            const double v = fma(as[k], Vs[f ? p : p2][k], f ? x1 : x2);
+            if (f) x1 = v; else x2 = v;
+            if (q < 16) y2 = fma(as[q + 16 - p], Vs[p2][q + 16 - p], y2);
+        }
+        const double l1 = x1 * Dinv[p], l2 = (x2 + y2) * Dinv[p2];
+        if (live && p < nbk) row[p] = l1;
+        if (live && p2 < nbk) row[p2] = l2;
+        if (oz_on) {                                              // all lanes: segment reductions inside
+            const long long sr = (long long)fr.s_off + min(r, r_end - 1);
+            oz_slice_pair(l1 * Dd[p], l2 * Dd[p2], p, live, oz + sr * (2 * kOzS * kPanel), oz_exp + 2 * sr);
+            oz_slice_pair(l1, l2, p, live, oz + sr * (2 * kOzS * kPanel) + kOzS * kPanel, oz_exp + 2 * sr + 1);
+        }
+        return;
+    }
+    const int rs = lane / W, j = lane % W;
     for (int base = r0 + w * R; base < r_end; base += 4 * R) {
         const int r = base + rs;
         const bool live = r < r_end && j < nbk;
@@ -1006,7 +1069,7 @@ LevelPlan plan_level(const Tables& t, int h) {
             if (k0 >= f.ne) continue;
             int k1 = k0 + std::min(kPanel, f.ne - k0);
             int m = f.n - k1;
-            rt = std::max(rt, (m + kPanelRows - 1) / kPanelRows);
+            rt = std::max(rt, (m + 2 * kPanelRows - 1) / (2 * kPanelRows));   // >= 8 rows per CTA
             int nt = (m + kPanel - 1) / kPanel;
             ut = std::max(ut, nt * (nt + 1) / 2);
         }

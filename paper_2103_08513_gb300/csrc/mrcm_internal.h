@@ -307,6 +307,8 @@ struct mrcm_handle {
     cudaGraphExec_t graph_exec = nullptr;
     const void* graph_key[9] = {};
     long long graph_launches = 0;
+    float tune_ms[2 * mrcm::kMaxSolveVariants] = {};   // last autotune: first solve / sweeps per variant
+    int tune_n = 0;                                    // variants timed (0: no autotune yet)
     int* col_list = nullptr;              // learned-path (subdomain, column) list of every MBF column
     int n_cols = 0;
     int* samp_off = nullptr;              // learned-path sample tables (internal)
@@ -326,6 +328,7 @@ void compute_layout(const Tables& t, Layout& lay);
 
 // Kernel launchers (CUDA translation units).  Each returns cudaError_t as int.
 namespace mrcm {
+int num_solve_variants();
 int launch_factor(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,
                   const double* K, int precision, void* stream, Prof& P);
 int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, char* ws,

@@ -1054,6 +1054,42 @@ __device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* _
     }
 }
 
+// Pair tile (b even): thread tile of rows (i0, i0 + 1) x 4 columns, one
+// 2-element load of W and one 4-element load of Z per k for 8 FMAs, no row
+// guard (every row pair lies inside the block).
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T, typename Store>
+__device__ __forceinline__ void block_gemm_pair(const T* __restrict__ Wsm, const T* __restrict__ Z, int b, int na,
+                                                int mpad, Store store) {
+    const int bh = b >> 1;
+    const int mq = (na + 3) >> 2;
+    for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
+        const int i0 = 2 * (task % bh), cq = task / bh;
+        T a0[4], a1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a0[q] = (T)0; a1[q] = (T)0; }
+        const T* zc = Z + 4 * cq;
+        const T* wc = Wsm + i0;
+#pragma unroll 2
+        for (int k = 0; k < b; ++k) {
+            const typename Vec4<T>::type z = ld4(zc + k * mpad);
+            const typename Vec2<T>::type w = *reinterpret_cast<const typename Vec2<T>::type*>(wc + k * b);
+            a0[0] += w.x * z.x; a0[1] += w.x * z.y; a0[2] += w.x * z.z; a0[3] += w.x * z.w;
+            a1[0] += w.y * z.x; a1[1] += w.y * z.y; a1[2] += w.y * z.z; a1[3] += w.y * z.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * cq + q;
+            if (jj < na) {
+                store(i0, jj, a0[q]);
+                store(i0 + 1, jj, a1[q]);
+            }
+        }
+    }
+}
+
 // Tensor-core variant of block_gemm (FP32 operands): warp-level
 // mma.sync.m16n8k8 with TF32 inputs and FP32 accumulation, each operand split
 // into a TF32 high part and a TF32 remainder, x*y ~ xh*yh + xh*yl + xl*yh
@@ -1114,10 +1150,14 @@ __device__ __forceinline__ void block_gemm_tc(const float* __restrict__ Wsm, con
 }
 
 // Dispatch: RT > 0 selects the SIMT tile with RT rows per thread, RT == 0 the
-// 3xTF32 tensor-core path (FP32 operands only).
+// 3xTF32 tensor-core path (FP32 operands only), RT < 0 the pair tile (odd b:
+// the one-row tile).
 template <typename T, int RT, typename Store>
 __device__ __forceinline__ void block_product(const T* Wsm, const T* Z, int b, int na, int mpad, Store store) {
-    if constexpr (RT == 0) {
+    if constexpr (RT < 0) {
+        if (b & 1) block_gemm<T, 1>(Wsm, Z, b, na, mpad, store);
+        else block_gemm_pair<T>(Wsm, Z, b, na, mpad, store);
+    } else if constexpr (RT == 0) {
         if constexpr (std::is_same<T, float>::value) block_gemm_tc(Wsm, Z, b, na, mpad, store);
     } else {
         block_gemm<T, RT>(Wsm, Z, b, na, mpad, store);
@@ -1491,11 +1531,12 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
 }
 
 // Tunable variants of the local solve: threads per CTA x block-product path
-// (SIMT with 2, 1 or 4 rows per thread, or 3xTF32 tensor cores for FP32).
-constexpr int kNumSolveVariants = 10;
+// (SIMT with 2, 1 or 4 rows per thread, the pair tile, or 3xTF32 tensor
+// cores for FP32).
+constexpr int kNumSolveVariants = 12;
 static_assert(kNumSolveVariants <= kMaxSolveVariants, "per-variant tables are too small");
 __host__ __device__ inline int variant_threads(int v) {
-    return v >= 8 ? 512 : v == 6 ? 256 : v == 7 ? 128 : v < 3 ? 256 : 128;
+    return v == 10 ? 256 : v == 11 ? 128 : v >= 8 ? 512 : v == 6 ? 256 : v == 7 ? 128 : v < 3 ? 256 : 128;
 }
 
 template <typename T, bool kScaled, bool kSweep>
@@ -1514,6 +1555,8 @@ const void* solve_kernel(int v) {
             if constexpr (std::is_same<T, float>::value) return (const void*)k_local_solve<T, kScaled, kSweep, 128, 0>;
             else return (const void*)k_local_solve<T, kScaled, kSweep, 128, 2>;
         case 8: return (const void*)k_local_solve<T, kScaled, kSweep, 512, 2>;
+        case 10: return (const void*)k_local_solve<T, kScaled, kSweep, 256, -2>;
+        case 11: return (const void*)k_local_solve<T, kScaled, kSweep, 128, -2>;
         default: return (const void*)k_local_solve<T, kScaled, kSweep, 512, 1>;
     }
 }
@@ -1530,14 +1573,18 @@ __global__ void __launch_bounds__(kThreads)
 k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
           const double* __restrict__ face_tr, const double* __restrict__ face_beta,
           const double* __restrict__ face_bst, const double* __restrict__ X, Geo geo,
-          double* __restrict__ elem, double* __restrict__ elem_b) {
+          double* __restrict__ elem, double* __restrict__ elem_b, int jb_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubInfo s = subs[blockIdx.x];
     const int nI = s.nI, m = s.m, N = s.N, dim = s.el_dim, nf = s.nface;
-    // the subdomain's face cells and weights, staged once
+    // the subdomain's face cells and weights, staged once; then the face
+    // cells' values of jb_max MBF columns at a time
     double* s_tr = reinterpret_cast<double*>(smem_raw);
     double* s_bst = s_tr + nf;
-    int* s_cell = reinterpret_cast<int*>(s_bst + nf);
+    double* s_be = s_bst + nf;
+    double* xs = s_be + nf;                           // [jb][face]
+    int* s_cell = reinterpret_cast<int*>(xs + (size_t)jb_max * nf);
+    int* s_sa = s_cell + nf;                          // side (+1 / -1) x 4 + normal axis
     __shared__ int start[kMaxI + 1];                  // per-column face ranges
     for (int q = threadIdx.x; q <= nI; q += blockDim.x) start[q] = nf;
     __syncthreads();
@@ -1546,63 +1593,91 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
         const int c = fi.col;
         if (q == 0 || faces[s.face_off + q - 1].col != c) start[c] = q;
         s_cell[q] = fi.cell;
+        s_sa[q] = 4 * fi.s + fi.axis;
         s_tr[q] = face_tr[s.face_off + q];
         s_bst[q] = face_bst[s.face_off + q];
+        s_be[q] = face_beta[s.face_off + q];
+    }
+    __syncthreads();
+    // per basis, the data terms of its own two columns (g = 1 on the P-MBF,
+    // g = -beta s on the U-MBF): sums over its faces in face order
+    __shared__ double s_gsum[4][kMaxI];             // sum T_R, sum beta s T_R, sum beta^2 s^2 T_R, sum beta A_f
+    for (int k = threadIdx.x; k < nI; k += blockDim.x) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int q = start[k]; q < start[k + 1]; ++q) {
+            const int sa = s_sa[q], ax = sa & 3;
+            const double be = s_be[q];
+            a0 += s_tr[q];
+            a1 += s_bst[q];
+            a2 += s_bst[q] * be * (double)((sa - ax) / 4);
+            a3 += be * geo.area[ax];
+        }
+        s_gsum[0][k] = a0; s_gsum[1][k] = a1; s_gsum[2][k] = a2; s_gsum[3][k] = a3;
     }
     __syncthreads();
     const double* Xs = X + s.x_off;
     // The faces of basis k all carry column k; the Robin data g of MBF column j
     // on them is 1 (j = k, P-MBF), -beta s (j = nI + k, U-MBF) or 0, so the
     // traces are sum T_R x and sum beta s T_R x plus a correction on those two
-    // columns: two FMAs per face and column.  Four faces' x values are read at
-    // once, into four partial sums per trace (four independent FMA chains; the
-    // partials are added in a fixed order).
-    for (int e = threadIdx.x; e < nI * m; e += blockDim.x) {
-        int k = e / m, j = e - (e / m) * m;
-        int q0 = start[k], q1 = start[k + 1];
-        const double* x = Xs + (long long)j * N;
-        double pf[4] = {0.0, 0.0, 0.0, 0.0}, pu[4] = {0.0, 0.0, 0.0, 0.0};
-        int q = q0;
-        for (; q + 3 < q1; q += 4) {
-            double xv[4];
+    // columns: two FMAs per face and column, in four partial sums per trace
+    // (face q0 + 4i + u of the basis to partial u; the partials are added in a
+    // fixed order).  The face values of a column batch are gathered first by
+    // consecutive threads over consecutive faces (neighbouring cells).
+    for (int j0 = 0; j0 < m; j0 += jb_max) {
+        const int jn = min(jb_max, m - j0);
+        const int tot = jn * nf;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 4 * blockDim.x) {
+            double v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = x[s_cell[q + u]];
+            for (int u = 0; u < 4; ++u) {                 // four loads in flight, then the stores
+                const int idx = i0 + u * blockDim.x;
+                const int jb = idx / nf, q = idx - jb * nf;
+                v[u] = idx < tot ? Xs[(long long)(j0 + jb) * N + s_cell[q]] : 0.0;
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                pf[u] = fma(s_tr[q + u], xv[u], pf[u]);
-                pu[u] = fma(s_bst[q + u], xv[u], pu[u]);
+                const int idx = i0 + u * blockDim.x;
+                if (idx < tot) xs[idx] = v[u];
             }
         }
-        for (int u = 0; q < q1; ++q, ++u) {
-            const double xv = x[s_cell[q]];
-            pf[u] = fma(s_tr[q], xv, pf[u]);
-            pu[u] = fma(s_bst[q], xv, pu[u]);
-        }
-        double sf = (pf[0] + pf[1]) + (pf[2] + pf[3]);
-        double su = (pu[0] + pu[1]) + (pu[2] + pu[3]);
-        double sdiag = 0.0;
-        if (j == k || j == nI + k) {
-            for (int q = q0; q < q1; ++q) {
-                const FaceInfo fi = faces[s.face_off + q];
-                const double tr = face_tr[s.face_off + q], bst = face_bst[s.face_off + q];
-                const double be = face_beta[s.face_off + q];
-                if (j == k) { sf -= tr; su -= bst; }                    // g = 1
-                else {                                                  // g = -beta s
-                    sf += bst;
-                    su += bst * be * fi.s;
-                    sdiag += be * geo.area[fi.axis];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nI * jn; e += blockDim.x) {
+            const int k = e / jn, jb = e - k * jn, j = j0 + jb;
+            const int q0 = start[k], q1 = start[k + 1];
+            const double* x = xs + (size_t)jb * nf;
+            double pf[4] = {0.0, 0.0, 0.0, 0.0}, pu[4] = {0.0, 0.0, 0.0, 0.0};
+            int q = q0;
+            for (; q + 3 < q1; q += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    pf[u] = fma(s_tr[q + u], x[q + u], pf[u]);
+                    pu[u] = fma(s_bst[q + u], x[q + u], pu[u]);
                 }
             }
+            for (int u = 0; q < q1; ++q, ++u) {
+                pf[u] = fma(s_tr[q], x[q], pf[u]);
+                pu[u] = fma(s_bst[q], x[q], pu[u]);
+            }
+            double sf = (pf[0] + pf[1]) + (pf[2] + pf[3]);
+            double su = (pu[0] + pu[1]) + (pu[2] + pu[3]);
+            double sdiag = 0.0;
+            if (j == k) { sf -= s_gsum[0][k]; su -= s_gsum[1][k]; }               // g = 1
+            else if (j == nI + k) {                                               // g = -beta s
+                sf += s_gsum[1][k];
+                su += s_gsum[2][k];
+                sdiag = s_gsum[3][k];
+            }
+            if (j < dim) {
+                elem[s.el_off + (long long)k * dim + j] = sf;
+                double uv = su;
+                if (j == nI + k) uv -= sdiag;
+                elem[s.el_off + (long long)(nI + k) * dim + j] = uv;
+            } else {
+                elem_b[s.elb_off + k] = -sf;
+                elem_b[s.elb_off + nI + k] = -su;
+            }
         }
-        if (j < dim) {
-            elem[s.el_off + (long long)k * dim + j] = sf;
-            double uv = su;
-            if (j == nI + k) uv -= sdiag;
-            elem[s.el_off + (long long)(nI + k) * dim + j] = uv;
-        } else {
-            elem_b[s.elb_off + k] = -sf;
-            elem_b[s.elb_off + nI + k] = -su;
-        }
+        __syncthreads();                              // xs is refilled by the next batch
     }
 }
 
@@ -1612,11 +1687,20 @@ __global__ void k_zero_int(int* p, int n) {
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
-// dynamic shared memory of k_element: cells and two weights of the largest face set
+// k_element: MBF columns per batch (at most 16, within about 96 KB of shared
+// memory for the largest face set) and its dynamic shared memory (per face:
+// cell, side and axis, three weights; the batch's face values)
+constexpr size_t kElFaceBytes = 3 * sizeof(double) + 2 * sizeof(int);
+static int element_batch(const Tables& t) {
+    int mx = 1;
+    for (const SubInfo& s : t.subs) mx = std::max(mx, s.nface);
+    const long long room = 96 * 1024 - (long long)mx * (long long)kElFaceBytes;
+    return (int)std::max(1LL, std::min(16LL, room / (long long)(mx * sizeof(double))));
+}
 static size_t element_smem(const Tables& t) {
     int mx = 1;
     for (const SubInfo& s : t.subs) mx = std::max(mx, s.nface);
-    return (size_t)mx * (2 * sizeof(double) + sizeof(int));
+    return (size_t)mx * kElFaceBytes + (size_t)element_batch(t) * mx * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
@@ -1676,6 +1760,49 @@ k_pp_coefficients(const SubInfo* __restrict__ subs, const double* __restrict__ u
         scale[i] = f32_to_f64(rsqrtf(f64_to_f32_rz(d)));
         rhs_part[i] = rd;
     }
+}
+
+// Stop scale of the post-processing refinement: the Neumann systems of
+// subdomains around a well have || |A||x| || up to 1e9 ||b|| (the oracle's
+// sparse LU leaves a relative residual ~1e-7 there), so ||r|| <= tol ||b|| is
+// out of FP64's reach.  After the first solve, the particular column's
+// squared scale becomes sum_c (|b_c| + sum_k |a_ck x_k|)^2 (normwise
+// Oettli-Prager form), and the sweeps stop on ||r|| <= tol times it.  One CTA
+// per listed subdomain, fixed-order reduction.
+__global__ void __launch_bounds__(kThreads)
+k_pp_scale(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
+           const double* __restrict__ rhs_part, const double* __restrict__ f, Geo geo, long long nct,
+           const double* __restrict__ X, double* __restrict__ bnorm) {
+    const SubInfo s = subs[list[blockIdx.x]];
+    const int N = s.N, b = s.b, su = s.su;
+    const double* cd = coef + s.cell_off;
+    const double* cu = coef + nct + s.cell_off;
+    const double* cv = coef + 2 * nct + s.cell_off;
+    const double* cs = coef + 3 * nct + s.cell_off;
+    const double* x = X + s.x_off + (long long)(s.m - 1) * N;
+    const double vol = geo.h[0] * geo.h[1] * geo.h[2];
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        int lc[3];
+        local_coords(s, c, lc);
+        const int i = c % b, u = i % su;
+        double t = fabs(rhs_part[s.cell_off + c] + f[global_cell(s, lc, geo.n)] * vol) + fabs(cd[c] * x[c]);
+        if (u + 1 < su) t += fabs(cu[c] * x[c + 1]);
+        if (u > 0) t += fabs(cu[c - 1] * x[c - 1]);
+        if (i + su < b) t += fabs(cv[c] * x[c + su]);
+        if (i >= su) t += fabs(cv[c - su] * x[c - su]);
+        if (c + b < N) t += fabs(cs[c] * x[c + b]);
+        if (c >= b) t += fabs(cs[c - b] * x[c - b]);
+        acc = fma(t, t, acc);
+    }
+    __shared__ double red[kThreads];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bnorm[s.rhs_off + s.m - 1] = fmin(red[0], 1e38);   // read back as FP32
 }
 
 // Post-processed velocity: TPFA of the Neumann solution (the particular column
@@ -1794,6 +1921,8 @@ Geo make_geo(const mrcm_config& c) {
 
 // Block factors of one wave's subdomains (register-resident FP32 kernel for
 // b <= 64, packed shared-memory kernel otherwise; one launch per class).
+int num_solve_variants() { return kNumSolveVariants; }
+
 static void launch_factor_wave(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, int precision,
                                int w, cudaStream_t st, Prof& P) {
     double* coef = (double*)(ws + L.coef);
@@ -2041,7 +2170,8 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
     MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_SWEEPS, precision == MRCM_FP64 ? 1 : sweeps));
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
-                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b),
+                                        element_batch(t)));
     return (int)cudaGetLastError();
 }
 
@@ -2072,6 +2202,8 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
             g.nlist = t.wave_off[w + 1] - t.wave_off[w];
             g.count_unconverged = 0;
             launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
+            MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<g.nlist, kThreads, 0, st>>>(g.subs, g.list, coef, g.rhs_dir,
+                        f, geo, t.n_cells, g.X, g.bnorm));
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
@@ -2098,6 +2230,8 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
             MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
             MRCM_LAUNCH(P, "k_pp_solve", st, cudaLaunchKernel(solve_kernel<double, false, false>(0), dim3(grid),
                         dim3(variant_threads(0)), args, d.f64_solve_smem, st));
+            MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<n, kThreads, 0, st>>>(g.subs, g.list, coef, g.rhs_dir,
+                        f, geo, t.n_cells, g.X, g.bnorm));
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps ? 1 : 0;
                 MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
@@ -2144,7 +2278,8 @@ int launch_local_finish(const Tables& t, const DeviceTables& d, const Layout& L,
     }
     MRCM_LAUNCH(P, "k_element", st, k_element<<<nsub, kThreads, element_smem(t), st>>>(d.subs, d.faces, (double*)(ws + L.face_tr), (double*)(ws + L.face_beta),
                                         (const double*)(ws + L.face_bst),
-                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b)));
+                                        (const double*)(ws + L.X), g.geo, (double*)(ws + L.elem), (double*)(ws + L.elem_b),
+                                        element_batch(t)));
     return (int)cudaGetLastError();
 }
 

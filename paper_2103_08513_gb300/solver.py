@@ -213,6 +213,14 @@ class MRCM:
         L.check(self.lib.mrcm_query_tuning(self.handle, *[C.byref(x) for x in v]), self.handle)
         return dict(zip(("solve", "sweep", "factor_small", "factor_mid"), (x.value for x in v)))
 
+    def tuning_times(self):
+        """(solve_ms, sweep_ms): per-variant median times of the last autotune (-1 = not timed)."""
+        cap = 16
+        a, b, n = (C.c_float * cap)(), (C.c_float * cap)(), C.c_int()
+        L.check(self.lib.mrcm_read_tuning_times(self.handle, a, b, cap, C.byref(n)), self.handle)
+        k = min(cap, n.value)
+        return [round(float(a[i]), 4) for i in range(k)], [round(float(b[i]), 4) for i in range(k)]
+
     def autotune(self, f, stream=None):
         """Pick the fastest local-solve kernel variants for this problem (after factor_local)."""
         v0, v1 = C.c_int(), C.c_int()

@@ -230,7 +230,7 @@ def test_repeat_calls_are_deterministic():
 
 @pytest.mark.parametrize("name", ["many_tiles", "uneven_mix", "blocks_128"])
 def test_every_solve_variant_matches_oracle(name, tmp_path):
-    """Each local-solve variant (SIMT tiles and the 3xTF32 tensor-core block
+    """Each local-solve variant (SIMT tiles, pair tiles and the 3xTF32 tensor-core block
     products), forced through the tune cache, reaches the mixed-mode bar."""
     import torch as T
     from paper_2103_08513_gb300 import MRCM
@@ -245,7 +245,7 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
     s.autotune(f)
     key, _, _, fv, fm = open(cache).read().split()[:5]
     # every solve variant with the tuned factors, then every factor kernel (b <= 64: 3, 64 < b <= 128: 2)
-    for v, fvv, fmv in [(v, fv, fm) for v in range(10)] + [(0, 0, 0), (0, 1, 0), (0, 2, 0), (0, 1, 1)]:
+    for v, fvv, fmv in [(v, fv, fm) for v in range(12)] + [(0, 0, 0), (0, 1, 0), (0, 2, 0), (0, 1, 1)]:
         with open(cache, "w") as fp:
             fp.write(f"{key} {v} {v} {fvv} {fmv}\n")
         sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)

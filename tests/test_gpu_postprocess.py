@@ -55,6 +55,7 @@ def test_postprocess_matches_oracle(name, prec, tol):
     print(f"{name} {prec}: rel err {rel_l2(up.ravel(), ref.ravel()):.3e}, mass residual {mres:.3e}, "
           f"unconverged columns {st['unconverged']}")
     assert rel_l2(up.ravel(), ref.ravel()) < tol
+    assert st["unconverged"] == 0                 # backward error <= 1e-13 after the FP64 steps
     # conservative on the fine scale, at the solve's accuracy
     fv = np.abs(prob.f).max() * prob.cell_volume
     assert mres <= (1e-11 if prec == "fp64" else 1e-7) * max(fv, 1.0)
