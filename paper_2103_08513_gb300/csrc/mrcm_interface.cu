@@ -45,6 +45,12 @@ namespace mrcm {
 namespace {
 
 constexpr int kThreads = 256;
+
+// Programmatic dependent launch: the kernels of the interface stage are
+// launched with programmatic stream serialization, so each can be scheduled
+// while its predecessor on the stream finishes; it waits here until the
+// predecessor has completed and its writes are visible.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr int kPanel = 32;        // LDL^T panel width
 constexpr int kTile = 64;         // assembly tile
 
@@ -54,6 +60,7 @@ __global__ void k_assemble_csr(int nrows, const int* __restrict__ rowptr, const 
                                const double* __restrict__ elem, const double* __restrict__ elem_b,
                                double* __restrict__ val, double* __restrict__ b, double* __restrict__ dscale,
                                int pin) {
+    pdl_begin();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     double diag = 0.0, rowmax = 0.0;
@@ -162,6 +169,7 @@ k_front_assemble(const FrontInfo* __restrict__ fronts, const int* __restrict__ i
                  const int* __restrict__ inv, const int* __restrict__ dofs, const SubInfo* __restrict__ subs,
                  const double* __restrict__ elem, const double* __restrict__ dscale, int NV,
                  double* __restrict__ F, double* __restrict__ P, int* __restrict__ status) {
+    pdl_begin();
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     const int n = fr.n;
     const int nt = (n + kTile - 1) / kTile;
@@ -349,6 +357,7 @@ __device__ __forceinline__ void oz_slice_pair(double x1, double x2, int p, bool 
 __global__ void __launch_bounds__(128)
 k_ldl_panel(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
             const double* __restrict__ P, __nv_bfloat16* __restrict__ oz, int* __restrict__ oz_exp) {
+    pdl_begin();
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
@@ -478,6 +487,7 @@ __global__ void __launch_bounds__(kThreads)
 k_ldl_update(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, int k0, double* __restrict__ F,
              double* __restrict__ P, int* __restrict__ status, const __nv_bfloat16* __restrict__ oz,
              const int* __restrict__ oz_exp) {
+    pdl_begin();
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     if (k0 >= fr.ne) return;
     const int n = fr.n;
@@ -610,6 +620,7 @@ k_front_forward(const FrontInfo* __restrict__ fronts, const int* __restrict__ id
                 const int* __restrict__ maps, const int* __restrict__ dofs,
                 const double* __restrict__ F, const double* __restrict__ P, const double* __restrict__ bglob,
                 const double* __restrict__ dscale, int NV, double* __restrict__ frhs) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* r = reinterpret_cast<double*>(smem_raw);
     const FrontInfo fr = fronts[ids[blockIdx.x]];
@@ -668,6 +679,7 @@ constexpr int kSolveRows = 8;
 __global__ void __launch_bounds__(kThreads)
 k_front_forward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const double* __restrict__ F,
                   double* __restrict__ frhs) {
+    pdl_begin();
     const FrontInfo fr = fronts[ids[blockIdx.y]];
     const int n = fr.n, ne = fr.ne;
     const int i = ne + blockIdx.x * kSolveRows + (threadIdx.x >> 5);
@@ -692,6 +704,7 @@ __global__ void __launch_bounds__(kThreads)
 k_front_backward_b(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids, const int* __restrict__ dofs,
                    const double* __restrict__ F, const double* __restrict__ xs, double* __restrict__ frhs,
                    double* __restrict__ bpart, unsigned* __restrict__ bcnt) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* xb = reinterpret_cast<double*>(smem_raw);
     const FrontInfo fr = fronts[ids[blockIdx.y]];
@@ -754,6 +767,7 @@ __global__ void __launch_bounds__(kThreads)
 k_front_backward(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                  const int* __restrict__ dofs, const double* __restrict__ F, const double* __restrict__ P,
                  const double* __restrict__ frhs, double* __restrict__ xs) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* w = reinterpret_cast<double*>(smem_raw);
     const FrontInfo fr = fronts[ids[blockIdx.x]];
@@ -853,6 +867,7 @@ k_front_forward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__
                    const int* __restrict__ maps, const int* __restrict__ dofs,
                    const double* __restrict__ F, const double* __restrict__ P, const double* __restrict__ bglob,
                    const double* __restrict__ dscale, int NV, double* __restrict__ frhs) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double ybuf[2][kPanel];
     const unsigned q = cluster_rank();
@@ -946,6 +961,7 @@ __global__ void __launch_bounds__(kThreads)
 k_front_backward_cl(const FrontInfo* __restrict__ fronts, const int* __restrict__ ids,
                     const int* __restrict__ dofs, const double* __restrict__ F, const double* __restrict__ P,
                     const double* __restrict__ frhs, double* __restrict__ xs) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kChunk = 8;                               // own earlier panels per reduction round
     __shared__ double xbuf[2][kPanel];
@@ -1033,6 +1049,7 @@ __global__ void k_csr_residual(int nrows, const int* __restrict__ rowptr, const 
                                const double* __restrict__ val, const double* __restrict__ b,
                                const double* __restrict__ x, const double* __restrict__ dscale, int pin,
                                double* __restrict__ r) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows) return;
     double acc = b[i];
@@ -1043,6 +1060,7 @@ __global__ void k_csr_residual(int nrows, const int* __restrict__ rowptr, const 
 
 __global__ void k_unscale(int n, const double* __restrict__ xs, const double* __restrict__ dscale,
                           double* __restrict__ x, int accumulate) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v = xs[i] * dscale[i];
@@ -1081,12 +1099,28 @@ LevelPlan plan_level(const Tables& t, int h) {
 
 }  // namespace
 
+// Launch with programmatic stream serialization (see pdl_begin).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, void* stream, Prof& P) {
     cudaStream_t st = (cudaStream_t)stream;
     const int nd = 2 * t.NV;
     if (nd == 0) return 0;
     double* dscale = (double*)(ws + L.dscale);
-    MRCM_LAUNCH(P, "k_assemble_csr", st, k_assemble_csr<<<(nd + 127) / 128, 128, 0, st>>>(nd, d.rowptr, d.src_lo, d.src_hi, d.rhs_src_lo, d.rhs_src_hi,
+    MRCM_LAUNCH(P, "k_assemble_csr", st, launch_pdl(k_assemble_csr, dim3((nd + 127) / 128), dim3(128), 0, st, nd, d.rowptr, d.src_lo, d.src_hi, d.rhs_src_lo, d.rhs_src_hi,
                                                    d.colidx, (const double*)(ws + L.elem),
                                                    (const double*)(ws + L.elem_b), (double*)(ws + L.csr_val),
                                                    (double*)(ws + L.b_int), dscale, t.has_dirichlet ? 0 : 1));
@@ -1103,14 +1137,14 @@ int launch_assemble_interface(const Tables& t, const DeviceTables& d, const Layo
         int maxT = 1;
         for (int id : t.levels[h]) { int nt = (t.fronts[id].n + kTile - 1) / kTile; maxT = std::max(maxT, nt * (nt + 1) / 2); }
         dim3 ga(maxT, cnt);
-        MRCM_LAUNCH(P, "k_front_assemble", st, k_front_assemble<<<ga, kThreads, 0, st>>>(d.fronts, ids, d.front_inv, d.front_dofs, d.subs,
+        MRCM_LAUNCH(P, "k_front_assemble", st, launch_pdl(k_front_assemble, dim3(ga), dim3(kThreads), 0, st, d.fronts, ids, d.front_inv, d.front_dofs, d.subs,
                                                   (const double*)(ws + L.elem), dscale, t.NV, F, Pv, status));
         LevelPlan p = plan_level(t, (int)h);
         for (int s = 0; s < p.steps; ++s) {
             dim3 gp(p.row_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_panel", st, k_ldl_panel<<<gp, 128, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, oz, oz_exp));
+            MRCM_LAUNCH(P, "k_ldl_panel", st, launch_pdl(k_ldl_panel, dim3(gp), dim3(128), 0, st, d.fronts, ids, s * kPanel, F, Pv, oz, oz_exp));
             dim3 gu(p.upd_tiles[s], cnt);
-            MRCM_LAUNCH(P, "k_ldl_update", st, k_ldl_update<<<gu, kThreads, 0, st>>>(d.fronts, ids, s * kPanel, F, Pv, status,
+            MRCM_LAUNCH(P, "k_ldl_update", st, launch_pdl(k_ldl_update, dim3(gu), dim3(kThreads), 0, st, d.fronts, ids, s * kPanel, F, Pv, status,
                                                                                    oz, oz_exp));
         }
     }
@@ -1125,13 +1159,15 @@ static void launch_cluster(void (*kern)(Args...), int fronts, size_t smem, cudaS
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = kSolveCl;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -1154,23 +1190,23 @@ static void multifrontal_solve(const Tables& t, const DeviceTables& d, const Lay
                                                                  (const int*)d.front_maps, (const int*)d.front_dofs, (const double*)F,
                                                                  Pv, rhs, dscale, (int)t.NV, frhs));
         else
-            MRCM_LAUNCH(P, "k_front_forward", st, k_front_forward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_maps,
+            MRCM_LAUNCH(P, "k_front_forward", st, launch_pdl(k_front_forward, dim3(cnt), dim3(kThreads), sm, st, d.fronts, ids, d.front_maps,
                                                       d.front_dofs, F, Pv, rhs, dscale, t.NV, frhs));
-        MRCM_LAUNCH(P, "k_front_forward_b", st, k_front_forward_b<<<dim3(p.fwd_rows, cnt), kThreads, 0, st>>>(d.fronts, ids, F, frhs));
+        MRCM_LAUNCH(P, "k_front_forward_b", st, launch_pdl(k_front_forward_b, dim3(p.fwd_rows, cnt), dim3(kThreads), 0, st, d.fronts, ids, F, frhs));
     }
     for (size_t h = t.levels.size() - 1; h >= 1; --h) {
         int cnt = (int)t.levels[h].size();
         if (!cnt) continue;
         const int* ids = d.level_ids + d.level_off[h];
         const LevelPlan p = plan_level(t, (int)h);
-        MRCM_LAUNCH(P, "k_front_backward_b", st, k_front_backward_b<<<dim3(p.bwd_cols, cnt, bwd_split(p.max_nb)), kThreads, sm, st>>>(
+        MRCM_LAUNCH(P, "k_front_backward_b", st, launch_pdl(k_front_backward_b, dim3(p.bwd_cols, cnt, bwd_split(p.max_nb)), dim3(kThreads), sm, st, 
                                                         d.fronts, ids, d.front_dofs, F, xs, frhs, bpart, bcnt));
         if (p.max_ne >= kSolveClMinNe && p.cl_smem <= kClSmemMax)
             MRCM_LAUNCH(P, "k_front_backward", st, launch_cluster(k_front_backward_cl, cnt, p.cl_smem, st, (const FrontInfo*)d.fronts, ids,
                                                                   (const int*)d.front_dofs, (const double*)F, Pv,
                                                                   (const double*)frhs, xs));
         else
-            MRCM_LAUNCH(P, "k_front_backward", st, k_front_backward<<<cnt, kThreads, sm, st>>>(d.fronts, ids, d.front_dofs, F, Pv,
+            MRCM_LAUNCH(P, "k_front_backward", st, launch_pdl(k_front_backward, dim3(cnt), dim3(kThreads), sm, st, d.fronts, ids, d.front_dofs, F, Pv,
                                                        frhs, xs));
     }
 }
@@ -1207,13 +1243,13 @@ int launch_solve_interface(const Tables& t, const DeviceTables& d, const Layout&
         cudaMemsetAsync(ws + L.bcnt, 0, cnts * sizeof(unsigned), st);
     }
     multifrontal_solve(t, d, L, ws, b, xs, st, P);
-    MRCM_LAUNCH(P, "k_unscale", st, k_unscale<<<(nd + 255) / 256, 256, 0, st>>>(nd, xs, dscale, X, 0));
+    MRCM_LAUNCH(P, "k_unscale", st, launch_pdl(k_unscale, dim3((nd + 255) / 256), dim3(256), 0, st, nd, xs, dscale, X, 0));
     const int refine = t.cfg.interface_refine == 0 ? 1 : std::max(0, t.cfg.interface_refine);
     for (int it = 0; it < refine; ++it) {
-        MRCM_LAUNCH(P, "k_csr_residual", st, k_csr_residual<<<(nd + 127) / 128, 128, 0, st>>>(nd, d.rowptr, d.colidx, (const double*)(ws + L.csr_val),
+        MRCM_LAUNCH(P, "k_csr_residual", st, launch_pdl(k_csr_residual, dim3((nd + 127) / 128), dim3(128), 0, st, nd, d.rowptr, d.colidx, (const double*)(ws + L.csr_val),
                                                        b, X, dscale, pin, r));
         multifrontal_solve(t, d, L, ws, r, xs, st, P);
-        MRCM_LAUNCH(P, "k_unscale", st, k_unscale<<<(nd + 255) / 256, 256, 0, st>>>(nd, xs, dscale, X, 1));
+        MRCM_LAUNCH(P, "k_unscale", st, launch_pdl(k_unscale, dim3((nd + 255) / 256), dim3(256), 0, st, nd, xs, dscale, X, 1));
     }
     return (int)cudaGetLastError();
 }
