@@ -783,7 +783,7 @@ def main():
                    "interface_unknowns": s.n_interface, "precision": args.precision,
                    "execution": "CUDA graph of the five device calls, replayed per step",
                    "autotuned_variants": s.tuning(),
-                   "autotune_ms": dict(zip(("first_solve", "sweeps"), s.tuning_times())),
+                   "autotune": s.tuning_times(),
                    "ir_sweeps": args.ir_sweeps if args.precision != "fp64" else 0,
                    "interface_refine_steps": max(0, bs["interface_refine"]) if bs["interface_refine"] else 1,
                    "ir_tol": args.ir_tol if args.precision != "fp64" else None,

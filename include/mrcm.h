@@ -304,9 +304,11 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
 /* Median times (ms) of every local-solve variant in the last mrcm_autotune
  * of this handle (host only): solve_ms[v] the first solve, sweep_ms[v] the
  * cfg.ir_max_sweeps refinement sweeps (-1 where not timed: FP64 handles time
- * no sweeps).  Writes min(*n, cap) entries of each non-NULL array; *n = the
- * number of variants (0 before any autotune). */
-mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int cap, int* n);
+ * no sweeps), and the resident CTAs per SM of each (solve_ctas[v],
+ * sweep_ctas[v]).  Writes min(*n, cap) entries of each non-NULL array; *n =
+ * the number of variants (0 before any autotune). */
+mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int* solve_ctas,
+                                   int* sweep_ctas, int cap, int* n);
 
 /* The kernel variants the handle uses (host only; after mrcm_autotune or a
  * tune-cache hit, else the defaults): local solve first pass and refinement

@@ -455,12 +455,15 @@ mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* swe
     return MRCM_OK;
 }
 
-mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int cap, int* n) {
+mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int* solve_ctas,
+                                   int* sweep_ctas, int cap, int* n) {
     if (!h || cap < 0) return MRCM_ERR_INVALID_ARG;
     if (n) *n = h->tune_n;
     for (int v = 0; v < h->tune_n && v < cap; ++v) {
         if (solve_ms) solve_ms[v] = h->tune_ms[2 * v];
         if (sweep_ms) sweep_ms[v] = h->tune_ms[2 * v + 1];
+        if (solve_ctas) solve_ctas[v] = h->d.solve_occ[v];
+        if (sweep_ctas) sweep_ctas[v] = h->d.sweep_occ[v];
     }
     return MRCM_OK;
 }

@@ -214,12 +214,16 @@ class MRCM:
         return dict(zip(("solve", "sweep", "factor_small", "factor_mid"), (x.value for x in v)))
 
     def tuning_times(self):
-        """(solve_ms, sweep_ms): per-variant median times of the last autotune (-1 = not timed)."""
+        """{'first_solve', 'sweeps'}: per-variant median times (ms) of the last autotune (-1 = not
+        timed), {'first_solve_ctas', 'sweeps_ctas'}: resident CTAs per SM of each variant."""
         cap = 16
-        a, b, n = (C.c_float * cap)(), (C.c_float * cap)(), C.c_int()
-        L.check(self.lib.mrcm_read_tuning_times(self.handle, a, b, cap, C.byref(n)), self.handle)
+        a, b = (C.c_float * cap)(), (C.c_float * cap)()
+        oa, ob, n = (C.c_int * cap)(), (C.c_int * cap)(), C.c_int()
+        L.check(self.lib.mrcm_read_tuning_times(self.handle, a, b, oa, ob, cap, C.byref(n)), self.handle)
         k = min(cap, n.value)
-        return [round(float(a[i]), 4) for i in range(k)], [round(float(b[i]), 4) for i in range(k)]
+        return {"first_solve": [round(float(a[i]), 4) for i in range(k)],
+                "sweeps": [round(float(b[i]), 4) for i in range(k)],
+                "first_solve_ctas": [int(oa[i]) for i in range(k)], "sweeps_ctas": [int(ob[i]) for i in range(k)]}
 
     def autotune(self, f, stream=None):
         """Pick the fastest local-solve kernel variants for this problem (after factor_local)."""
