@@ -1192,6 +1192,8 @@ struct LocalArgs {
     int bar_off;          // shared-memory offset of the two mbarriers (after the largest layout)
     int last_only;        // solve only the last (particular) column of every subdomain
     const int* nlist_dev; // when set: the list holds min(nlist, *nlist_dev) subdomains (written by an earlier kernel)
+    int col_groups;       // > 1: up to this many CTAs share a subdomain, each taking the columns j = grp mod G
+                          // (G = min(col_groups, grid / subdomains)); 1: one CTA per subdomain
 };
 
 
@@ -1222,7 +1224,7 @@ struct WPipe {
 };
 
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
-__device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restrict__ Wall, int l,
+__device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restrict__ Wall, int l, int grp, int G,
                                           unsigned char* smem_raw, WPipe& pipe) {
     constexpr int NY = NT / 32;
     const SubInfo s = g.subs[l];
@@ -1261,7 +1263,8 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
         int base = 0;
         for (int j0 = 0; j0 < m; j0 += 32) {
             const int j = j0 + threadIdx.x;
-            const bool act = j < m && (!g.last_only || j == m - 1) && (!kSweep || conv[j] == 0);
+            const bool act = j < m && (!g.last_only || j == m - 1) && (!kSweep || conv[j] == 0) &&
+                             (G == 1 || j % G == grp);
             const unsigned bal = __ballot_sync(0xffffffffu, act);
             if (act) cols[base + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
             base += __popc(bal);
@@ -1519,13 +1522,14 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
     pipe.pending[0] = pipe.pending[1] = 0;
     pipe.abort = 0;
     const int nlist = g.nlist_dev ? min(g.nlist, *g.nlist_dev) : g.nlist;
+    const int G = g.col_groups <= 1 || nlist <= 0 ? 1 : max(1, min(g.col_groups, (int)gridDim.x / nlist));
     for (;;) {
         if (threadIdx.x == 0) item = atomicAdd(g.queue, 1);
         __syncthreads();
         const int it = item;
         __syncthreads();
-        if (it >= nlist || pipe.abort) break;
-        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it], smem_raw, pipe);
+        if (it >= nlist * G || pipe.abort) break;
+        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it / G], it % G, G, smem_raw, pipe);
     }
     drain_pipe(pipe, bar);
 }
@@ -2080,6 +2084,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.bar_off = (int)d.solve_smem - 16;
     g.last_only = 0;
     g.nlist_dev = nullptr;
+    g.col_groups = 1;
     return g;
 }
 
@@ -2099,6 +2104,8 @@ static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs&
 
 // FP64 fallback of one wave (see k_fb_collect): slots, FP64 block factors of
 // the slots, FP64 solve of all their columns (replacing the mixed ones).
+constexpr int kFbGroups = 4;
+
 static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const LocalArgs& g0,
                             int cap, long long wstride_slot, long long ystride_slot, cudaStream_t st, Prof& P) {
     int* status = (int*)(ws + L.status);
@@ -2121,7 +2128,10 @@ static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout
     g.last_only = 0;
     g.bar_off = (int)d.f64_solve_smem - 16;
     g.count_unconverged = 0;
-    const int grid = std::max(1, std::min(cap, d.sms * d.f64_occ));
+    // a few fallback subdomains would leave most SMs idle on a long FP64 chain: up to
+    // kFbGroups CTAs share each one, split by columns
+    g.col_groups = kFbGroups;
+    const int grid = std::max(1, std::min(cap * kFbGroups, d.sms * d.f64_occ));
     const void* Wfb = (const void*)(ws + L.fb_W);
     void* args[] = {(void*)&g, (void*)&Wfb};
     // the FP64 form's solve: direct solve through the FP64 block inverses, then one FP64 refinement step
