@@ -290,6 +290,19 @@ enum { MRCM_SOLVE_GRAPH = 1 };
 mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
                        double* mass_residual_max, void* ws, size_t ws_bytes, void* stream, int flags);
 
+/* mrcm_solve with HOST buffers (same layouts): K and f are copied to device
+ * staging buffers (allocated by the first call, 11 n_cells + 2 N_V + 1
+ * doubles, freed by mrcm_destroy), the solve runs, and X, p, u and
+ * mass_residual_max (may be NULL) are copied back, all ordered on `stream`
+ * (required, not NULL; the larger copies are split with a library-owned side
+ * stream so that two copies run at once).  The results are in the host
+ * buffers once `stream` has completed.  With MRCM_SOLVE_GRAPH copies and solve
+ * are captured into one CUDA graph (host buffers must then be page-locked)
+ * and replayed by later calls with the same pointers, workspace size and
+ * stream. */
+mrcm_status mrcm_solve_host(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                            double* mass_residual_max, void* ws, size_t ws_bytes, void* stream, int flags);
+
 /* Autotuner (run after mrcm_factor_local): times every variant of the local
  * solve kernels (128, 256 or 512 threads per CTA x SIMT block products with
  * 1, 2 or 4 rows per thread, 2 adjacent rows per thread (even blocks) or

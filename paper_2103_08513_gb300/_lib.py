@@ -76,6 +76,7 @@ SIGNATURES = {
     "mrcm_read_work": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "mrcm_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t]),
     "mrcm_solve": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7 + [C.c_size_t, C.c_void_p, C.c_int]),
+    "mrcm_solve_host": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7 + [C.c_size_t, C.c_void_p, C.c_int]),
     "mrcm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_query_tuning": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 4),
     "mrcm_read_tuning_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),

@@ -545,6 +545,99 @@ mrcm_status mrcm_solve(mrcm_handle* h, const double* K, const double* f, double*
     return MRCM_OK;
 }
 
+// Host-buffer solve: inputs copied in (K in two halves, one on a side stream
+// with f), the solve, outputs copied out (u in two halves, p on the side
+// stream); graph mode captures copies and solve into one CUDA graph.
+static mrcm_status host_body(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                             double* mres, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const size_t nc = (size_t)h->t.n_cells, nx = (size_t)std::max(2 * h->t.NV, 1);
+    double* dK = h->io;
+    double* df = dK + 3 * nc;
+    double* dX = df + nc;
+    double* dp = dX + nx;
+    double* du = dp + nc;
+    double* dm = du + 6 * nc;
+    cudaStream_t sd = h->io_side;
+    const size_t kh = (3 * nc) / 2, uh = (6 * nc) / 2;
+    cudaEventRecord(h->io_ev[0], st);
+    cudaStreamWaitEvent(sd, h->io_ev[0], 0);
+    cudaMemcpyAsync(dK, K, kh * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dK + kh, K + kh, (3 * nc - kh) * sizeof(double), cudaMemcpyHostToDevice, sd);
+    cudaMemcpyAsync(df, f, nc * sizeof(double), cudaMemcpyHostToDevice, sd);
+    cudaEventRecord(h->io_ev[1], sd);
+    cudaStreamWaitEvent(st, h->io_ev[1], 0);
+    mrcm_status rs = run_all(h, dK, df, dX, dp, du, dm, ws, ws_bytes, st);
+    if (rs != MRCM_OK) return rs;
+    cudaEventRecord(h->io_ev[0], st);
+    cudaStreamWaitEvent(sd, h->io_ev[0], 0);
+    cudaMemcpyAsync(u, du, uh * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(u + uh, du + uh, (6 * nc - uh) * sizeof(double), cudaMemcpyDeviceToHost, sd);
+    cudaMemcpyAsync(p, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, sd);
+    cudaMemcpyAsync(X, dX, 2 * (size_t)h->t.NV * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (mres) cudaMemcpyAsync(mres, dm, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(h->io_ev[1], sd);
+    cudaStreamWaitEvent(st, h->io_ev[1], 0);
+    return MRCM_OK;
+}
+
+mrcm_status mrcm_solve_host(mrcm_handle* h, const double* K, const double* f, double* X, double* p, double* u,
+                            double* mres, void* ws, size_t ws_bytes, void* stream, int flags) {
+    if (!h) return MRCM_ERR_INVALID_ARG;
+    mrcm_status st = check_ws(h, ws);
+    if (st != MRCM_OK) return st;
+    if (!K || !f || !X || !p || !u) return fail(h, MRCM_ERR_INVALID_ARG, "K, f, X, p and u must be non-NULL");
+    if (!stream) return fail(h, MRCM_ERR_INVALID_ARG, "the host-buffer solve needs a non-default stream");
+    if (ws_bytes < h->lay.total) return fail(h, MRCM_ERR_OOM, "workspace smaller than mrcm_query_workspace");
+    if ((st = ensure_device(h, stream)) != MRCM_OK) return st;
+    cudaError_t e;
+    if (!h->io) {
+        const size_t nc = (size_t)h->t.n_cells, nx = (size_t)std::max(2 * h->t.NV, 1);
+        h->io_bytes = (11 * nc + nx + 1) * sizeof(double);
+        if ((e = cudaMalloc(&h->io, h->io_bytes)) != cudaSuccess) { h->io = nullptr; return cuda_fail(h, e, "cudaMalloc (staging)"); }
+        if ((e = cudaStreamCreateWithFlags(&h->io_side, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+        for (auto& ev : h->io_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & MRCM_SOLVE_GRAPH)) {
+        st = host_body(h, K, f, X, p, u, mres, ws, ws_bytes, s);
+        if (st != MRCM_OK) return st;
+        e = cudaGetLastError();
+        return e == cudaSuccess ? MRCM_OK : cuda_fail(h, e, "mrcm_solve_host");
+    }
+    const void* key[10] = {K, f, X, p, u, mres, ws, stream, (const void*)(size_t)ws_bytes, (const void*)1};
+    bool same = h->hgraph_exec != nullptr;
+    for (int i = 0; i < 10 && same; ++i) same = key[i] == h->hgraph_key[i];
+    if (!same) {
+        if (h->hgraph_exec) cudaGraphExecDestroy(h->hgraph_exec);
+        if (h->hgraph) cudaGraphDestroy(h->hgraph);
+        h->hgraph_exec = nullptr;
+        h->hgraph = nullptr;
+        const bool prof = h->prof.on;
+        h->prof.on = false;
+        const long long n0 = h->prof.launches;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { h->prof.on = prof; return cuda_fail(h, e, "cudaStreamBeginCapture"); }
+        mrcm_status rs = host_body(h, K, f, X, p, u, mres, ws, ws_bytes, s);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        h->prof.on = prof;
+        h->hgraph_launches = h->prof.launches - n0;
+        h->prof.launches = n0;
+        if (rs != MRCM_OK) { if (g) cudaGraphDestroy(g); return rs; }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture (host buffers must be pinned)");
+        h->hgraph = g;
+        e = cudaGraphInstantiate(&h->hgraph_exec, g, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); h->hgraph = nullptr; h->hgraph_exec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+        for (int i = 0; i < 10; ++i) h->hgraph_key[i] = key[i];
+    }
+    e = cudaGraphLaunch(h->hgraph_exec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    h->prof.launches += h->hgraph_launches;
+    h->stage = 4;
+    return MRCM_OK;
+}
+
 mrcm_status mrcm_profile(mrcm_handle* h, int enable) {
     if (!h) return MRCM_ERR_INVALID_ARG;
     h->prof.reset();
@@ -590,6 +683,11 @@ void mrcm_destroy(mrcm_handle* h) {
     if (!h) return;
     h->prof.release();
     drop_graph(h);
+    if (h->hgraph_exec) cudaGraphExecDestroy(h->hgraph_exec);
+    if (h->hgraph) cudaGraphDestroy(h->hgraph);
+    if (h->io) cudaFree(h->io);
+    if (h->io_side) cudaStreamDestroy(h->io_side);
+    for (auto ev : h->io_ev) if (ev) cudaEventDestroy(ev);
     if (h->samp_off) cudaFree(h->samp_off);
     if (h->samp_list) cudaFree(h->samp_list);
     if (h->col_list) cudaFree(h->col_list);

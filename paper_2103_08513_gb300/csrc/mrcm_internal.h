@@ -307,6 +307,15 @@ struct mrcm_handle {
     cudaGraphExec_t graph_exec = nullptr;
     const void* graph_key[9] = {};
     long long graph_launches = 0;
+    // host-buffer solve (mrcm_solve_host): device staging, a side stream for parallel copies, its graph
+    double* io = nullptr;
+    size_t io_bytes = 0;
+    cudaStream_t io_side = nullptr;
+    cudaEvent_t io_ev[2] = {nullptr, nullptr};
+    cudaGraph_t hgraph = nullptr;
+    cudaGraphExec_t hgraph_exec = nullptr;
+    const void* hgraph_key[10] = {};
+    long long hgraph_launches = 0;
     float tune_ms[2 * mrcm::kMaxSolveVariants] = {};   // last autotune: first solve / sweeps per variant
     int tune_n = 0;                                    // variants timed (0: no autotune yet)
     int* col_list = nullptr;              // learned-path (subdomain, column) list of every MBF column

@@ -207,6 +207,16 @@ class MRCM:
             self.reconstruct(X, p, u, mres, stream=stream)
         return p, u, X, mres
 
+    def solve_host(self, K, f, X, p, u, mres=None, stream=None, graph=False):
+        """mrcm_solve with host (CPU) tensors: K, f in; X, p, u (and mres) out, written
+        once `stream` completes.  graph=True needs page-locked tensors."""
+        for t in (K, f, X, p, u) + ((mres,) if mres is not None else ()):
+            assert not t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        L.check(self.lib.mrcm_solve_host(self.handle, _ptr(K), _ptr(f), _ptr(X), _ptr(p), _ptr(u),
+                                         _ptr(mres) if mres is not None else None, self.ws_ptr,
+                                         C.c_size_t(self.ws_bytes), _stream(stream), 1 if graph else 0), self.handle)
+        return p, u, X, mres
+
     def tuning(self):
         """{'solve', 'sweep', 'factor_small', 'factor_mid'}: the kernel variants in use."""
         v = [C.c_int() for _ in range(4)]
