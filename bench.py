@@ -726,10 +726,11 @@ def main():
     ranked = sorted(kprof.items(), key=lambda kv: -kv[1][1])
     wkey = args.workload if args.precision == "fp32_ir" else None
     roof = roofline(ranked[0][0], ranked[0][1][1], ranked[0][1][0], args.steps, sizes, swept, args.precision, peaks,
-                    wkey, sweeps=ranked[0][1][0] / args.steps)
+                    wkey, sweeps=status["sweeps"] if ranked[0][0] == "k_ir_sweep" else ranked[0][1][0] / args.steps)
     if ranked[0][0] == "k_ir_sweep":
         roof["fp64_view"] = fp64_view(ranked[0][1][1], args.steps, swept, peaks)
-    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks, wkey, sweeps=v[0] / args.steps)
+    others = [roofline(k, v[1], v[0], args.steps, sizes, swept, args.precision, peaks, wkey,
+                       sweeps=status["sweeps"] if k == "k_ir_sweep" else v[0] / args.steps)
               for k, v in ranked[1:4]]
     # the paper's local solver as the algorithmic work: sparse LDL^T (minimum degree) + one solve of
     # every column, against the time the local stage takes here (factor, first solve, sweeps, fallback)

@@ -1194,6 +1194,7 @@ struct LocalArgs {
     const int* nlist_dev; // when set: the list holds min(nlist, *nlist_dev) subdomains (written by an earlier kernel)
     int col_groups;       // > 1: up to this many CTAs share a subdomain, each taking the columns j = grp mod G
                           // (G = min(col_groups, grid / subdomains)); 1: one CTA per subdomain
+    int passes;           // refinement sweeps run back to back on each subdomain by one launch (sweeps only)
 };
 
 
@@ -1225,7 +1226,7 @@ struct WPipe {
 
 template <typename T, bool kScaled, bool kSweep, int NT, int RT>
 __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restrict__ Wall, int l, int grp, int G,
-                                          unsigned char* smem_raw, WPipe& pipe) {
+                                          bool count_unconverged, unsigned char* smem_raw, WPipe& pipe) {
     constexpr int NY = NT / 32;
     const SubInfo s = g.subs[l];
     const int b = s.b, m = s.m, N = s.N, su = s.su, nI = s.nI, mpad = g.mpad;
@@ -1485,7 +1486,7 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             else atomicAdd(&nbad, 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && nbad && g.count_unconverged) atomicAdd(&g.status[ST_UNCONVERGED], nbad);
+        if (threadIdx.x == 0 && nbad && count_unconverged) atomicAdd(&g.status[ST_UNCONVERGED], nbad);
     } else {
         for (int jj = threadIdx.x; jj < na; jj += blockDim.x) {
             const int j = cols[jj];
@@ -1529,7 +1530,12 @@ k_local_solve(LocalArgs g, const T* __restrict__ Wall) {
         const int it = item;
         __syncthreads();
         if (it >= nlist * G || pipe.abort) break;
-        solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it / G], it % G, G, smem_raw, pipe);
+        // sweeps: g.passes passes on this subdomain back to back (the columns retired by one
+        // pass, written to conv[] before the pass's last barrier, drop out of the next)
+        const int np = kSweep ? max(1, g.passes) : 1;
+        for (int ps = 0; ps < np && !pipe.abort; ++ps)
+            solve_one<T, kScaled, kSweep, NT, RT>(g, Wall, g.list[it / G], it % G, G,
+                                                  g.count_unconverged && ps + 1 == np, smem_raw, pipe);
     }
     drain_pipe(pipe, bar);
 }
@@ -2085,6 +2091,7 @@ static LocalArgs local_args(const Tables& t, const DeviceTables& d, const Layout
     g.last_only = 0;
     g.nlist_dev = nullptr;
     g.col_groups = 1;
+    g.passes = 1;
     return g;
 }
 
@@ -2105,6 +2112,7 @@ static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs&
 // FP64 fallback of one wave (see k_fb_collect): slots, FP64 block factors of
 // the slots, FP64 solve of all their columns (replacing the mixed ones).
 constexpr int kFbGroups = 4;
+constexpr int kSeparateSweeps = 2;
 
 static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const LocalArgs& g0,
                             int cap, long long wstride_slot, long long ystride_slot, cudaStream_t st, Prof& P) {
@@ -2165,10 +2173,16 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
         g.count_unconverged = 0;
         launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
         if (precision != MRCM_FP64) {
-            for (int it = 0; it < sweeps; ++it) {
-                g.count_unconverged = it + 1 == sweeps && fb_cap == 0 ? 1 : 0;
+            // the first kSeparateSweeps sweeps touch nearly every column: one launch each; the
+            // later ones touch few subdomains, which run all their remaining sweeps in one launch
+            for (int it = 0; it < sweeps;) {
+                const int np = it < kSeparateSweeps ? 1 : sweeps - it;
+                g.passes = np;
+                g.count_unconverged = it + np == sweeps && fb_cap == 0 ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+                it += np;
             }
+            g.passes = 1;
             if (fb_cap > 0) launch_fallback(t, d, L, ws, g, fb_cap, fb_stride, fb_ystride, st, P);
         } else {
             // FP64 form: the direct solve through the explicit block inverses plus one
