@@ -316,12 +316,17 @@ mrcm_status mrcm_autotune(mrcm_handle* h, const double* f, void* ws, void* strea
 
 /* Median times (ms) of every local-solve variant in the last mrcm_autotune
  * of this handle (host only): solve_ms[v] the first solve, sweep_ms[v] the
- * cfg.ir_max_sweeps refinement sweeps (-1 where not timed: FP64 handles time
- * no sweeps), and the resident CTAs per SM of each (solve_ctas[v],
- * sweep_ctas[v]).  Writes min(*n, cap) entries of each non-NULL array; *n =
- * the number of variants (0 before any autotune). */
+ * cfg.ir_max_sweeps refinement sweeps in one launch (-1 where not timed: FP64
+ * handles time no sweeps), and the resident CTAs per SM of each
+ * (solve_ctas[v], sweep_ctas[v]).  Writes min(*n, cap) entries of each
+ * non-NULL array; *n = the number of variants (0 before any autotune).
+ * *sweeps_separate = 1 when the handle runs one launch per sweep (the
+ * autotuner measured that faster than one launch for all sweeps), and
+ * *sweeps_separate_ms that time for the chosen sweep variant (-1: not timed).
+ * Any output pointer may be NULL. */
 mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int* solve_ctas,
-                                   int* sweep_ctas, int cap, int* n);
+                                   int* sweep_ctas, int cap, int* n, int* sweeps_separate,
+                                   float* sweeps_separate_ms);
 
 /* The kernel variants the handle uses (host only; after mrcm_autotune or a
  * tune-cache hit, else the defaults): local solve first pass and refinement

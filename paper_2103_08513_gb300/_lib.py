@@ -80,7 +80,8 @@ SIGNATURES = {
     "mrcm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrcm_query_tuning": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 4),
     "mrcm_read_tuning_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
-                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "mrcm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mrcm_profile_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_longlong)]),
     "mrcm_box_solve_noalloc": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]

@@ -104,21 +104,25 @@ std::string tune_key(const mrcm_handle* h) {
     return buf;
 }
 
-// Tune cache: text lines "key solve_variant sweep_variant factor_variant factor_mid_variant".
+// Tune cache: text lines "key solve_variant sweep_variant factor_variant factor_mid_variant
+// [sweeps_separate]" (the last field is optional: 0 when absent).
 void load_tune_cache(mrcm_handle* h) {
     if (h->t.tune_cache.empty()) return;
     FILE* fp = fopen(h->t.tune_cache.c_str(), "r");
     if (!fp) return;
-    char key[256];
-    int v0, v1, v2, v3;
+    char line[512], key[256];
     const std::string want = tune_key(h);
-    while (fscanf(fp, "%255s %d %d %d %d", key, &v0, &v1, &v2, &v3) == 5) {
+    while (fgets(line, sizeof(line), fp)) {
+        int v0, v1, v2, v3, v4 = 0;
+        const int n = sscanf(line, "%255s %d %d %d %d %d", key, &v0, &v1, &v2, &v3, &v4);
+        if (n < 5) continue;
         if (want == key && v0 >= 0 && v0 < mrcm::kMaxSolveVariants && v1 >= 0 && v1 < mrcm::kMaxSolveVariants &&
-            v2 >= 0 && v2 < mrcm::kNumFactorVariants && (v3 == 0 || v3 == 1)) {
+            v2 >= 0 && v2 < mrcm::kNumFactorVariants && (v3 == 0 || v3 == 1) && (v4 == 0 || v4 == 1)) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
             h->d.factor_variant = v2;
             h->d.factor_mid_variant = v3;
+            h->d.sweeps_separate = v4;
         }
     }
     fclose(fp);
@@ -129,18 +133,20 @@ void store_tune_cache(mrcm_handle* h) {
     std::vector<std::string> keep;
     const std::string want = tune_key(h);
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "r")) {
-        char key[256];
-        int v0, v1, v2, v3;
-        while (fscanf(fp, "%255s %d %d %d %d", key, &v0, &v1, &v2, &v3) == 5)
-            if (want != key)
-                keep.push_back(std::string(key) + " " + std::to_string(v0) + " " + std::to_string(v1) + " " +
-                               std::to_string(v2) + " " + std::to_string(v3));
+        char line[512], key[256];
+        while (fgets(line, sizeof(line), fp)) {
+            int v[5] = {0, 0, 0, 0, 0};
+            const int n = sscanf(line, "%255s %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4]);
+            if (n >= 5 && want != key)
+                keep.push_back(std::string(key) + " " + std::to_string(v[0]) + " " + std::to_string(v[1]) + " " +
+                               std::to_string(v[2]) + " " + std::to_string(v[3]) + " " + std::to_string(v[4]));
+        }
         fclose(fp);
     }
     if (FILE* fp = fopen(h->t.tune_cache.c_str(), "w")) {
         for (auto& line : keep) fprintf(fp, "%s\n", line.c_str());
-        fprintf(fp, "%s %d %d %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant, h->d.factor_variant,
-                h->d.factor_mid_variant);
+        fprintf(fp, "%s %d %d %d %d %d\n", want.c_str(), h->d.solve_variant, h->d.sweep_variant, h->d.factor_variant,
+                h->d.factor_mid_variant, h->d.sweeps_separate);
         fclose(fp);
     }
 }
@@ -456,9 +462,11 @@ mrcm_status mrcm_query_tuning(const mrcm_handle* h, int* solve_variant, int* swe
 }
 
 mrcm_status mrcm_read_tuning_times(const mrcm_handle* h, float* solve_ms, float* sweep_ms, int* solve_ctas,
-                                   int* sweep_ctas, int cap, int* n) {
+                                   int* sweep_ctas, int cap, int* n, int* sweeps_separate, float* sweeps_separate_ms) {
     if (!h || cap < 0) return MRCM_ERR_INVALID_ARG;
     if (n) *n = h->tune_n;
+    if (sweeps_separate) *sweeps_separate = h->d.sweeps_separate;
+    if (sweeps_separate_ms) *sweeps_separate_ms = h->d.sweeps_separate_ms;
     for (int v = 0; v < h->tune_n && v < cap; ++v) {
         if (solve_ms) solve_ms[v] = h->tune_ms[2 * v];
         if (sweep_ms) sweep_ms[v] = h->tune_ms[2 * v + 1];

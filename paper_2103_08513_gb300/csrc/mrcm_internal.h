@@ -158,6 +158,9 @@ struct DeviceTables {
     int solve_occ[kMaxSolveVariants] = {};
     int sweep_occ[kMaxSolveVariants] = {};
     int solve_variant = 0, sweep_variant = 0;  // chosen by the autotuner (or the tune cache)
+    int sweeps_separate = 0;                   // 1: one launch per refinement sweep, 0: all sweeps in one
+                                               // launch (autotuner or tune cache; default 0)
+    float sweeps_separate_ms = -1.0f;          // last autotune: the chosen sweep variant, one launch per sweep
     size_t front_smem = 0;
     int* rowptr = nullptr;
     int* colidx = nullptr;

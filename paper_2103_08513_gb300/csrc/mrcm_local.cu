@@ -1651,25 +1651,39 @@ k_element(const SubInfo* __restrict__ subs, const FaceInfo* __restrict__ faces,
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < nI * jn; e += blockDim.x) {
-            const int k = e / jn, jb = e - k * jn, j = j0 + jb;
-            const int q0 = start[k], q1 = start[k + 1];
+        // S consecutive lanes per (basis, column) task when there are few tasks (large
+        // whole-face bases): lane s takes the faces q0 + s + S i, four partial sums each,
+        // combined in a fixed order (partials, then a butterfly over the S lanes)
+        const int tasks = nI * jn;
+        int S = 1;
+        while (S < 32 && 2 * S * tasks <= (int)blockDim.x) S <<= 1;
+        const int sub = threadIdx.x & (S - 1);
+        for (int e0 = 0; e0 < tasks; e0 += blockDim.x / S) {
+            const int e = e0 + threadIdx.x / S;
+            const bool live = e < tasks;
+            const int k = live ? e / jn : 0, jb = live ? e - k * jn : 0, j = j0 + jb;
+            const int q0 = live ? start[k] : 0, q1 = live ? start[k + 1] : 0;
             const double* x = xs + (size_t)jb * nf;
             double pf[4] = {0.0, 0.0, 0.0, 0.0}, pu[4] = {0.0, 0.0, 0.0, 0.0};
-            int q = q0;
-            for (; q + 3 < q1; q += 4) {
+            int q = q0 + sub;
+            for (; q + 3 * S < q1; q += 4 * S) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    pf[u] = fma(s_tr[q + u], x[q + u], pf[u]);
-                    pu[u] = fma(s_bst[q + u], x[q + u], pu[u]);
+                    pf[u] = fma(s_tr[q + u * S], x[q + u * S], pf[u]);
+                    pu[u] = fma(s_bst[q + u * S], x[q + u * S], pu[u]);
                 }
             }
-            for (int u = 0; q < q1; ++q, ++u) {
+            for (int u = 0; q < q1; q += S, ++u) {
                 pf[u] = fma(s_tr[q], x[q], pf[u]);
                 pu[u] = fma(s_bst[q], x[q], pu[u]);
             }
             double sf = (pf[0] + pf[1]) + (pf[2] + pf[3]);
             double su = (pu[0] + pu[1]) + (pu[2] + pu[3]);
+            for (int o = 1; o < S; o <<= 1) {             // the same sum in every lane of the group
+                sf += __shfl_xor_sync(0xffffffffu, sf, o);
+                su += __shfl_xor_sync(0xffffffffu, su, o);
+            }
+            if (!live || sub != 0) continue;
             double sdiag = 0.0;
             if (j == k) { sf -= s_gsum[0][k]; su -= s_gsum[1][k]; }               // g = 1
             else if (j == nI + k) {                                               // g = -beta s
@@ -2112,7 +2126,6 @@ static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs&
 // FP64 fallback of one wave (see k_fb_collect): slots, FP64 block factors of
 // the slots, FP64 solve of all their columns (replacing the mixed ones).
 constexpr int kFbGroups = 4;
-constexpr int kSeparateSweeps = 0;
 
 static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const LocalArgs& g0,
                             int cap, long long wstride_slot, long long ystride_slot, cudaStream_t st, Prof& P) {
@@ -2173,11 +2186,11 @@ int launch_solve_mbf(const Tables& t, const DeviceTables& d, const Layout& L, ch
         g.count_unconverged = 0;
         launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
         if (precision != MRCM_FP64) {
-            // sweeps after the first kSeparateSweeps run in one launch, each subdomain's back to back:
-            // a subdomain that needs more sweeps than most no longer holds up a launch of its own per
-            // sweep (0 measured fastest at C2: 8.60 ms, against 8.68 with 1 and 8.81 with 2)
+            // all sweeps in one launch, each subdomain's back to back (a subdomain that needs more
+            // sweeps than most no longer holds up a launch of its own per sweep), or one launch per
+            // sweep when the autotuner measured that faster (uneven subdomain sizes)
             for (int it = 0; it < sweeps;) {
-                const int np = it < kSeparateSweeps ? 1 : sweeps - it;
+                const int np = d.sweeps_separate ? 1 : sweeps - it;
                 g.passes = np;
                 g.count_unconverged = it + np == sweeps && fb_cap == 0 ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
@@ -2411,7 +2424,7 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
             for (int r = 0; r < reps; ++r) {
                 launch_local_pass(t, d, g, W, false, *best_solve, st, dummy);
                 cudaEventRecord(e0, st);
-                g.passes = t.cfg.ir_max_sweeps;          // as launch_solve_mbf runs them (kSeparateSweeps = 0)
+                g.passes = t.cfg.ir_max_sweeps;          // all sweeps in one launch
                 if (g.passes > 0) launch_local_pass(t, d, g, W, true, v, st, dummy);
                 g.passes = 1;
                 cudaEventRecord(e1, st);
@@ -2424,6 +2437,20 @@ int autotune_local(const Tables& t, DeviceTables& d, const Layout& L, char* ws, 
             if (ms_out) ms_out[2 * v + 1] = m1;
             if (m1 < best1) { best1 = m1; *best_sweep = v; }
         }
+        // the chosen variant with one launch per sweep
+        std::vector<float> t2;
+        for (int r = 0; r < reps && t.cfg.ir_max_sweeps > 0; ++r) {
+            launch_local_pass(t, d, g, W, false, *best_solve, st, dummy);
+            cudaEventRecord(e0, st);
+            for (int it = 0; it < t.cfg.ir_max_sweeps; ++it) launch_local_pass(t, d, g, W, true, *best_sweep, st, dummy);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t2.push_back(ms);
+        }
+        d.sweeps_separate_ms = t2.empty() ? -1.0f : median(t2);
+        d.sweeps_separate = (!t2.empty() && d.sweeps_separate_ms < best1) ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

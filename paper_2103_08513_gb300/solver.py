@@ -229,11 +229,14 @@ class MRCM:
         cap = 16
         a, b = (C.c_float * cap)(), (C.c_float * cap)()
         oa, ob, n = (C.c_int * cap)(), (C.c_int * cap)(), C.c_int()
-        L.check(self.lib.mrcm_read_tuning_times(self.handle, a, b, oa, ob, cap, C.byref(n)), self.handle)
+        sep, sep_ms = C.c_int(), C.c_float()
+        L.check(self.lib.mrcm_read_tuning_times(self.handle, a, b, oa, ob, cap, C.byref(n), C.byref(sep),
+                                                C.byref(sep_ms)), self.handle)
         k = min(cap, n.value)
         return {"first_solve": [round(float(a[i]), 4) for i in range(k)],
                 "sweeps": [round(float(b[i]), 4) for i in range(k)],
-                "first_solve_ctas": [int(oa[i]) for i in range(k)], "sweeps_ctas": [int(ob[i]) for i in range(k)]}
+                "first_solve_ctas": [int(oa[i]) for i in range(k)], "sweeps_ctas": [int(ob[i]) for i in range(k)],
+                "sweeps_one_launch_each": bool(sep.value), "sweeps_one_launch_each_ms": round(float(sep_ms.value), 4)}
 
     def autotune(self, f, stream=None):
         """Pick the fastest local-solve kernel variants for this problem (after factor_local)."""

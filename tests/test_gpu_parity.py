@@ -245,9 +245,11 @@ def test_every_solve_variant_matches_oracle(name, tmp_path):
     s.autotune(f)
     key, _, _, fv, fm = open(cache).read().split()[:5]
     # every solve variant with the tuned factors, then every factor kernel (b <= 64: 3, 64 < b <= 128: 2)
-    for v, fvv, fmv in [(v, fv, fm) for v in range(12)] + [(0, 0, 0), (0, 1, 0), (0, 2, 0), (0, 1, 1)]:
+    # (the last field: 1 = one launch per refinement sweep, 0 = all sweeps in one launch)
+    for v, fvv, fmv, sep in ([(v, fv, fm, 0) for v in range(12)] + [(10, fv, fm, 1), (1, fv, fm, 1)]
+                             + [(0, 0, 0, 0), (0, 1, 0, 0), (0, 2, 0, 0), (0, 1, 1, 0)]):
         with open(cache, "w") as fp:
-            fp.write(f"{key} {v} {v} {fvv} {fmv}\n")
+            fp.write(f"{key} {v} {v} {fvv} {fmv} {sep}\n")
         sv = MRCM(w.n, w.edges, w.patch, precision="fp32_ir", ir_max_sweeps=8, ir_tol=1e-13, tune_cache=cache)
         p, u, X, _ = sv.solve(K, f)
         assert rel_l2(X.cpu().numpy(), r.X) < 1e-8, v
