@@ -193,6 +193,6 @@ BENCH_SETTINGS = {
     "c2": dict(ir_sweeps=5, ir_tol=1e-9, wave_gb=0.0, interface_refine=-1),
     "c2_betaHK": dict(ir_sweeps=5, ir_tol=1e-9, wave_gb=0.0, interface_refine=-1),
     "c3": dict(ir_sweeps=4, ir_tol=1e-9, wave_gb=0.0, interface_refine=-1),
-    "c5": dict(ir_sweeps=6, ir_tol=1e-9, wave_gb=16.0, interface_refine=-1),
+    "c5": dict(ir_sweeps=7, ir_tol=1e-9, wave_gb=16.0, interface_refine=-1),
     "c5_slab": dict(ir_sweeps=6, ir_tol=1e-9, wave_gb=0.0, interface_refine=-1),
 }
