@@ -397,9 +397,10 @@ def variants_sections(make, w, K, dev, stream, fd, u_ms, n_sub):
     out["postprocess_mean_velocity"] = {
         "ms": round(statistics.median(ms), 4), "subdomains_per_s": round(n_sub / (statistics.median(ms) / 1e3), 1),
         "mass_residual_max": float(mres.cpu()[0]), "unconverged": st["unconverged"],
+        "fp64_stage_subdomains": s.read_fallback()[0],
         "what": "Eq. locprob_submean: Gamma faces averaged, Neumann TPFA re-solve of every subdomain "
-                "(FP64 block factors in waves inside the factor region, FP64 solve + 3 refinement steps), "
-                "fine-scale conservative velocity"}
+                "(FP32 block factors + FP32 solve + 10 FP64 refinement sweeps to backward error 1e-13; FP64 block "
+                "factors, solve and 3 refinement steps for the subdomains left above it), fine-scale conservative velocity"}
     del s, up, u
     # --- alpha / Hbar variants (beta = alpha H / K)
     rows = []

@@ -234,8 +234,12 @@ mrcm_status mrcm_reconstruct(mrcm_handle* h, const double* X, double* p, double*
  * re-solves its TPFA problem (Eq. aijk, harmonic means) with Neumann data:
  * Ubar.n on its Gamma faces and u.n on the domain walls.  The pure Neumann
  * matrix is factored and solved like the local problems (cfg.precision;
- * mixed precision: the tied Neumann blocks in FP64, in waves inside the
- * factor region, each solve with three FP64 refinement steps); the
+ * mixed precision: FP32 block factors, the FP32 solve and up to ten FP64
+ * refinement sweeps to a normwise backward error of 1e-13 for every
+ * subdomain, then FP64 block factors, in waves inside the factor region, and
+ * the FP64 solve with three FP64 refinement steps for the subdomains whose
+ * column stayed above it -- their count is what mrcm_read_fallback reports
+ * after this call); the
  * subdomain's pressure constant is fixed internally (it does not affect the
  * velocity).
  *  u      device FP64 [6][nz][ny][nx]: the multiscale velocity as written by

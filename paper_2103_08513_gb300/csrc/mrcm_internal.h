@@ -140,6 +140,7 @@ struct Layout {
     size_t elem, elem_b, csr_val, b_int, dscale, fronts, frhs, panel, oz, oz_exp, xres, xtmp, psum, status;
     size_t bpart, bcnt;    // row-chunk partial sums and counters of the split boundary back substitution
     size_t fb_W, fb_Y, fb_subs, fb_list;   // FP64 fallback: block factors, forward values, subdomain records, slots
+    size_t pp_list;                        // post-processing (mixed): the subdomains its FP32 pass left unconverged
     size_t big;                            // FP64 form: packed triangles of blocks with b > kMaxBlock64 (one wave)
     size_t total;
 };

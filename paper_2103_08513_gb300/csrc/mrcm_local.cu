@@ -1796,7 +1796,9 @@ k_pp_coefficients(const SubInfo* __restrict__ subs, const double* __restrict__ u
 __global__ void __launch_bounds__(kThreads)
 k_pp_scale(const SubInfo* __restrict__ subs, const int* __restrict__ list, const double* __restrict__ coef,
            const double* __restrict__ rhs_part, const double* __restrict__ f, Geo geo, long long nct,
-           const double* __restrict__ X, double* __restrict__ bnorm) {
+           const double* __restrict__ X, double* __restrict__ bnorm,
+           const int* __restrict__ limit /* CTAs from *limit on have no subdomain; may be NULL */) {
+    if (limit && (int)blockIdx.x >= *limit) return;
     const SubInfo s = subs[list[blockIdx.x]];
     const int N = s.N, b = s.b, su = s.su;
     const double* cd = coef + s.cell_off;
@@ -1827,6 +1829,21 @@ k_pp_scale(const SubInfo* __restrict__ subs, const int* __restrict__ list, const
         __syncthreads();
     }
     if (threadIdx.x == 0) bnorm[s.rhs_off + s.m - 1] = fmin(red[0], 1e38);   // read back as FP32
+}
+
+// The subdomains of list[0 .. n) whose particular column did not converge, in
+// any order (each keeps its own slots), and their count.
+__global__ void k_pp_unconverged(const SubInfo* __restrict__ subs, const int* __restrict__ list, int n,
+                                 const int* __restrict__ conv, int* __restrict__ out, int* __restrict__ count,
+                                 int* __restrict__ total) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = list[i];
+    const SubInfo s = subs[l];
+    if (conv[s.rhs_off + s.m - 1] == 0) {
+        out[atomicAdd(count, 1)] = l;
+        atomicAdd(total, 1);
+    }
 }
 
 // Post-processed velocity: TPFA of the Neumann solution (the particular column
@@ -2126,6 +2143,9 @@ static void launch_local_pass(const Tables& t, const DeviceTables& d, LocalArgs&
 // FP64 fallback of one wave (see k_fb_collect): slots, FP64 block factors of
 // the slots, FP64 solve of all their columns (replacing the mixed ones).
 constexpr int kFbGroups = 4;
+constexpr int kPpMixedSweeps = 10;         // FP64 refinement sweeps of the post-processing's FP32 pass
+constexpr double kPpMixedTol = 1e-13;      // and their stop on the backward error: the post-processed
+                                           // velocity must balance mass to about FP64 level
 
 static void launch_fallback(const Tables& t, const DeviceTables& d, const Layout& L, char* ws, const LocalArgs& g0,
                             int cap, long long wstride_slot, long long ystride_slot, cudaStream_t st, Prof& P) {
@@ -2227,6 +2247,8 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
     double* coef = (double*)(ws + L.coef);
     const Geo geo = make_geo(t.cfg);
     MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_UNCONVERGED, 0));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_TOTAL, 0));
+    MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_FB_LOST, 0));
     MRCM_LAUNCH(P, "k_pp_coefficients", st, k_pp_coefficients<<<nsub, kThreads, 0, st>>>(d.subs, u, geo, coef,
                 (double*)(ws + L.scale), (double*)(ws + L.rhs_part), t.n_cells));
     LocalArgs g = local_args(t, d, L, ws, f);
@@ -2241,35 +2263,61 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
             g.count_unconverged = 0;
             launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
             MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<g.nlist, kThreads, 0, st>>>(g.subs, g.list, coef, g.rhs_dir,
-                        f, geo, t.n_cells, g.X, g.bnorm));
+                        f, geo, t.n_cells, g.X, g.bnorm, nullptr));
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps ? 1 : 0;
                 launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
             }
         }
     } else {
-        // the tied Neumann blocks are too ill-conditioned for an FP32 factor: FP64 block
-        // factors in the W region, wave by wave, FP64 solve and refinement of the one column
+        // (1) every subdomain: FP32 block factors of the tied Neumann matrix, the FP32 solve
+        // of the one column and kPpMixedSweeps FP64 refinement sweeps in one launch (stop on
+        // the backward error, kPpMixedTol); most subdomains converge
+        for (int w = 0; w < t.n_waves; ++w) {
+            launch_factor_wave(t, d, L, ws, precision, w, st, P);
+            g.list = d.solve_list + t.wave_off[w];
+            g.nlist = t.wave_off[w + 1] - t.wave_off[w];
+            g.count_unconverged = 0;
+            launch_local_pass(t, d, g, W, false, d.solve_variant, st, P);
+            MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<g.nlist, kThreads, 0, st>>>(g.subs, g.list, coef, g.rhs_dir,
+                        f, geo, t.n_cells, g.X, g.bnorm, nullptr));
+            g.passes = kPpMixedSweeps;
+            g.tol2 = kPpMixedTol * kPpMixedTol;
+            launch_local_pass(t, d, g, W, true, d.sweep_variant, st, P);
+            g.passes = 1;
+            g.tol2 = tol * tol;
+        }
+        // (2) the tied Neumann blocks too ill-conditioned for that: FP64 block factors in the W
+        // region (post-processing waves), FP64 solve and refinement of the one column.  A
+        // non-positive FP32 pivot of (1) only marks a block for this stage (its column then does
+        // not converge): the count restarts for the FP64 factors.
+        MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(status + ST_NOT_SPD, 0));
         g.subs = d.pp_subs;
         g.bar_off = (int)d.f64_solve_smem - 16;
         const int nw = (int)t.pp_wave_off.size() - 1;
         int bmax = 0;
         for (const SubInfo& s : t.subs) bmax = std::max(bmax, s.b);
+        int* plist = (int*)(ws + L.pp_list);
+        int* cnt = status + ST_FB_WAVE;
+        g.list = plist;
+        g.nlist_dev = cnt;
         for (int w = 0; w < nw; ++w) {
             const int n = t.pp_wave_off[w + 1] - t.pp_wave_off[w];
-            g.list = d.solve_list + t.pp_wave_off[w];
             g.nlist = n;
+            MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(cnt, 0));
+            MRCM_LAUNCH(P, "k_pp_unconverged", st, k_pp_unconverged<<<(n + 127) / 128, 128, 0, st>>>(d.subs,
+                        d.solve_list + t.pp_wave_off[w], n, g.conv, plist, cnt, status + ST_FB_TOTAL));
             MRCM_LAUNCH(P, "k_pp_factor", st, k_block_factor<double, false><<<n, kThreads, factor_smem<double>(bmax), st>>>(
-                        d.pp_subs, g.list, coef, (const double*)(ws + L.scale), (double*)(ws + L.W), status, t.n_cells,
-                        nullptr, nullptr, nullptr, nullptr));
+                        d.pp_subs, plist, coef, (const double*)(ws + L.scale), (double*)(ws + L.W), status, t.n_cells,
+                        nullptr, nullptr, cnt, nullptr));
             const int grid = std::max(1, std::min(n, d.sms * d.f64_occ));
             void* args[] = {(void*)&g, (void*)&W};
             g.count_unconverged = 0;
             MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
             MRCM_LAUNCH(P, "k_pp_solve", st, cudaLaunchKernel(solve_kernel<double, false, false>(0), dim3(grid),
                         dim3(variant_threads(0)), args, d.f64_solve_smem, st));
-            MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<n, kThreads, 0, st>>>(g.subs, g.list, coef, g.rhs_dir,
-                        f, geo, t.n_cells, g.X, g.bnorm));
+            MRCM_LAUNCH(P, "k_pp_scale", st, k_pp_scale<<<n, kThreads, 0, st>>>(g.subs, plist, coef, g.rhs_dir,
+                        f, geo, t.n_cells, g.X, g.bnorm, cnt));
             for (int it = 0; it < sweeps; ++it) {
                 g.count_unconverged = it + 1 == sweeps ? 1 : 0;
                 MRCM_LAUNCH(P, "k_set_int", st, k_set_int<<<1, 1, 0, st>>>(g.queue, 0));
@@ -2277,6 +2325,7 @@ int launch_postprocess(const Tables& t, const DeviceTables& d, const Layout& L, 
                             dim3(variant_threads(0)), args, d.f64_solve_smem, st));
             }
         }
+        g.nlist_dev = nullptr;
     }
     double* psum = (double*)(ws + L.psum);
     unsigned long long* mbits = (unsigned long long*)(psum + nsub + 1);

@@ -538,6 +538,7 @@ void compute_layout(const Tables& t, Layout& L) {
         L.fb_subs = take((size_t)cap * sizeof(SubInfo));
         L.fb_list = take((size_t)cap * sizeof(int));
     }
+    L.pp_list = take((size_t)std::max<size_t>(t.subs.size(), 1) * sizeof(int));
     L.big = take((size_t)t.big_slots * ((size_t)kMaxBlock * (kMaxBlock + 1) / 2) * sizeof(double));
     L.total = off;
 }
