@@ -31,6 +31,7 @@ struct mrcm_net {
     std::vector<long long> act_off;      // offsets (floats per sample) of stored activations
     long long act_per_sample = 0;
     int max_ch = 0;
+    bool mma_ok = false;                 // 32 -> 32 layers take the tensor-core forward (its shared memory fits)
 };
 
 namespace mrcm {
@@ -55,6 +56,7 @@ __device__ __forceinline__ int tap_offset_ok(const ConvShape& sh, int p, int tap
 // out[b][co][p] = act( bias[co] + sum_ci sum_tap w[co][ci][tap] in[b][ci][p + tap] )
 // Weights come from the BF16 copy; the CTA stages them as FP32 [ci][tap][co].
 // mode 0: leaky ReLU, 1: logistic, 2: none.  One CTA per sample.
+template <int CO>   // accumulators per thread: kMaxCh, or 1 for the one-channel output layer
 __global__ void __launch_bounds__(kNetThreads)
 k_conv_forward(ConvShape sh, int Cin, int Cout, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
                const float* __restrict__ in, float* __restrict__ out, int mode) {
@@ -71,9 +73,9 @@ k_conv_forward(ConvShape sh, int Cin, int Cout, const __nv_bfloat16* __restrict_
     __syncthreads();
     float* ob = out + (long long)b * Cout * sh.S;
     for (int p = threadIdx.x; p < sh.S; p += blockDim.x) {
-        float acc[kMaxCh];
+        float acc[CO];
 #pragma unroll
-        for (int co = 0; co < kMaxCh; ++co) acc[co] = 0.0f;
+        for (int co = 0; co < CO; ++co) acc[co] = 0.0f;
         for (int tap = 0; tap < 27; ++tap) {
             int q;
             if (!tap_offset_ok(sh, p, tap, &q)) continue;
@@ -81,17 +83,145 @@ k_conv_forward(ConvShape sh, int Cin, int Cout, const __nv_bfloat16* __restrict_
                 const float x = xin[ci * sh.S + q];
                 const float* wr = ws + (ci * 27 + tap) * Cout;
 #pragma unroll
-                for (int co = 0; co < kMaxCh; ++co)
+                for (int co = 0; co < CO; ++co)
                     if (co < Cout) acc[co] = fmaf(wr[co], x, acc[co]);
             }
         }
 #pragma unroll
-        for (int co = 0; co < kMaxCh; ++co) {
+        for (int co = 0; co < CO; ++co) {
             if (co >= Cout) break;
             float v = acc[co] + bias[co];
             if (mode == 0) v = v > 0.0f ? v : kLeak * v;
             else if (mode == 1) v = 1.0f / (1.0f + __expf(-v));
             ob[(long long)co * sh.S + p] = v;
+        }
+    }
+}
+
+// The same forward for a 32 -> 32 channel layer as an implicit GEMM on the BF16
+// tensor cores: out[co][p] = bias[co] + sum_k A[co][k] B[k][p] with k = tap 32 + ci,
+// A = the BF16 weights (exact in BF16), B[k][p] = in[ci][p + tap] cut into three BF16
+// pieces x = x1 + x2 + x3 (x1 the rounded value, x2 and x3 the rounded remainders, which
+// carry x to FP32 accuracy); mma.sync m16n8k16 with FP32 accumulation (a BF16 x BF16
+// product is exact in FP32), so the result matches the FP32 direct convolution to FP32
+// rounding.  The sample sits in shared memory with a zero halo, channels innermost
+// ([padded voxel][32] FP32), the weights as [co][k] BF16 pairs; one CTA per SM walks the
+// samples, staging the weights once.  Each warp takes up to 8 tiles of 8 voxels at a time.
+constexpr int kMmaCh = 32;
+constexpr int kMmaTiles = 8;
+size_t conv_mma_smem(const ConvShape& sh) {
+    return sizeof(float) * (size_t)(sh.D + 2) * (sh.H + 2) * (sh.W + 2) * kMmaCh + sizeof(uint32_t) * kMmaCh * 27 * kMmaCh / 2;
+}
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+// v = v1 + v2 + v3, each a BF16 pair (low half = v.x)
+__device__ __forceinline__ void split3_bf16(float2 v, uint32_t& p1, uint32_t& p2, uint32_t& p3) {
+    const __nv_bfloat162 h1 = __float22bfloat162_rn(v);
+    const float2 f1 = __bfloat1622float2(h1);
+    const float2 r1 = make_float2(v.x - f1.x, v.y - f1.y);
+    const __nv_bfloat162 h2 = __float22bfloat162_rn(r1);
+    const float2 f2 = __bfloat1622float2(h2);
+    const float2 r2 = make_float2(r1.x - f2.x, r1.y - f2.y);
+    p1 = bf2_bits(h1);
+    p2 = bf2_bits(h2);
+    p3 = bf2_bits(__float22bfloat162_rn(r2));
+}
+__global__ void __launch_bounds__(kNetThreads, 1)
+k_conv_forward_mma(ConvShape sh, int batch, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
+                   const float* __restrict__ in, float* __restrict__ out, int mode) {
+    extern __shared__ __align__(16) unsigned char smc[];
+    const int Hp = sh.H + 2, Wp = sh.W + 2, Sp = (sh.D + 2) * Hp * Wp;
+    constexpr int KW = 27 * kMmaCh / 2;                                 // BF16 pairs per weight row
+    float* xs = reinterpret_cast<float*>(smc);                          // [Sp][32]
+    uint32_t* wsm = reinterpret_cast<uint32_t*>(xs + (size_t)Sp * kMmaCh);   // [co][KW]
+    for (int e = threadIdx.x; e < kMmaCh * KW; e += blockDim.x) {
+        const int co = e / KW, r = e - co * KW, tap = r / (kMmaCh / 2), cp = r - tap * (kMmaCh / 2);
+        const __nv_bfloat16 lo = w[(co * kMmaCh + 2 * cp) * 27 + tap], hi = w[(co * kMmaCh + 2 * cp + 1) * 27 + tap];
+        wsm[e] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+    for (int e = threadIdx.x; e < Sp * kMmaCh; e += blockDim.x) xs[e] = 0.0f;   // the halo stays zero
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int nwarps = blockDim.x >> 5;
+    const int ntiles = (sh.S + 7) / 8;
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        __syncthreads();                                                // previous sample done with xs
+        const float* ib = in + (long long)b * kMmaCh * sh.S;
+        for (int e = threadIdx.x; e < kMmaCh * sh.S; e += blockDim.x) {
+            const int ci = e / sh.S, p = e - ci * sh.S;
+            const int z = p / (sh.H * sh.W), r = p - z * sh.H * sh.W, y = r / sh.W, x = r - y * sh.W;
+            xs[(((z + 1) * Hp + y + 1) * Wp + x + 1) * kMmaCh + ci] = ib[e];
+        }
+        __syncthreads();
+        for (int nt0 = warp; nt0 < ntiles; nt0 += nwarps * kMmaTiles) {
+            float acc[kMmaTiles][2][4];
+            int pvb[kMmaTiles];
+#pragma unroll
+            for (int j = 0; j < kMmaTiles; ++j) {
+                const int p = (nt0 + nwarps * j) * 8 + g;
+                int pv = (Hp + 1) * Wp + 1;                             // padding columns: voxel 0 (all 27
+                                                                        // neighbours in range), discarded
+                if (nt0 + nwarps * j < ntiles && p < sh.S) {
+                    const int z = p / (sh.H * sh.W), r = p - z * sh.H * sh.W, y = r / sh.W, x = r - y * sh.W;
+                    pv = ((z + 1) * Hp + y + 1) * Wp + x + 1;
+                }
+                pvb[j] = pv;
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[j][mt][q] = 0.0f;
+            }
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int toff = ((tap / 9 - 1) * Hp + (tap / 3) % 3 - 1) * Wp + tap % 3 - 1;
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    const int kw = tap * (kMmaCh / 2) + kc * 8 + t;
+                    uint32_t a[2][4];
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const int r0 = mt * 16 + g;
+                        a[mt][0] = wsm[r0 * KW + kw];
+                        a[mt][1] = wsm[(r0 + 8) * KW + kw];
+                        a[mt][2] = wsm[r0 * KW + kw + 4];
+                        a[mt][3] = wsm[(r0 + 8) * KW + kw + 4];
+                    }
+#pragma unroll
+                    for (int j = 0; j < kMmaTiles; ++j) {
+                        if (nt0 + nwarps * j >= ntiles) break;          // warp-uniform
+                        const float* xp = xs + (pvb[j] + toff) * kMmaCh + kc * 16 + 2 * t;
+                        uint32_t b1[2], b2[2], b3[2];
+                        split3_bf16(*reinterpret_cast<const float2*>(xp), b1[0], b2[0], b3[0]);
+                        split3_bf16(*reinterpret_cast<const float2*>(xp + 8), b1[1], b2[1], b3[1]);
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt) {
+                            mma_bf16_16816(acc[j][mt], a[mt], b3);      // smallest pieces first
+                            mma_bf16_16816(acc[j][mt], a[mt], b2);
+                            mma_bf16_16816(acc[j][mt], a[mt], b1);
+                        }
+                    }
+                }
+            }
+            float* ob = out + (long long)b * kMmaCh * sh.S;
+#pragma unroll
+            for (int j = 0; j < kMmaTiles; ++j) {
+                const int nt = nt0 + nwarps * j;
+                if (nt >= ntiles) break;
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int co = mt * 16 + g + (q >> 1) * 8, p = nt * 8 + 2 * t + (q & 1);
+                        if (p >= sh.S) continue;
+                        float v = acc[j][mt][q] + bias[co];
+                        if (mode == 0) v = v > 0.0f ? v : kLeak * v;
+                        else if (mode == 1) v = 1.0f / (1.0f + __expf(-v));
+                        ob[(long long)co * sh.S + p] = v;
+                    }
+            }
         }
     }
 }
@@ -299,9 +429,21 @@ void forward(const mrcm_net* n, const NetPtrs& p, const float* x, int batch, flo
     for (int l = 0; l < n->layers; ++l) {
         float* out = acts + (long long)batch * n->act_off[l];
         const int mode = l + 1 == n->layers ? 1 : 0;
-        const size_t sm = mrcm::conv_smem(n->cin[l], n->cout[l], n->S);
-        mrcm::k_conv_forward<<<batch, mrcm::kNetThreads, sm, st>>>(sh, n->cin[l], n->cout[l], p.wb + n->w_off[l],
-                                                                  p.w + n->b_off[l], in, out, mode);
+        if (n->cin[l] == mrcm::kMmaCh && n->cout[l] == mrcm::kMmaCh && n->mma_ok) {
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            mrcm::k_conv_forward_mma<<<std::max(1, std::min(batch, sms)), mrcm::kNetThreads, mrcm::conv_mma_smem(sh), st>>>(
+                sh, batch, p.wb + n->w_off[l], p.w + n->b_off[l], in, out, mode);
+        } else {
+            const size_t sm = mrcm::conv_smem(n->cin[l], n->cout[l], n->S);
+            if (n->cout[l] == 1)
+                mrcm::k_conv_forward<1><<<batch, mrcm::kNetThreads, sm, st>>>(sh, n->cin[l], n->cout[l], p.wb + n->w_off[l],
+                                                                             p.w + n->b_off[l], in, out, mode);
+            else
+                mrcm::k_conv_forward<mrcm::kMaxCh><<<batch, mrcm::kNetThreads, sm, st>>>(sh, n->cin[l], n->cout[l],
+                    p.wb + n->w_off[l], p.w + n->b_off[l], in, out, mode);
+        }
         in = out;
     }
 }
@@ -360,7 +502,14 @@ mrcm_status mrcm_net_create(int in_channels, int hidden, int layers, int D, int 
     n->act_per_sample = aoff;
     const size_t sm = std::max(mrcm::conv_smem(hidden, hidden, n->S), mrcm::conv_smem(in_channels, hidden, n->S));
     if (sm > 227 * 1024) { delete n; return MRCM_ERR_NOT_IMPLEMENTED; }
-    cudaFuncSetAttribute(mrcm::k_conv_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(mrcm::k_conv_forward<mrcm::kMaxCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(mrcm::k_conv_forward<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {
+        const size_t smm = mrcm::conv_mma_smem(mrcm::ConvShape{n->D, n->H, n->W, n->S});
+        n->mma_ok = smm <= 227 * 1024 &&
+                    cudaFuncSetAttribute(mrcm::k_conv_forward_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm) == cudaSuccess;
+        cudaGetLastError();
+    }
     cudaFuncSetAttribute(mrcm::k_conv_backward_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     *out = n;
     return MRCM_OK;
