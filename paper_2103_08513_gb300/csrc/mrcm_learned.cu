@@ -106,9 +106,10 @@ k_conv_forward(ConvShape sh, int Cin, int Cout, const __nv_bfloat16* __restrict_
 // product is exact in FP32), so the result matches the FP32 direct convolution to FP32
 // rounding.  The sample sits in shared memory with a zero halo, channels innermost
 // ([padded voxel][32] FP32), the weights as [co][k] BF16 pairs; one CTA per SM walks the
-// samples, staging the weights once.  Each warp takes up to 8 tiles of 8 voxels at a time.
+// samples, staging the weights once.  Each of 16 warps takes up to 4 tiles of 8 voxels at a time.
 constexpr int kMmaCh = 32;
-constexpr int kMmaTiles = 8;
+constexpr int kMmaTiles = 4;
+constexpr int kMmaThreads = 512;
 size_t conv_mma_smem(const ConvShape& sh) {
     return sizeof(float) * (size_t)(sh.D + 2) * (sh.H + 2) * (sh.W + 2) * kMmaCh + sizeof(uint32_t) * kMmaCh * 27 * kMmaCh / 2;
 }
@@ -130,7 +131,7 @@ __device__ __forceinline__ void split3_bf16(float2 v, uint32_t& p1, uint32_t& p2
     p2 = bf2_bits(h2);
     p3 = bf2_bits(__float22bfloat162_rn(r2));
 }
-__global__ void __launch_bounds__(kNetThreads, 1)
+__global__ void __launch_bounds__(kMmaThreads, 1)
 k_conv_forward_mma(ConvShape sh, int batch, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
                    const float* __restrict__ in, float* __restrict__ out, int mode) {
     extern __shared__ __align__(16) unsigned char smc[];
@@ -433,7 +434,7 @@ void forward(const mrcm_net* n, const NetPtrs& p, const float* x, int batch, flo
             int dev = 0, sms = 1;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            mrcm::k_conv_forward_mma<<<std::max(1, std::min(batch, sms)), mrcm::kNetThreads, mrcm::conv_mma_smem(sh), st>>>(
+            mrcm::k_conv_forward_mma<<<std::max(1, std::min(batch, sms)), mrcm::kMmaThreads, mrcm::conv_mma_smem(sh), st>>>(
                 sh, batch, p.wb + n->w_off[l], p.w + n->b_off[l], in, out, mode);
         } else {
             const size_t sm = mrcm::conv_smem(n->cin[l], n->cout[l], n->S);
