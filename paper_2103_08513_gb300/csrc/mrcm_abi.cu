@@ -602,10 +602,17 @@ mrcm_status mrcm_solve_host(mrcm_handle* h, const double* K, const double* f, do
         const size_t nc = (size_t)h->t.n_cells, nx = (size_t)std::max(2 * h->t.NV, 1);
         h->io_bytes = (11 * nc + nx + 1) * sizeof(double);
         if ((e = cudaMalloc(&h->io, h->io_bytes)) != cudaSuccess) { h->io = nullptr; return cuda_fail(h, e, "cudaMalloc (staging)"); }
-        if ((e = cudaStreamCreateWithFlags(&h->io_side, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
-        for (auto& ev : h->io_ev)
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
     }
+    // side stream and events: created once; a call after a failed creation retries it
+    if (!h->io_side && (e = cudaStreamCreateWithFlags(&h->io_side, cudaStreamNonBlocking)) != cudaSuccess) {
+        h->io_side = nullptr;
+        return cuda_fail(h, e, "cudaStreamCreate");
+    }
+    for (auto& ev : h->io_ev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            ev = nullptr;
+            return cuda_fail(h, e, "cudaEventCreate");
+        }
     cudaStream_t s = (cudaStream_t)stream;
     if (!(flags & MRCM_SOLVE_GRAPH)) {
         st = host_body(h, K, f, X, p, u, mres, ws, ws_bytes, s);

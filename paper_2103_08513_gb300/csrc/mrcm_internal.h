@@ -223,8 +223,9 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     rest += sizeof(double) * mpad + sizeof(int) * mpad;    // nrm, cols
     rest += sizeof(short) * 6 * (size_t)N;                 // cf
     rest = (rest + 15) & ~size_t(15);
-    rest += (5 * sizeof(double) + sizeof(float) + sizeof(T) + 6) * (size_t)b + 16;   // one slab's stencil
-                                                      // coefficients, scale, slab coupling and face columns
+    rest += (5 * sizeof(double) + sizeof(float) + sizeof(T) + sizeof(unsigned) + 6) * (size_t)b + 16;
+                                                      // one slab's stencil coefficients, scale, slab
+                                                      // coupling, cell masks and face columns
     rest += 16;                                            // mbarriers (after the largest layout)
     L.nbuf = (2 * wb + rest + 128 <= kSolveTwoCta) ? 2 : (wb + rest + 128 <= kSolveSmemBudget ? 1 : 0);
     size_t x = 0;
@@ -243,7 +244,7 @@ inline SolveSmem solve_smem_layout(int b, int mpad, int N) {
     x += sizeof(short) * 6 * (size_t)N;
     x = (x + 15) & ~size_t(15);
     L.co = x;
-    x += (5 * sizeof(double) + sizeof(float) + sizeof(T) + 6) * (size_t)b + 16;
+    x += (5 * sizeof(double) + sizeof(float) + sizeof(T) + sizeof(unsigned) + 6) * (size_t)b + 16;
     L.total = (x + 127) & ~size_t(127);
     return L;
 }

@@ -1164,6 +1164,9 @@ __device__ __forceinline__ void block_product(const T* Wsm, const T* Z, int b, i
     }
 }
 
+// Neighbour flags of a slab cell in the local solve's per-cell mask (bits 0-15: bases mod 16).
+constexpr unsigned kNbUp = 1u << 16, kNbUm = 1u << 17, kNbVp = 1u << 18, kNbVm = 1u << 19;
+
 struct LocalArgs {
     const SubInfo* subs;
     const FaceInfo* faces;
@@ -1335,19 +1338,30 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
     // the slab's Jacobi scale (mixed mode) and its coupling to the neighbouring slab of the sweep
     T* t_s = reinterpret_cast<T*>(co_sm + b);
     float* sc_s = reinterpret_cast<float*>(t_s + b);
-    signed char* fcol_s = reinterpret_cast<signed char*>(sc_s + b);   // basis column of each cell side's face, -1 none
+    // per slab cell: bits 0-15 flag the bases (mod 16) of its Robin faces, bits 16-19 which
+    // in-slab neighbours exist (+u, -u, +v, -v)
+    unsigned* msk_s = reinterpret_cast<unsigned*>(sc_s + b);
+    signed char* fcol_s = reinterpret_cast<signed char*>(msk_s + b);  // basis column of each cell side's face, -1 none
     auto stage_slab = [&](int base, int nb_off) {       // nb_off: -b (forward), +b (backward)
         for (int i = threadIdx.x; i < b; i += blockDim.x) {
             const int c = base + i;
             if constexpr (kScaled) sc_s[i] = cp.scf[c];
             const int ct = nb_off < 0 ? c - b : c;
             t_s[i] = (nb_off < 0 ? c >= b : c + b < N) ? cp.t(ct) : (T)0;
-        }
-        if (nb_off < 0)
-            for (int k = threadIdx.x; k < 6 * b; k += blockDim.x) {
-                const int q = cf[6 * base + k];
-                fcol_s[k] = q >= 0 ? (signed char)g.faces[s.face_off + q].col : (signed char)-1;
+            if (nb_off < 0) {
+                const int u = i % su;
+                unsigned mk = (u + 1 < su ? kNbUp : 0u) | (u > 0 ? kNbUm : 0u) | (i + su < b ? kNbVp : 0u) |
+                              (i >= su ? kNbVm : 0u);
+#pragma unroll
+                for (int a = 0; a < 6; ++a) {
+                    const int q = cf[6 * c + a];
+                    const int col = q >= 0 ? g.faces[s.face_off + q].col : -1;
+                    fcol_s[6 * i + a] = (signed char)col;
+                    if (col >= 0) mk |= 1u << (col & 15);
+                }
+                msk_s[i] = mk;
             }
+        }
     };
     auto zin = [&](double r, float rf, int i) -> T {
         if constexpr (kScaled) return rf * sc_s[i];
@@ -1383,31 +1397,34 @@ __device__ __forceinline__ void solve_one(const LocalArgs& g, const T* __restric
             for (int e = threadIdx.x; e < na * b; e += NT) {
                 const int j = cols[jj];
                 const int c = base + i;
+                const unsigned mk = msk_s[i];
                 double r;
                 if (j == m - 1) {
                     int lc[3];
                     local_coords(s, c, lc);
                     r = g.rhs_dir[s.cell_off + c] + g.f[global_cell(s, lc, g.geo.n)] * vol;
                 } else {
-                    // MBF column: the value on the one Robin face of this cell that carries
-                    // basis j, if any (faces of one cell belong to different bases); moves only
+                    // MBF column of basis kb (P for j < nI, U after): the value on the one Robin
+                    // face of this cell that carries kb, if any (faces of one cell belong to
+                    // different bases); the mask rules out most cells, moves only
                     r = 0.0;
+                    const int kb = j < nI ? j : j - nI;
+                    if ((mk >> (kb & 15)) & 1u) {
 #pragma unroll
-                    for (int a = 0; a < 6; ++a) {
-                        const int col = fcol_s[6 * i + a];
-                        if (col < 0) continue;
-                        if (j == col) r = g.face_tr[s.face_off + cf[6 * c + a]];
-                        else if (j == nI + col) r = g.face_u[s.face_off + cf[6 * c + a]];
+                        for (int a = 0; a < 6; ++a)
+                            if (fcol_s[6 * i + a] == kb) {
+                                const int q = s.face_off + cf[6 * c + a];
+                                r = j < nI ? g.face_tr[q] : g.face_u[q];
+                            }
                     }
                 }
                 if (kSweep) {                     // r - A x as one FMA chain
                     const double* x = Xs + (long long)j * N;
-                    const int u = i % su;
                     r = fma(-co_d[i], x[c], r);
-                    if (u + 1 < su) r = fma(co_u[i], x[c + 1], r);
-                    if (u > 0) r = fma(co_u[i - 1], x[c - 1], r);
-                    if (i + su < b) r = fma(co_v[i], x[c + su], r);
-                    if (i >= su) r = fma(co_v[i - su], x[c - su], r);
+                    if (mk & kNbUp) r = fma(co_u[i], x[c + 1], r);
+                    if (mk & kNbUm) r = fma(co_u[i - 1], x[c - 1], r);
+                    if (mk & kNbVp) r = fma(co_v[i], x[c + su], r);
+                    if (mk & kNbVm) r = fma(co_v[i - su], x[c - su], r);
                     if (c + b < N) r = fma(co_sp[i], x[c + b], r);
                     if (c >= b) r = fma(co_sm[i], x[c - b], r);
                 }
