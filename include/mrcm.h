@@ -154,6 +154,9 @@ typedef struct {
                                    run on a cluster of CTAs from 128 on) */
     int max_front_nb;           /* largest boundary block of a front (its back substitution
                                    is split into row chunks above 128) */
+    double ldl_update_tensor_flops; /* BF16 tensor-core flops the emulated trailing updates
+                                   execute (all slice products of the steps that emulate;
+                                   ldl_update_flops counts the FP64 work they stand for) */
 } mrcm_sizes;
 
 typedef struct mrcm_handle mrcm_handle;

@@ -52,6 +52,7 @@ class mrcm_sizes(C.Structure):
         ("n_waves", C.c_int),
         ("max_front_ne", C.c_int),
         ("max_front_nb", C.c_int),
+        ("ldl_update_tensor_flops", C.c_double),
     ]
 
 

@@ -232,6 +232,7 @@ mrcm_status mrcm_query_sizes(const mrcm_handle* h, mrcm_sizes* o) {
     o->mbf_entries = t.total_x;
     o->ldl_flops = t.ldl_flops;
     o->ldl_update_flops = t.ldl_update_flops;
+    o->ldl_update_tensor_flops = t.ldl_update_tensor_flops;
     o->n_waves = t.n_waves;
     o->max_front_ne = 0;
     o->max_front_nb = 0;

@@ -274,8 +274,6 @@ constexpr int kPanelRows = 4;           // warp passes per panel-kernel CTA (one
 // operations per entry instead of one FMA per panel column.
 constexpr int kOzS = 8;                     // slices per operand
 constexpr int kOzRowWords = 2 * kOzS * kPanel / 2;   // u32 words per slice row (2 operands x 8 slices x 32 bf16)
-constexpr int kOzMinM = 24;                 // emulate when the trailing block has >= kOzMinM rows
-constexpr int kOzMinK = 4;                  // and the panel >= kOzMinK columns
 
 __device__ __forceinline__ bool oz_step(const FrontInfo& fr, int m, int nbk) {
     return fr.s_off >= 0 && m >= kOzMinM && nbk >= kOzMinK;

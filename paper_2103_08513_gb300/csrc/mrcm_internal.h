@@ -16,6 +16,11 @@ constexpr int kRegBlock = 64;       // blocks with b <= kRegBlock use the regist
 constexpr int kMaxSolveVariants = 16;  // capacity of the per-variant tables
 constexpr int kNumFactorVariants = 3;  // factor kernels for blocks with b <= 64
 constexpr int kOzMinN = 32;        // fronts with n >= kOzMinN may take the tensor-core emulated FP64 update
+constexpr int kOzMinM = 24;        // a step emulates when the trailing block has >= kOzMinM rows
+constexpr int kOzMinK = 4;         // and the panel >= kOzMinK columns
+// BF16 flops one 32 x 32 tile of the emulated update executes: 8 warps x 36 slice pairs
+// (8 slices per operand, pairs with t + u < 8) x 2 halves of the panel x m16n8k16 MMAs
+constexpr double kOzTileFlops = 8.0 * 36.0 * 2.0 * (2.0 * 16 * 8 * 16);
 constexpr int kTileBlock = 128;     // 64 < b <= kTileBlock: register-tiled FP32 factor (8 x 8 per thread)
 constexpr int kMaxI = 128;          // largest |I^l| (basis functions touching one subdomain)
 
@@ -120,7 +125,7 @@ struct Tables {
     int total_panels = 0;          // sum over fronts of ceil(ne / 32)
     long long oz_rows = 0;         // slice rows of the emulated trailing update (max over levels)
     int max_front = 0;
-    double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
+    double front_flops = 0, ldl_flops = 0, ldl_update_flops = 0, ldl_update_tensor_flops = 0, local_factor_flops = 0, local_solve_flops = 0;
     int root = -1;
     int pin_front = -1;
 

@@ -1018,9 +1018,18 @@ __device__ __forceinline__ typename Vec4<T>::type ld4(const T* p) { return *rein
 // Y[i][jj] = sum_k W[k][i] Z[k][jj] for i < b, jj < na; thread tile RT rows x 4
 // columns (rows i0, i0 + bh, ..., bh = ceil(b / RT)).  Results are handed to
 // `store(i, jj, value)`.
+template <int RT, typename Store>
+__device__ __forceinline__ void block_gemm_sh(const float* Wsm, const float* Z, int b, int na, int mpad, Store store);
+
 template <typename T, int RT, typename Store>
 __device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* __restrict__ Z, int b, int na,
                                            int mpad, Store store) {
+    if constexpr (std::is_same<T, float>::value && RT <= 2) {   // (four rows per thread would spill)
+        if (__isShared(Wsm)) {                    // staged W block (otherwise W is read from global memory)
+            block_gemm_sh<RT>(Wsm, Z, b, na, mpad, store);
+            return;
+        }
+    }
     const int bh = (b + RT - 1) / RT;
     const int mq = (na + 3) >> 2;
     for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
@@ -1054,15 +1063,107 @@ __device__ __forceinline__ void block_gemm(const T* __restrict__ Wsm, const T* _
     }
 }
 
+// block_gemm with both operands in shared memory (FP32): 32-bit shared
+// addresses stepped by the row strides.  Rows past the block read row b - 1
+// (their sums are never stored), so the loads need no guard.  The same FMAs in
+// the same order as the generic form.
+template <int RT, typename Store>
+__device__ __forceinline__ void block_gemm_sh(const float* Wsm, const float* Z, int b, int na, int mpad, Store store) {
+    const int bh = (b + RT - 1) / RT;
+    const int mq = (na + 3) >> 2;
+    const uint32_t zbase = smem_u32(Z), wbase = smem_u32(Wsm);
+    const uint32_t zstep = 4u * (uint32_t)mpad, wstep = 4u * (uint32_t)b;
+    for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
+        const int i0 = task % bh, cq = task / bh;
+        float acc[RT][4];
+        uint32_t wr[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+            wr[r] = wbase + 4u * (uint32_t)min(i0 + r * bh, b - 1);
+        }
+        uint32_t za = zbase + 16u * (uint32_t)cq, ko = 0;
+        for (int k = 0; k < b; ++k) {
+            float4 z;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(z.x), "=f"(z.y), "=f"(z.z), "=f"(z.w) : "r"(za));
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                float w;
+                asm volatile("ld.shared.f32 %0, [%1];" : "=f"(w) : "r"(wr[r] + ko));
+                acc[r][0] += w * z.x; acc[r][1] += w * z.y; acc[r][2] += w * z.z; acc[r][3] += w * z.w;
+            }
+            za += zstep;
+            ko += wstep;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * cq + q;
+            if (jj < na) {
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    const int i = i0 + r * bh;
+                    if (i < b) store(i, jj, acc[r][q]);
+                }
+            }
+        }
+    }
+}
+
 // Pair tile (b even): thread tile of rows (i0, i0 + 1) x 4 columns, one
 // 2-element load of W and one 4-element load of Z per k for 8 FMAs, no row
 // guard (every row pair lies inside the block).
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
+
+// The pair tile with both operands in shared memory (FP32): 32-bit shared
+// addresses stepped by the row strides, vector shared loads.  The same FMAs
+// in the same order as the generic form below.
+template <typename Store>
+__device__ __forceinline__ void block_gemm_pair_sh(const float* Wsm, const float* Z, int b, int na, int mpad,
+                                                   Store store) {
+    const int bh = b >> 1;
+    const int mq = (na + 3) >> 2;
+    const uint32_t zbase = smem_u32(Z), wbase = smem_u32(Wsm);
+    const uint32_t zstep = 4u * (uint32_t)mpad, wstep = 4u * (uint32_t)b;
+    for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {
+        const int i0 = 2 * (task % bh), cq = task / bh;
+        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t za = zbase + 16u * (uint32_t)cq, wa = wbase + 4u * (uint32_t)i0;
+#pragma unroll 2
+        for (int k = 0; k < b; ++k) {
+            float4 z;
+            float2 w;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(z.x), "=f"(z.y), "=f"(z.z), "=f"(z.w) : "r"(za));
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(w.x), "=f"(w.y) : "r"(wa));
+            za += zstep;
+            wa += wstep;
+            a0[0] += w.x * z.x; a0[1] += w.x * z.y; a0[2] += w.x * z.z; a0[3] += w.x * z.w;
+            a1[0] += w.y * z.x; a1[1] += w.y * z.y; a1[2] += w.y * z.z; a1[3] += w.y * z.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * cq + q;
+            if (jj < na) {
+                store(i0, jj, a0[q]);
+                store(i0 + 1, jj, a1[q]);
+            }
+        }
+    }
+}
+
 template <typename T, typename Store>
 __device__ __forceinline__ void block_gemm_pair(const T* __restrict__ Wsm, const T* __restrict__ Z, int b, int na,
                                                 int mpad, Store store) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (__isShared(Wsm)) {                    // staged W block (otherwise W is read from global memory)
+            block_gemm_pair_sh(Wsm, Z, b, na, mpad, store);
+            return;
+        }
+    }
     const int bh = b >> 1;
     const int mq = (na + 3) >> 2;
     for (int task = threadIdx.x; task < bh * mq; task += blockDim.x) {

@@ -428,6 +428,15 @@ mrcm_status build_tables(const mrcm_config* cfg, Tables& t, std::string& err) {
             }
             t.oz_rows = std::max(t.oz_rows, rows);
         }
+        for (const FrontInfo& f : t.fronts) {         // BF16 work of the steps the update emulates
+            if (f.s_off < 0) continue;
+            for (int k0 = 0; k0 < f.ne; k0 += 32) {
+                const int nbk = std::min(32, f.ne - k0), m = f.n - k0 - nbk;
+                if (m < kOzMinM || nbk < kOzMinK) continue;
+                const double nt = (m + 31) / 32;
+                t.ldl_update_tensor_flops += nt * (nt + 1.0) / 2.0 * kOzTileFlops;
+            }
+        }
         t.total_front = foff;
         t.total_frhs = roff;
         if (t.root < 0 || t.fronts[t.root].nb != 0) { err = "internal: elimination tree root keeps boundary dofs"; return MRCM_ERR_INVALID_ARG; }

@@ -112,6 +112,13 @@ def test_c2_sizes(lib):
     sz = mrcm_sizes()
     lib.mrcm_query_sizes(h, C.byref(sz))
     assert sz.n_sub == 2244 and sz.max_rhs == 33 and 2 * sz.n_basis == 32944
+    # the emulated trailing updates: whole 32 x 32 tiles, each 8 warps x 36 slice pairs x 2
+    # m16n8k16 BF16 MMAs; at C2 every step with a trailing block of >= 24 rows emulates, and the
+    # tiles (at most 32 x 32 entries x 2 x 32 FP64-equivalent flops each) cover the update's work
+    tile = 8 * 36 * 2 * (2 * 16 * 8 * 16)
+    tiles = sz.ldl_update_tensor_flops / tile
+    assert tiles == int(tiles) and tiles > 0
+    assert tiles * 32 * 32 * 2 * 32 >= sz.ldl_update_flops
     lib.mrcm_destroy(h)
 
 
