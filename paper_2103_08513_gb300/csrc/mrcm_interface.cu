@@ -99,6 +99,13 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 // from the fresh diagonal, while warps 1.. update the other rows.  A zero or
 // NaN pivot is replaced by 1 and counted.  Block-wide, >= 2 warps.
 constexpr int kDiagW = 2 * kPanel + 1;
+
+// v == 0 or NaN, from the bits (integer operations: an FP64 compare would add
+// an FP64-unit latency to the pivot chain).
+__device__ __forceinline__ bool zero_or_nan(double v) {
+    const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    return m == 0ull || m > 0x7FF0000000000000ull;
+}
 constexpr int kDiagWork = kPanel * kDiagW + kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
                                   int* status, double* work) {
@@ -118,15 +125,16 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
     if (tid == 0) {
         *zero = 0;
         double d = T[0][0];
-        if (d == 0.0 || d != d) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
+        if (zero_or_nan(d)) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
         sinv[0] = rcp64c(d);
     }
     for (int k = 0; k < nbk; ++k) {
         __syncthreads();                                      // rows of step k - 1 done, 1 / d_k ready
-        const double inv = sinv[k];
         const int c = lane;
-        // this lane's multiplier and target column
+        // this lane's multiplier and target column (only warps with a row this step form it)
         const bool vpart = c <= k;
+        if (k + 1 + (w == 0 ? 0 : w) >= nbk) continue;
+        const double inv = sinv[k];
         const double wc = (vpart ? T[k][kPanel + c] : T[c][k]) * inv;
         if (w == 0) {
             if (k + 1 < nbk) {
@@ -135,7 +143,7 @@ __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk
                     double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
                     double v = fma(-T[i][k], wc, *dst);
                     if (c == i) {                             // the next pivot, straight from the register
-                        if (v == 0.0 || v != v) { v = 1.0; *zero = 1; }
+                        if (zero_or_nan(v)) { v = 1.0; *zero = 1; }
                         sinv[i] = rcp64c(v);
                     }
                     *dst = v;
