@@ -87,17 +87,21 @@ __device__ __forceinline__ double dof_sign(int dof, int NV) { return dof < NV ? 
 
 // LDL^T of the nbk x nbk (nbk <= 32) diagonal block of a front, in place
 // (strict lower part becomes L11, the diagonal D), together with V = L11^{-1}.
-// Row i of the work array T holds [row i of the block | row i of V]; V starts
-// as I.  Step k: with w_c = T[c][k] / d_k on the block part (k < c) and
-// w_c = V[k][c] / d_k on the V part (c <= k), every row i > k takes
-//   T[i][c] -= T[i][k] w_c   (k < c <= i, and all c <= k of V),
+// Row i of the work array T holds [row i of the block, both triangles | row i
+// of V]; V starts as I.  Step k: with the multipliers w_c = T[k][c] / d_k on
+// the block part (k < c) and w_c = V[k][c] / d_k on the V part (c <= k), every
+// row i > k takes
+//   T[i][c] -= T[i][k] w_c   (every block column c > k and every c <= k of V),
 // the rank-1 Schur update of the block and V <- (I - l e_k^T) V at once (row k
 // of V is final at step k).  Block column k is not written after step k - 1,
 // so L = T[i][k] / d_k is formed once at the end: one barrier per pivot.  One
 // lane per column: a row costs one FP64 FMA per step.  Warp 0 updates row
-// k + 1 alone and its lane k + 1 computes 1 / d_{k+1} (one cubic Newton step)
-// from the fresh diagonal, while warps 1.. update the other rows.  A zero or
-// NaN pivot is replaced by 1 and counted.  Block-wide, >= 2 warps.
+// k + 1 alone; its lane k + 1 computes 1 / d_{k+1} (one cubic Newton step)
+// from the fresh diagonal, and the warp forms the next step's multipliers
+// from the row it holds (the upper triangle is kept for that) into one of two
+// shared vectors, so the other warps, which update the remaining rows, read
+// them instead of each forming them.  A zero or NaN pivot is replaced by 1
+// and counted.  Block-wide, >= 2 warps.
 constexpr int kDiagW = 2 * kPanel + 1;
 
 // v == 0 or NaN, from the bits (integer operations: an FP64 compare would add
@@ -106,55 +110,59 @@ __device__ __forceinline__ bool zero_or_nan(double v) {
     const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
     return m == 0ull || m > 0x7FF0000000000000ull;
 }
-constexpr int kDiagWork = kPanel * kDiagW + kPanel + 4;   // doubles of shared work space
+
+constexpr int kDiagWork = kPanel * kDiagW + 3 * kPanel + 4;   // doubles of shared work space
 __device__ void factor_diag_block(double* __restrict__ A, int n, int k0, int nbk, double* __restrict__ Pinv,
                                   int* status, double* work) {
     double (*T)[kDiagW] = reinterpret_cast<double (*)[kDiagW]>(work);
     double* sinv = work + kPanel * kDiagW;                    // 1 / d_k for every k
-    int* zero = reinterpret_cast<int*>(sinv + kPanel);
+    double* swc = sinv + kPanel;                              // multipliers of step k at swc[(k & 1) * kPanel]
+    int* zero = reinterpret_cast<int*>(swc + 2 * kPanel);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nthr >> 5;
     __syncthreads();                                          // the block's last writes are complete
     for (int e = tid; e < kPanel * 2 * kPanel; e += nthr) {
         const int i = e >> 6, c = e & 63;
         double v;
-        if (c < kPanel) v = (i < nbk && c <= i) ? A[(long long)(k0 + i) * n + k0 + c] : 0.0;
+        if (c < kPanel) v = (i < nbk && c < nbk) ? A[(long long)(k0 + max(i, c)) * n + k0 + min(i, c)] : 0.0;
         else v = (c - kPanel == i) ? 1.0 : 0.0;
         T[i][c] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        *zero = 0;
+    if (w == 0) {                                             // the first pivot and its multipliers
         double d = T[0][0];
-        if (zero_or_nan(d)) { d = 1.0; T[0][0] = 1.0; *zero = 1; }
-        sinv[0] = rcp64c(d);
+        const bool z = zero_or_nan(d);
+        if (z) d = 1.0;
+        const double inv0 = rcp64c(d);
+        swc[lane] = (lane == 0 ? 1.0 : T[0][lane]) * inv0;
+        if (lane == 0) {
+            *zero = z ? 1 : 0;
+            if (z) T[0][0] = 1.0;
+            sinv[0] = inv0;
+        }
     }
     for (int k = 0; k < nbk; ++k) {
-        __syncthreads();                                      // rows of step k - 1 done, 1 / d_k ready
+        __syncthreads();                                      // rows of step k - 1 done, multipliers of step k ready
         const int c = lane;
-        // this lane's multiplier and target column (only warps with a row this step form it)
         const bool vpart = c <= k;
-        if (k + 1 + (w == 0 ? 0 : w) >= nbk) continue;
-        const double inv = sinv[k];
-        const double wc = (vpart ? T[k][kPanel + c] : T[c][k]) * inv;
+        if (k + 1 + (w == 0 ? 0 : w) >= nbk) continue;        // no row for this warp at this step
+        const double wc = swc[(k & 1) * kPanel + c];
         if (w == 0) {
-            if (k + 1 < nbk) {
-                const int i = k + 1;
-                if (c <= i) {
-                    double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
-                    double v = fma(-T[i][k], wc, *dst);
-                    if (c == i) {                             // the next pivot, straight from the register
-                        if (zero_or_nan(v)) { v = 1.0; *zero = 1; }
-                        sinv[i] = rcp64c(v);
-                    }
-                    *dst = v;
-                }
+            const int i = k + 1;
+            double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
+            double v = fma(-T[i][k], wc, *dst);
+            double inv = 0.0;
+            if (c == i) {                                     // the next pivot, straight from the register
+                if (zero_or_nan(v)) { v = 1.0; *zero = 1; }
+                inv = rcp64c(v);
+                sinv[i] = inv;
             }
+            *dst = v;
+            inv = __shfl_sync(0xffffffffu, inv, i);
+            swc[((k + 1) & 1) * kPanel + c] = (c == i ? 1.0 : v) * inv;
         } else {
             for (int i = k + 1 + w; i < nbk; i += nw - 1) {
-                if (c <= i) {
-                    double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
-                    *dst = fma(-T[i][k], wc, *dst);
-                }
+                double* dst = vpart ? &T[i][kPanel + c] : &T[i][c];
+                *dst = fma(-T[i][k], wc, *dst);
             }
         }
     }
