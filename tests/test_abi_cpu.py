@@ -190,6 +190,16 @@ def test_device_calls_reject_bad_arguments_without_gpu(lib):
     assert lib.mrcm_factor_local(h, None, None, 0, None) == 1
     assert lib.mrcm_solve_mbf(h, C.c_void_p(256), C.c_void_p(256), None) == 9   # out of order
     assert lib.mrcm_factor_local(h, C.c_void_p(256), C.c_void_p(257), 1 << 30, None) == 1
+    # the host-buffer solve: workspace, buffers, stream and workspace size are checked first
+    ws_bytes, nif = C.c_size_t(), C.c_size_t()
+    assert lib.mrcm_query_workspace(h, C.byref(ws_bytes), C.byref(nif)) == 0
+    buf = [C.c_void_p(4096 * (q + 1)) for q in range(5)]
+    ws, st = C.c_void_p(1 << 20), C.c_void_p(0x100)
+    assert lib.mrcm_solve_host(h, *buf, None, None, ws_bytes.value, st, 0) == 1          # no workspace
+    assert lib.mrcm_solve_host(h, *buf, None, C.c_void_p((1 << 20) + 8), ws_bytes.value, st, 0) == 1
+    assert lib.mrcm_solve_host(h, None, *buf[1:], None, ws, ws_bytes.value, st, 0) == 1  # no K
+    assert lib.mrcm_solve_host(h, *buf, None, ws, ws_bytes.value, None, 0) == 1          # default stream
+    assert lib.mrcm_solve_host(h, *buf, None, ws, ws_bytes.value - 256, st, 0) == 7      # workspace too small
     lib.mrcm_destroy(h)
 
 
