@@ -116,7 +116,7 @@ void load_tune_cache(mrcm_handle* h) {
         int v0, v1, v2, v3, v4 = 0;
         const int n = sscanf(line, "%255s %d %d %d %d %d", key, &v0, &v1, &v2, &v3, &v4);
         if (n < 5) continue;
-        if (want == key && v0 >= 0 && v0 < mrcm::kMaxSolveVariants && v1 >= 0 && v1 < mrcm::kMaxSolveVariants &&
+        if (want == key && v0 >= 0 && v0 < mrcm::num_solve_variants() && v1 >= 0 && v1 < mrcm::num_solve_variants() &&
             v2 >= 0 && v2 < mrcm::kNumFactorVariants && (v3 == 0 || v3 == 1) && (v4 == 0 || v4 == 1)) {
             h->d.solve_variant = v0;
             h->d.sweep_variant = v1;
